@@ -1,0 +1,370 @@
+"""Benchmark: exact HN 1-NN queries/s on one B300 (or N, one process each).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c2|c1|c0]
+
+Workload (default c2): N = 4,000,000 database entries, a batch of 65,536
+queries, D = 128, K = 16, alpha = 1/8, clustered synthetic descriptors
+(800,000 centres, entry noise 0.15, query noise 0.10), BF16 major prefix.
+
+A step is one pass of the hot path over one query batch, all through the C
+ABI: HN normalisation of the raw queries, query prefix packing, Phase-1
+prefix scan, threshold from the Phase-1 winner, Phase-2 prefix scan with the
+bound test, survivor rescore with binary64 near-ties, argmax.  The database
+index (normalisation and SoA packing of the 4M entries) is built once before
+timing; its build time is reported separately.  L2 is flushed (256 MiB
+write) before every timed step.
+
+N > 1 (torchrun): every rank holds its own copy of the index and answers its
+own 65,536-query batch (weak scaling, no data-path collective); the barrier
+serves timing only.
+
+--impl reference times the binary64 CPU oracle on this host's cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hn_synth  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS))
+    ap.add_argument("--prefix", default=None, choices=["f32", "bf16"])
+    ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bruteforce", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, under_load = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    s, m, pw = float(parts[1]), float(parts[2]), float(parts[3])
+                except ValueError:
+                    continue
+                sm.append(s)
+                smax.append(m)
+                if pw > 200:
+                    under_load.append(s)
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        use = under_load or sm
+        return {"sm_mhz": statistics.median(use) if use else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(under_load)}
+
+
+# ---------------------------------------------------------------- oracle (CPU baseline)
+def cpu_baseline(wl, c, budget_s: float = 12.0):
+    """Time the binary64 oracle on this host on a bounded query sample of the same workload."""
+    import oracle
+    k, alpha = c["k"], c["alpha"]
+    t0 = time.perf_counter()
+    db = oracle.normalize(wl.db_raw, k, alpha)
+    norm_s = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    probe = min(8, wl.q_raw.shape[0])
+    q = oracle.normalize(wl.q_raw[:probe], k, alpha)
+    t0 = time.perf_counter()
+    oracle.search(db, q)
+    dt = time.perf_counter() - t0
+    per_q = dt / probe
+    m = int(max(probe, min(wl.q_raw.shape[0], budget_s / max(per_q, 1e-9))))
+    q = oracle.normalize(wl.q_raw[:m], k, alpha)
+    t0 = time.perf_counter()
+    oracle.search(db, q)
+    dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {m} of {wl.q_raw.shape[0]} queries against all {c['n']} entries "
+                      f"(binary64 exhaustive search, OpenMP over {cores} threads); "
+                      f"database normalisation {norm_s:.1f}s not included",
+            "seconds": dt}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return 0
+    wl, c = hn_synth.config_workload(args.workload)
+    per_step, total_q = [], 0
+    import oracle
+    db = oracle.normalize(wl.db_raw, c["k"], c["alpha"])
+    # bounded sample per step so that the whole run ends within a few minutes
+    m = 64 if c["n"] >= 1_000_000 else min(256, c["nq"])
+    for s in range(args.warmup + args.steps):
+        lo = (s * m) % max(1, c["nq"] - m)
+        t0 = time.perf_counter()
+        q = oracle.normalize(wl.q_raw[lo:lo + m], c["k"], c["alpha"])
+        oracle.search(db, q)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            per_step.append(dt)
+            total_q += m
+    t = sum(per_step)
+    value = total_q / t
+    cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": "exact 1-NN queries/s", "value": value, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": c["n"], "queries_per_step": m, "k": c["k"],
+                       "alpha": c["alpha"], "d": 128},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{m} queries per step against all {c['n']} entries (binary64 exhaustive "
+                                       f"search incl. query normalisation)"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- ours
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import paper_2606_27280_b300 as hn
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    wl, c = hn_synth.config_workload(args.workload)
+    k, alpha = c["k"], c["alpha"]
+    prefix_name = args.prefix or ("bf16" if args.workload == "c2" else "f32")
+    prefix = hn.PREFIX_BF16 if prefix_name == "bf16" else hn.PREFIX_F32
+    scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE}[args.scan]
+    stream = torch.cuda.current_stream()
+
+    # ---- index (built once, outside the timed region)
+    db_raw = torch.from_numpy(wl.db_raw).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    db = hn.normalize(db_raw, k, alpha)
+    ix = hn.Index(db, k, alpha, prefix=prefix)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del db_raw, db
+    info = ix.info()
+
+    q_host = torch.from_numpy(wl.q_raw).pin_memory()
+    q_raw = q_host.cuda()
+    nq = q_raw.shape[0]
+    q_norm = torch.empty_like(q_raw)
+    out_idx = torch.empty(nq, dtype=torch.int64, device="cuda")
+    out_sim = torch.empty(nq, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step(timing=False):
+        hn.normalize(q_raw, k, alpha, out=q_norm)
+        return ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, timing=timing)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, events per step, L2 flushed before each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            r = step(timing=True)
+            ev[i][1].record(stream)
+            phase.append(r.stats)
+        torch.cuda.synchronize()
+    barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms) / 1e3
+    t_all = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    t_max = float(t_all.item())
+    value = world * nq * args.steps / t_max
+
+    # ---- end to end through the public API: pinned host raw queries in, results out
+    res_idx_host = torch.empty(nq, dtype=torch.int64).pin_memory()
+    res_sim_host = torch.empty(nq, dtype=torch.float64).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    q_stage = torch.empty_like(q_raw)
+    torch.cuda.synchronize()
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e2e_ev[i][0].record(stream)
+        q_stage.copy_(q_host, non_blocking=True)
+        hn.normalize(q_stage, k, alpha, out=q_norm)
+        ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim)
+        res_idx_host.copy_(out_idx, non_blocking=True)
+        res_sim_host.copy_(out_sim, non_blocking=True)
+        e2e_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
+    e2e_all = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(e2e_all, op=dist.ReduceOp.MAX)
+    e2e_value = world * nq * args.steps / float(e2e_all.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (the prefix scan, one launch per phase)
+    peaks, peak_src = load_peaks()
+    st = phase[-1]
+    scan_ms = [p["ms_phase1"] for p in phase] + [p["ms_phase2"] for p in phase]
+    scan_ms_avg = sum(scan_ms) / len(scan_ms)
+    k_alg = k
+    flops = 2.0 * nq * c["n"] * k_alg
+    if st["scan"] == hn.SCAN_DENSE:
+        peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained (cuBLAS)"}
+    else:
+        # CUDA-core FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
+        smax = (clocks.summary().get("sm_max_mhz") or 2032.0)
+        peak = 148 * 128 * 2 * smax * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "prefix scan (Phase 1 and Phase 2 launches)"
+    roof["algorithmic"] = f"2*Q*N*K = {flops:.3e} flop per launch (Q={nq}, N={c['n']}, K={k_alg})"
+    roof["avg_launch_ms"] = scan_ms_avg
+
+    line = {
+        "metric": "exact 1-NN queries/s", "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prefix_name,
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: N={c['n']} entries, Q={nq} queries per step, D=128, K={k}, "
+                               f"alpha={alpha}, {c['n_centres']} centres, {prefix_name} prefix",
+                   "n": c["n"], "queries_per_step": nq, "k": k, "alpha": alpha, "prefix": prefix_name,
+                   "parallelism": f"replicated index, {world} GPU(s), independent query batches",
+                   "l2": "flushed before every timed step (256 MiB write); index 2 GiB > L2"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * 128 * 4,
+                "d2h_bytes_per_step": nq * (8 + 8)},
+        "gpu_launches": args.steps * (st["kernels"] + 1),
+        "clocks": clocks.summary(),
+        "phases_ms": {kk: statistics.median(p[kk] for p in phase) for kk in
+                      ("ms_prep", "ms_phase1", "ms_threshold", "ms_phase2", "ms_rescore", "ms_total")},
+        "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan")},
+        "survivor_frac": st["survivors"] / (nq * c["n"]),
+        "index_build_s": build_s, "index_bytes": info["device_bytes"],
+    }
+
+    # ---- GPU brute force (FP32 128-dim) on a query subset, for comparison
+    if not args.no_bruteforce:
+        sub = min(nq, 2048 if c["n"] >= 1_000_000 else nq)
+        qs = q_norm[:sub].contiguous()
+        ix.bruteforce(qs)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        rb = ix.bruteforce(qs)
+        b.record(stream)
+        torch.cuda.synchronize()
+        bf_s = a.elapsed_time(b) / 1e3
+        line["gpu_bruteforce"] = {"value": sub / bf_s, "unit": "queries/s",
+                                  "sample": f"{sub} queries x all {c['n']} entries, FP32 128-dim FMA",
+                                  "index_mismatch_vs_hn": int((rb.idx != out_idx[:sub]).sum().item())}
+        line["vs_gpu_bruteforce"] = value / (sub / bf_s)
+
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl, c)
+    elif not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, c)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -121,3 +121,24 @@ def log_uniform_sizes(seed: int, count: int, lo: int, hi: int) -> np.ndarray:
     u = _gen(seed, 7).random(count)
     s = np.rint(lo * np.exp(u * np.log(hi / lo))).astype(np.int64)
     return np.clip(s, lo, hi)
+
+
+# Workload recipes: sizes, centre counts, prefix width K, energy split alpha, seed.
+CONFIGS = {
+    # plain FP32 branch-and-bound, small enough for the oracle in seconds
+    "c0": dict(n=10_000, nq=1_000, n_centres=2_000, k=8, alpha=1 / 32, seed=0),
+    # FP32 at the recommended operating point (K = 16, alpha = 1/8, §7)
+    "c1": dict(n=1_000_000, nq=16_384, n_centres=200_000, k=16, alpha=1 / 8, seed=1),
+    # reduced-precision prefix at N = 4M
+    "c2": dict(n=4_000_000, nq=65_536, n_centres=800_000, k=16, alpha=1 / 8, seed=2),
+}
+
+
+def config_workload(name: str, n: int | None = None, nq: int | None = None) -> tuple[Workload, dict]:
+    c = dict(CONFIGS[name])
+    if n is not None:
+        c["n_centres"] = max(1, c["n_centres"] * n // c["n"])
+        c["n"] = n
+    if nq is not None:
+        c["nq"] = nq
+    return make_workload(c["n"], c["nq"], c["n_centres"], c["seed"]), c

@@ -1,0 +1,184 @@
+/*
+ * hn.h -- C ABI of the B300 (sm_103a) exact 1-NN search library for
+ * Hierarchical-Normalization (HN) descriptors.
+ *
+ * The method (§3): a 128-dim descriptor is split into a K-dim major prefix of
+ * norm sqrt(1-alpha) and a (128-K)-dim minor part of norm sqrt(alpha) (Eq. 1).
+ * Because <q_minor, x_minor> <= alpha (Cauchy-Schwarz, Eq. 3), dot_K + alpha
+ * bounds the full inner product (Eq. 2 and Eq. 3), so a scan of the major
+ * prefixes prunes every entry whose bound cannot beat the best fully scored
+ * entry, and only survivors are scored at 128 dims (Algorithm 1, §3.3).  The
+ * result equals exhaustive search (Theorem 1) and is deterministic with ties
+ * resolved by index (Theorem 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Every array argument is a DEVICE pointer on the current CUDA device,
+ *    owned by the caller, row-major and densely packed.  Float arrays need
+ *    16-byte alignment.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls that must report device-detected errors
+ *    (normalisation, invariant checks, survivor overflow) synchronise that
+ *    stream once before returning, as documented per call.
+ *  - Argument errors are detected on the host before any work is enqueued and
+ *    leave outputs untouched.
+ *  - Handles (hn_index) are owned by the library and released by their
+ *    destroy call.  A handle may be used by one host thread at a time.
+ *  - hn_last_error() returns a message for the most recent failure on the
+ *    calling host thread.
+ *  - D (the descriptor dimension) must be 128 (HardNet's width, §1, §3.1).
+ */
+#ifndef HN_H
+#define HN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hn_status {
+    HN_OK = 0,
+    HN_ERR_INVALID_ARG = 1,    /* bad size, pointer, alignment or parameter */
+    HN_ERR_NOT_NORMALIZED = 2, /* input violates the norm identities below Eq. 1 */
+    HN_ERR_ZERO_NORM = 3,      /* Eq. 1 undefined: zero major (or zero minor with alpha > 0) */
+    HN_ERR_OOM = 4,            /* device allocation failed */
+    HN_ERR_CUDA = 5,           /* a CUDA runtime call failed */
+    HN_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+    HN_ERR_OVERFLOW = 7,       /* survivor storage still too small after re-running */
+    HN_ERR_UNSUPPORTED = 8     /* valid request this build does not serve (e.g. D != 128) */
+} hn_status;
+
+/* Storage precision of the major prefix that the scan reads. */
+typedef enum hn_prefix {
+    HN_PREFIX_F32 = 0,  /* binary32 prefix, scanned with FP32 FMA */
+    HN_PREFIX_BF16 = 1  /* bfloat16 prefix, scanned on the tensor cores (FP32 accumulation) */
+} hn_prefix;
+
+/* Which prefix-scan kernel runs (Phase 1 and Phase 2 of Algorithm 1). */
+typedef enum hn_scan {
+    HN_SCAN_AUTO = 0,   /* pick by query count and prefix type */
+    HN_SCAN_STREAM = 1, /* CUDA-core FMA scan streaming the prefix (any prefix type) */
+    HN_SCAN_DENSE = 2   /* tcgen05 tensor-core scan (HN_PREFIX_BF16 only) */
+} hn_scan;
+
+typedef struct hn_index_opts {
+    int32_t prefix;       /* hn_prefix; default HN_PREFIX_F32 */
+    int32_t reserved[7];  /* must be zero */
+} hn_index_opts;
+
+typedef struct hn_search_opts {
+    int32_t scan;         /* hn_scan; default HN_SCAN_AUTO */
+    int32_t bucket_cap;   /* survivor slots per query; 0 = library default (grown on overflow) */
+    int32_t timing;       /* non-zero: time each step with CUDA events on `stream` (fills stats->ms_*) */
+    int32_t reserved[5];  /* must be zero */
+} hn_search_opts;
+
+/* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */
+typedef struct hn_search_stats {
+    int64_t n_queries;
+    int64_t n_entries;
+    int64_t survivors;      /* (query, entry) pairs passing the Phase-2 bound test */
+    int64_t max_survivors;  /* largest survivor count of a single query */
+    int64_t fp64_rescored;  /* near-tie candidates re-scored in binary64 */
+    int32_t reruns;         /* Phase-2 re-runs after survivor-slot overflow */
+    int32_t scan;           /* hn_scan that ran */
+    int32_t kernels;        /* kernel launches made by this call (all runs) */
+    int32_t reserved;
+    /* device time of each step of the last run, milliseconds (with opts->timing) */
+    float ms_prep;          /* query prefix packing and slack computation */
+    float ms_phase1;        /* Phase-1 prefix scan (best prefix score per query) */
+    float ms_threshold;     /* full score of the Phase-1 winner -> threshold */
+    float ms_phase2;        /* Phase-2 prefix scan with the bound test */
+    float ms_rescore;       /* survivor rescore, binary64 near-ties, argmax */
+    float ms_total;         /* whole search */
+} hn_search_stats;
+
+typedef struct hn_index_info {
+    int64_t n;              /* entries */
+    int32_t d, k;           /* dimension (128) and major width K */
+    double alpha;           /* energy split */
+    int32_t prefix;         /* hn_prefix */
+    int32_t k_pad;          /* stored prefix width (K rounded up for the scan) */
+    int64_t device_bytes;   /* device memory held by the index */
+    float minor_norm_max;   /* max_i |x_i,minor| of the stored values, rounded up */
+    float major_norm_max;   /* max_i |x_i,major|, rounded up */
+    float resid_norm_max;   /* max_i |x_i,major - prefix_i| (0 for HN_PREFIX_F32), rounded up */
+    float prefix_norm_max;  /* max_i |prefix_i|, rounded up */
+} hn_index_info;
+
+typedef struct hn_index hn_index;
+
+/* Library version, (major << 16) | minor. */
+int32_t hn_version(void);
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char *hn_last_error(void);
+
+/*
+ * HN normalisation (Eq. 1, §3.1), row by row:
+ *   out[:k] = sqrt(1-alpha) * in[:k] / |in[:k]|,  out[k:] = sqrt(alpha) * in[k:] / |in[k:]|
+ * Arithmetic: binary64 sums of squares in dimension order, sqrt and division
+ * correctly rounded, each output rounded once to binary32; alpha == 0 sets the
+ * minor to zero.  in, out: n x d float32 (may be the same buffer).
+ * Requirements: d == 128, 1 <= k < d, 0 <= alpha < 1, n >= 0.
+ * Errors: HN_ERR_ZERO_NORM if some row has a zero major part (or a zero minor
+ * part with alpha > 0); out is then unspecified.  Synchronises `stream`.
+ */
+hn_status hn_normalize(const float *in, float *out, int64_t n, int32_t d, int32_t k, double alpha,
+                       void *stream);
+
+/*
+ * Build a search index over n HN-normalised entries x (n x d float32, device).
+ * The index copies x (the caller may free it once this call returns) and packs
+ * the major prefixes into a separate contiguous array in the chosen precision
+ * (the Structure-of-Arrays layout of §6.1), plus per-entry minor norms.
+ * Checks the norm identities below Eq. 1 on every row:
+ *   | |x_major|^2 - (1-alpha) | <= (d+4) 2^-24 (1-alpha), same for the minor with alpha;
+ * otherwise HN_ERR_NOT_NORMALIZED.  Synchronises `stream`.
+ * Requirements: d == 128, 1 <= k <= 64 (else HN_ERR_UNSUPPORTED), 0 <= alpha < 1,
+ * 1 <= n < 2^31 - 256.  opts may be NULL (defaults).  On success *out owns
+ * device memory until hn_index_destroy.
+ */
+hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double alpha,
+                         const hn_index_opts *opts, hn_index **out, void *stream);
+
+hn_status hn_index_destroy(hn_index *index);
+
+hn_status hn_index_get_info(const hn_index *index, hn_index_info *info);
+
+/*
+ * Exact 1-NN search of nq HN-normalised queries q (nq x d float32, device):
+ *   out_idx[j] = min{ i : <q_j, x_i> = max_i' <q_j, x_i'> },  out_sim[j] = that maximum,
+ * where <.,.> is the binary64 sum of the d products in dimension order -- the
+ * result of exhaustive full-vector search (Theorem 1) with ties resolved by
+ * the lowest index (Theorem 2).  out_idx: nq int64, out_sim: nq double.
+ *
+ * Steps (Algorithm 1 on the GPU): Phase 1 scans every prefix and takes each
+ * query's best prefix score; that entry is scored in full, giving a certified
+ * threshold; Phase 2 rescans the prefixes and keeps entry i only if
+ *   prefix_score + scan_error + |q_minor| |x_minor| >= threshold;
+ * survivors are scored in FP32, and the ones within the FP32 error band of
+ * the best are scored again in binary64 to pick the exact winner.
+ * The index's scratch storage is reused and grown on demand (device
+ * allocation on first use and after an overflow).  Calls on one index must
+ * not overlap.  Checks the query norm identities (HN_ERR_NOT_NORMALIZED).
+ * Synchronises `stream` once at the end.  opts and stats may be NULL.
+ */
+hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts,
+                          int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
+
+/*
+ * Brute-force baseline (the denominator of the paper's speed-ups, §6.2): the
+ * full 128-dim FP32 inner product of every (query, entry) pair on CUDA cores,
+ * argmax by (FP32 score, lowest index).  NOT exact in the sense of
+ * hn_search_batch: it ranks by FP32 scores.  out_sim receives the FP32 score
+ * widened to double.  Does not synchronise.
+ */
+hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx,
+                        double *out_sim, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HN_H */

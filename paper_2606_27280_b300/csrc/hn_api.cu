@@ -1,0 +1,335 @@
+// C-ABI entry points of libhn (declared in include/hn.h).
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "hn_internal.cuh"
+
+namespace hn {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+hn_status fail(hn_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+hn_status cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? HN_ERR_OOM : HN_ERR_CUDA;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int next_width(int k, int lo) {
+    int w = lo;
+    while (w < k) w *= 2;
+    return w;
+}
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t count) {
+    return cudaMalloc((void **)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+static void free_ws(Workspace &ws) {
+    cudaFree(ws.bucket);
+    cudaFree(ws.count);
+    cudaFree(ws.key1);
+    cudaFree(ws.tau);
+    cudaFree(ws.qpre32);
+    cudaFree(ws.qpre16);
+    cudaFree(ws.qeps);
+    cudaFree(ws.qnorm);
+    ws.bucket = nullptr;
+    ws.count = nullptr;
+    ws.key1 = nullptr;
+    ws.tau = nullptr;
+    ws.qpre32 = nullptr;
+    ws.qpre16 = nullptr;
+    ws.qeps = nullptr;
+    ws.qnorm = nullptr;
+    ws.q_cap = 0;
+    ws.bucket_cap = 0;
+}
+
+static void free_index(Index *ix) {
+    if (!ix) return;
+    free_ws(ix->ws);
+    if (ix->ws.ev_ready)
+        for (cudaEvent_t e : ix->ws.ev) cudaEventDestroy(e);
+    cudaFree(ix->ws.status);
+    cudaFree(ix->ws.counters);
+    cudaFreeHost(ix->ws.h_status);
+    cudaFree(ix->rows);
+    cudaFree(ix->pre32);
+    cudaFree(ix->pre16);
+    cudaFree(ix->mx);
+    cudaFree(ix->dev_max);
+    delete ix;
+}
+
+// Make the per-query scratch hold nq queries and `cap` survivor slots each.
+static hn_status ensure_ws(Index &ix, int64_t nq, int32_t cap) {
+    Workspace &ws = ix.ws;
+    const int64_t nq_pad = (nq + kTileQ - 1) / kTileQ * kTileQ;
+    if (nq_pad <= ws.q_cap && cap <= ws.bucket_cap) return HN_OK;
+    const int64_t qc = std::max(nq_pad, ws.q_cap);
+    const int32_t bc = std::max(cap, ws.bucket_cap);
+    free_ws(ws);
+    HN_CUDA(dalloc(&ws.bucket, (size_t)qc * bc));
+    HN_CUDA(dalloc(&ws.count, qc));
+    HN_CUDA(dalloc(&ws.key1, qc));
+    HN_CUDA(dalloc(&ws.tau, qc));
+    HN_CUDA(dalloc(&ws.qpre32, (size_t)qc * ix.k_pad4));
+    HN_CUDA(dalloc(&ws.qpre16, (size_t)qc * ix.k_pad16));
+    HN_CUDA(dalloc(&ws.qeps, qc));
+    HN_CUDA(dalloc(&ws.qnorm, qc));
+    ws.q_cap = qc;
+    ws.bucket_cap = bc;
+    return HN_OK;
+}
+
+static hn_status check_dims(int32_t d, int32_t k, double alpha, bool for_index) {
+    if (d != kD) return fail(HN_ERR_UNSUPPORTED, "d must be 128");
+    if (k < 1 || k >= d) return fail(HN_ERR_INVALID_ARG, "need 1 <= k < d");
+    if (for_index && k > 64) return fail(HN_ERR_UNSUPPORTED, "an index needs k <= 64");
+    if (!(alpha >= 0.0 && alpha < 1.0)) return fail(HN_ERR_INVALID_ARG, "need 0 <= alpha < 1");
+    return HN_OK;
+}
+
+}  // namespace hn
+
+using namespace hn;
+
+struct hn_index {
+    Index ix;
+};
+
+extern "C" {
+
+int32_t hn_version(void) { return (0 << 16) | 1; }
+
+const char *hn_last_error(void) { return g_err.c_str(); }
+
+hn_status hn_normalize(const float *in, float *out, int64_t n, int32_t d, int32_t k, double alpha, void *stream) {
+    hn_status st = check_dims(d, k, alpha, false);
+    if (st != HN_OK) return st;
+    if (n < 0) return fail(HN_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return HN_OK;
+    if (!in || !out || !aligned16(in) || !aligned16(out)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *dstat = nullptr;
+    HN_CUDA(cudaMallocAsync((void **)&dstat, 8 * sizeof(int32_t), s));
+    int32_t h[8];
+    cudaError_t e = cudaMemsetAsync(dstat, 0, 8 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_normalize(in, out, n, k, alpha, dstat, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dstat, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dstat, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "hn_normalize");
+    if (h[ST_NOT_NORMALIZED]) return fail(HN_ERR_INVALID_ARG, "non-finite input row");
+    if (h[ST_ZERO_NORM]) return fail(HN_ERR_ZERO_NORM, "zero major (or minor) norm");
+    return HN_OK;
+}
+
+hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double alpha, const hn_index_opts *opts,
+                         hn_index **out, void *stream) {
+    if (!out) return fail(HN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    hn_status st = check_dims(d, k, alpha, true);
+    if (st != HN_OK) return st;
+    if (n < 1 || n > 0x7FFFFFFFll - kTileE) return fail(HN_ERR_INVALID_ARG, "need 1 <= n < 2^31 - 256");
+    if (!x || !aligned16(x)) return fail(HN_ERR_INVALID_ARG, "null or unaligned x");
+    hn_index_opts o{};
+    if (opts) o = *opts;
+    if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16) return fail(HN_ERR_INVALID_ARG, "bad prefix type");
+    for (int i = 0; i < 7; ++i)
+        if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    cudaStream_t s = (cudaStream_t)stream;
+    hn_index *h = new hn_index();
+    Index &ix = h->ix;
+    ix.n = n;
+    ix.k = k;
+    ix.alpha = alpha;
+    ix.prefix = o.prefix;
+    ix.k_pad16 = next_width(k, 16);
+    ix.k_pad4 = ix.prefix == HN_PREFIX_BF16 ? ix.k_pad16 : next_width(k, 8);
+    ix.n_tiles = (n + kTileE - 1) / kTileE;
+    const int64_t n_pad = ix.n_tiles * kTileE;
+    cudaError_t e = cudaSuccess;
+#define TRY(call)                       \
+    do {                                \
+        e = (call);                     \
+        if (e != cudaSuccess) {         \
+            hn_index_destroy(h);        \
+            return cuda_fail(e, #call); \
+        }                               \
+    } while (0)
+    TRY(dalloc(&ix.rows, (size_t)n_pad * kD));
+    TRY(cudaMemsetAsync(ix.rows + n * kD, 0, (size_t)(n_pad - n) * kD * sizeof(float), s));
+    if (ix.prefix == HN_PREFIX_F32) {
+        TRY(dalloc(&ix.pre32, (size_t)n_pad * ix.k_pad4));
+    } else {
+        TRY(dalloc(&ix.pre16, (size_t)n_pad * ix.k_pad16));
+    }
+    TRY(dalloc(&ix.mx, n));
+    TRY(dalloc(&ix.dev_max, 8));
+    TRY(dalloc(&ix.ws.status, 8));
+    TRY(dalloc(&ix.ws.counters, 8));
+    TRY(cudaMallocHost((void **)&ix.ws.h_status, 8 * sizeof(int32_t) + 8 * sizeof(long long)));
+    TRY(cudaMemsetAsync(ix.dev_max, 0, 8 * sizeof(float), s));
+    TRY(cudaMemsetAsync(ix.ws.status, 0, 8 * sizeof(int32_t), s));
+    TRY(cudaMemsetAsync(ix.ws.status + ST_BAD_ROW, 0x7F, sizeof(int32_t), s));
+    TRY(launch_pack(ix, x, s));
+    int32_t hs[8];
+    TRY(cudaMemcpyAsync(hs, ix.ws.status, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    TRY(cudaMemcpyAsync(ix.host_max, ix.dev_max, sizeof(ix.host_max), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+#undef TRY
+    ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
+               (ix.pre16 ? n_pad * ix.k_pad16 * 2 : 0) + n * 4;
+    if (hs[ST_NOT_NORMALIZED]) {
+        const int row = hs[ST_BAD_ROW];
+        hn_index_destroy(h);
+        return fail(HN_ERR_NOT_NORMALIZED, "entry " + std::to_string(row) + " violates the HN norm identities");
+    }
+    *out = h;
+    return HN_OK;
+}
+
+hn_status hn_index_destroy(hn_index *index) {
+    if (!index) return HN_OK;
+    Index *ix = new Index(std::move(index->ix));
+    delete index;
+    free_index(ix);
+    return HN_OK;
+}
+
+hn_status hn_index_get_info(const hn_index *index, hn_index_info *info) {
+    if (!index || !info) return fail(HN_ERR_INVALID_ARG, "NULL argument");
+    const Index &ix = index->ix;
+    info->n = ix.n;
+    info->d = ix.d;
+    info->k = ix.k;
+    info->alpha = ix.alpha;
+    info->prefix = ix.prefix;
+    info->k_pad = ix.prefix == HN_PREFIX_BF16 ? ix.k_pad16 : ix.k_pad4;
+    info->device_bytes = ix.bytes;
+    info->minor_norm_max = ix.host_max[0];
+    info->major_norm_max = ix.host_max[1];
+    info->resid_norm_max = ix.host_max[2];
+    info->prefix_norm_max = ix.host_max[3];
+    return HN_OK;
+}
+
+// One run of the search pipeline (Algorithm 1 on the GPU); 5 kernel launches.
+// With `timing`, events ev[0..5] bracket the steps on stream s.
+static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, int64_t *out_idx, double *out_sim,
+                            bool timing, cudaStream_t s) {
+    Workspace &ws = ix.ws;
+    auto mark = [&](int i) { return timing ? cudaEventRecord(ws.ev[i], s) : cudaSuccess; };
+    HN_CUDA(cudaMemsetAsync(ws.key1, 0, sizeof(unsigned long long) * nq, s));
+    HN_CUDA(mark(0));
+    HN_CUDA(launch_query_prep(ix, q, nq, s));
+    HN_CUDA(mark(1));
+    HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s) : launch_stream_scan(ix, nq, 1, s));
+    HN_CUDA(mark(2));
+    HN_CUDA(launch_seed_threshold(ix, q, nq, s));
+    HN_CUDA(mark(3));
+    HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
+    HN_CUDA(mark(4));
+    HN_CUDA(launch_rescore(ix, q, nq, out_idx, out_sim, s));
+    HN_CUDA(mark(5));
+    return HN_OK;
+}
+
+hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts, int64_t *out_idx,
+                          double *out_sim, hn_search_stats *stats, void *stream) {
+    if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
+    Index &ix = index->ix;
+    if (nq < 0 || nq > (int64_t)1 << 30) return fail(HN_ERR_INVALID_ARG, "need 0 <= nq <= 2^30");
+    hn_search_opts o{};
+    if (opts) o = *opts;
+    for (int i = 0; i < 5; ++i)
+        if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.bucket_cap < 0) return fail(HN_ERR_INVALID_ARG, "bucket_cap < 0");
+    int scan = o.scan;
+    if (scan == HN_SCAN_AUTO) scan = (ix.prefix == HN_PREFIX_BF16 && nq >= 1024 && dense_scan_supported(ix)) ? HN_SCAN_DENSE : HN_SCAN_STREAM;
+    if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
+    if (scan == HN_SCAN_DENSE && !dense_scan_supported(ix))
+        return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 prefix index");
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->n_queries = nq;
+        stats->n_entries = ix.n;
+        stats->scan = scan;
+    }
+    if (nq == 0) return HN_OK;
+    if (!q || !out_idx || !out_sim || !aligned16(q)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t cap = o.bucket_cap;
+    if (cap == 0) cap = std::max<int32_t>(std::max<int32_t>(256, ix.ws.bucket_cap), ix.ws.last_max + ix.ws.last_max / 4);
+    Workspace &ws = ix.ws;
+    const bool timing = o.timing != 0;
+    if (timing && !ws.ev_ready) {
+        for (cudaEvent_t &e : ws.ev) HN_CUDA(cudaEventCreate(&e));
+        ws.ev_ready = true;
+    }
+    int32_t reruns = 0, kernels = 0;
+    for (;;) {
+        hn_status st = ensure_ws(ix, nq, cap);
+        if (st != HN_OK) return st;
+        HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
+        HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
+        st = run_search(ix, q, nq, scan, out_idx, out_sim, timing, s);
+        if (st != HN_OK) return st;
+        kernels += 5;
+        HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+        HN_CUDA(cudaStreamSynchronize(s));
+        const long long *hc = reinterpret_cast<const long long *>(ws.h_status + 8);
+        ws.last_max = (int32_t)std::min<long long>(hc[CT_MAXSURV], 1 << 30);
+        if (ws.h_status[ST_NOT_NORMALIZED]) return fail(HN_ERR_NOT_NORMALIZED, "a query violates the HN norm identities");
+        if (ws.h_status[ST_TIMEOUT]) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
+        if (!ws.h_status[ST_OVERFLOW]) {
+            if (stats) {
+                stats->survivors = hc[CT_SURVIVORS];
+                stats->max_survivors = hc[CT_MAXSURV];
+                stats->fp64_rescored = hc[CT_FP64];
+                stats->reruns = reruns;
+                stats->kernels = kernels;
+                if (timing) {
+                    float *ms[5] = {&stats->ms_prep, &stats->ms_phase1, &stats->ms_threshold, &stats->ms_phase2,
+                                    &stats->ms_rescore};
+                    for (int i = 0; i < 5; ++i) HN_CUDA(cudaEventElapsedTime(ms[i], ws.ev[i], ws.ev[i + 1]));
+                    HN_CUDA(cudaEventElapsedTime(&stats->ms_total, ws.ev[0], ws.ev[5]));
+                }
+            }
+            return HN_OK;
+        }
+        // survivors did not fit: grow the slots to the largest count seen and run again
+        if (reruns >= 2 || hc[CT_MAXSURV] >= (1 << 30))
+            return fail(HN_ERR_OVERFLOW, "survivor storage overflow after re-runs");
+        const int64_t want = hc[CT_MAXSURV] + hc[CT_MAXSURV] / 8 + 32;
+        if ((int64_t)nq * want * 4 > ((int64_t)96 << 30)) return fail(HN_ERR_OVERFLOW, "survivor storage would exceed 96 GiB");
+        cap = (int32_t)want;
+        ++reruns;
+    }
+}
+
+hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
+                        void *stream) {
+    if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
+    if (nq < 0 || nq > (int64_t)1 << 30) return fail(HN_ERR_INVALID_ARG, "need 0 <= nq <= 2^30");
+    if (nq == 0) return HN_OK;
+    if (!q || !out_idx || !out_sim || !aligned16(q)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    Index &ix = const_cast<hn_index *>(index)->ix;
+    hn_status st = ensure_ws(ix, nq, std::max<int32_t>(ix.ws.bucket_cap, 1));
+    if (st != HN_OK) return st;
+    HN_CUDA(launch_bruteforce(ix, q, nq, out_idx, out_sim, (cudaStream_t)stream));
+    return HN_OK;
+}
+
+}  // extern "C"

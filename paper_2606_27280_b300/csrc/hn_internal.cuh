@@ -1,0 +1,125 @@
+// Internal declarations shared by the CUDA translation units of libhn.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "hn.h"
+
+namespace hn {
+
+constexpr int kD = 128;           // descriptor width (HardNet, §3.1)
+constexpr int kTileE = 256;       // entries per scan tile (dense kernel N dimension)
+constexpr int kTileQ = 128;       // queries per dense tile (UMMA M)
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+hn_status fail(hn_status st, const std::string &msg);
+hn_status cuda_fail(cudaError_t e, const char *what);
+
+#define HN_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::hn::cuda_fail(e_, #call);      \
+    } while (0)
+
+__host__ __device__ inline int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ inline int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------- keys
+// Order-preserving map of a binary32 value onto uint32: a < b  <=>  key(a) < key(b)
+// for all non-NaN a, b (with -0 < +0).  Used for atomicMax across CTAs.
+__host__ __device__ inline uint32_t f2key(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float key2f(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+// (score, index) packed so that a larger key means a larger score, then a lower index.
+__host__ __device__ inline unsigned long long pack_best(float s, uint32_t idx) {
+    return ((unsigned long long)f2key(s) << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
+}
+__host__ __device__ inline uint32_t best_idx(unsigned long long k) {
+    return 0xFFFFFFFFu - (uint32_t)(k & 0xFFFFFFFFull);
+}
+__host__ __device__ inline float best_score(unsigned long long k) { return key2f((uint32_t)(k >> 32)); }
+
+// ---------------------------------------------------------------- index
+struct QueryPrep;  // per-search query-side arrays (hn_search.cu)
+
+struct Workspace {
+    // per-query scratch, sized for `q_cap` queries and `bucket_cap` survivors each
+    int64_t q_cap = 0;
+    int32_t bucket_cap = 0;
+    int32_t *bucket = nullptr;         // [q_cap][bucket_cap] survivor entry ids
+    int32_t *count = nullptr;          // [q_cap] survivor counts (may exceed bucket_cap)
+    unsigned long long *key1 = nullptr;// [q_cap] Phase-1 best (score, index) key
+    float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
+    float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
+    __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles
+    float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
+    float *qnorm = nullptr;            // [q_cap] |q| rounded up
+    int32_t *status = nullptr;         // [8] device status words
+    long long *counters = nullptr;     // [8] device counters for stats
+    int32_t *h_status = nullptr;       // pinned host mirror of status + counters
+    int32_t last_max = 0;              // largest survivor count seen (sizing hint)
+    cudaEvent_t ev[8] = {};            // step timers (created on first timed search)
+    bool ev_ready = false;
+};
+
+struct Index {
+    int64_t n = 0;
+    int32_t d = kD, k = 0;
+    double alpha = 0;
+    int32_t prefix = HN_PREFIX_F32;
+    int32_t k_pad4 = 0;    // FP32 prefix row width
+    int32_t k_pad16 = 0;   // BF16 prefix width (multiple of 16, UMMA K step)
+    int64_t n_tiles = 0;   // ceil(n / kTileE)
+    float *rows = nullptr;           // [n][128] FP32 master copy (full rescore)
+    float *pre32 = nullptr;          // [n][k_pad4] FP32 prefix (HN_PREFIX_F32)
+    __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
+    float *mx = nullptr;             // [n] |x_minor| rounded up
+    float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
+    float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
+    int64_t bytes = 0;
+    Workspace ws;
+};
+
+// status word slots
+enum { ST_NOT_NORMALIZED = 0, ST_ZERO_NORM = 1, ST_OVERFLOW = 2, ST_TIMEOUT = 3, ST_BAD_ROW = 4 };
+// counter slots
+enum { CT_SURVIVORS = 0, CT_MAXSURV = 1, CT_FP64 = 2 };
+
+// byte offset of (entry e, prefix column c) in the BF16 UMMA-ordered prefix:
+// groups of 8 entries; inside a group, 16-byte core-matrix rows per 8 columns.
+__host__ __device__ inline int64_t pre16_offset(int64_t e, int c, int k_pad16) {
+    const int64_t g = e >> 3;
+    const int r = (int)(e & 7);
+    return g * (int64_t)k_pad16 * 16 + (int64_t)(c >> 3) * 128 + r * 16 + (c & 7) * 2;
+}
+
+// launches (defined in the .cu files)
+cudaError_t launch_normalize(const float *in, float *out, int64_t n, int k, double alpha,
+                             int32_t *status, cudaStream_t s);
+cudaError_t launch_check_hn(const float *x, int64_t n, int k, double alpha, int32_t *status,
+                            cudaStream_t s);
+cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t s);
+cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t s);
+cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
+cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, cudaStream_t s);
+cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
+                           double *out_sim, cudaStream_t s);
+cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
+                              double *out_sim, cudaStream_t s);
+bool dense_scan_supported(const Index &ix);
+
+}  // namespace hn

@@ -1,0 +1,256 @@
+// HN normalisation (Eq. 1), index packing (§6.1 SoA layout) and query preparation.
+#include <math.h>
+
+#include "hn_internal.cuh"
+
+namespace hn {
+
+// ------------------------------------------------------------------ Eq. 1
+// One thread per row, so that each sum of squares runs in dimension order
+// exactly as defined: binary64, products of binary32 values are exact, then
+// sqrt and division correctly rounded, each output rounded once to binary32.
+// Rows are staged through shared memory (stride 129 words: conflict-free).
+constexpr int kNormRows = 64;
+
+__global__ void __launch_bounds__(kNormRows) k_normalize(const float *__restrict__ in,
+                                                         float *__restrict__ out, int64_t n, int k,
+                                                         double alpha, int32_t *status) {
+    __shared__ float s[kNormRows * (kD + 1)];
+    const int64_t r0 = (int64_t)blockIdx.x * kNormRows;
+    const int rows = (int)min64(kNormRows, n - r0);
+    const float *src = in + r0 * kD;
+    for (int i = threadIdx.x; i < rows * kD; i += blockDim.x) s[(i / kD) * (kD + 1) + (i % kD)] = src[i];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < rows) {
+        float *f = s + t * (kD + 1);
+        double s_maj = 0.0, s_min = 0.0;
+        for (int c = 0; c < k; ++c) s_maj = fma((double)f[c], (double)f[c], s_maj);
+        for (int c = k; c < kD; ++c) s_min = fma((double)f[c], (double)f[c], s_min);
+        const bool bad = !isfinite(s_maj) || !isfinite(s_min);
+        const bool zero = s_maj == 0.0 || (alpha > 0.0 && s_min == 0.0);
+        if (bad || zero) {
+            atomicExch(status + (bad ? ST_NOT_NORMALIZED : ST_ZERO_NORM), 1);
+        } else {
+            const double c_maj = sqrt(1.0 - alpha) / sqrt(s_maj);
+            for (int c = 0; c < k; ++c) f[c] = __double2float_rn((double)f[c] * c_maj);
+            if (alpha == 0.0) {
+                for (int c = k; c < kD; ++c) f[c] = 0.0f;
+            } else {
+                const double c_min = sqrt(alpha) / sqrt(s_min);
+                for (int c = k; c < kD; ++c) f[c] = __double2float_rn((double)f[c] * c_min);
+            }
+        }
+    }
+    __syncthreads();
+    float *dst = out + r0 * kD;
+    for (int i = threadIdx.x; i < rows * kD; i += blockDim.x) dst[i] = s[(i / kD) * (kD + 1) + (i % kD)];
+}
+
+cudaError_t launch_normalize(const float *in, float *out, int64_t n, int k, double alpha,
+                             int32_t *status, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = (n + kNormRows - 1) / kNormRows;
+    k_normalize<<<(unsigned)blocks, kNormRows, 0, st>>>(in, out, n, k, alpha, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ helpers
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// An upper bound, in binary32, on sqrt(s) where s is a binary64 sum of <= 128
+// non-negative terms carrying relative error <= 128 * 2^-53 < 2^-45.
+__device__ inline float sqrt_up(double s) {
+    return __double2float_ru(__dsqrt_ru(s * (1.0 + 0x1p-44)));
+}
+// Relative tolerance of the norm identities for binary32-stored coordinates.
+__device__ inline bool hn_ok(double maj2, double min2, double alpha) {
+    const double tol = (kD + 4) * 0x1p-24;
+    return fabs(maj2 - (1.0 - alpha)) <= tol * (1.0 - alpha) && fabs(min2 - alpha) <= tol * alpha;
+}
+
+__device__ inline float4 bf16_round4(float4 v) {
+    return make_float4(__bfloat162float(__float2bfloat16_rn(v.x)), __bfloat162float(__float2bfloat16_rn(v.y)),
+                       __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
+}
+
+// ------------------------------------------------------------------ index build
+// One warp per entry (grid-stride).  Lane l owns dimensions 4l..4l+3.  Writes
+// the FP32 master row, the prefix in the index precision, |x_minor| rounded up,
+// and checks the norm identities.  Block maxima of the norms go to dev_max via
+// one atomicMax per block (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64_t n, int k, double alpha,
+                                              int prefix, int k_pad4, int k_pad16, int64_t n_pad,
+                                              float *__restrict__ rows, float *__restrict__ pre32,
+                                              __nv_bfloat16 *__restrict__ pre16, float *__restrict__ mx,
+                                              float *dev_max, int32_t *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float m_min = 0.f, m_maj = 0.f, m_res = 0.f, m_pre = 0.f, m_full = 0.f;
+    for (int64_t e = warp; e < n_pad; e += nwarps) {
+        const int c0 = lane * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < n) v = reinterpret_cast<const float4 *>(x + e * kD)[lane];
+        if (e < n) reinterpret_cast<float4 *>(rows + e * kD)[lane] = v;
+        float vv[4] = {v.x, v.y, v.z, v.w};
+        double maj2 = 0, min2 = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double d = vv[j];
+            if (c0 + j < k) maj2 += d * d; else min2 += d * d;
+        }
+        // prefix in storage precision (zero beyond k)
+        float pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pv[j] = (c0 + j < k) ? vv[j] : 0.f;
+        float4 p4 = make_float4(pv[0], pv[1], pv[2], pv[3]);
+        if (prefix == HN_PREFIX_BF16) p4 = bf16_round4(p4);
+        const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+        double res2 = 0, pre2 = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double r = (double)pv[j] - (double)pp[j];  // exact: both binary32
+            res2 += r * r;
+            pre2 += (double)pp[j] * (double)pp[j];
+        }
+        if (prefix == HN_PREFIX_F32 && c0 < k_pad4)
+            reinterpret_cast<float4 *>(pre32 + e * k_pad4)[lane] = p4;
+        if (prefix == HN_PREFIX_BF16 && c0 < k_pad16) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(p4.x, p4.y), hi = __floats2bfloat162_rn(p4.z, p4.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16) + pre16_offset(e, c0, k_pad16)) = pk;
+        }
+        maj2 = warp_sum(maj2);
+        min2 = warp_sum(min2);
+        res2 = warp_sum(res2);
+        pre2 = warp_sum(pre2);
+        if (e < n) {
+            const float umin = sqrt_up(min2), umaj = sqrt_up(maj2), ures = sqrt_up(res2);
+            const float upre = sqrt_up(pre2), ufull = sqrt_up(maj2 + min2);
+            if (lane == 0) {
+                mx[e] = umin;
+                if (!hn_ok(maj2, min2, alpha)) {
+                    atomicExch(status + ST_NOT_NORMALIZED, 1);
+                    atomicMin(status + ST_BAD_ROW, (int32_t)min64(e, 0x7FFFFFFF));
+                }
+            }
+            m_min = fmaxf(m_min, umin);
+            m_maj = fmaxf(m_maj, umaj);
+            m_res = fmaxf(m_res, ures);
+            m_pre = fmaxf(m_pre, upre);
+            m_full = fmaxf(m_full, ufull);
+        }
+    }
+    __shared__ float red[5][8];
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) { red[0][w] = m_min; red[1][w] = m_maj; red[2][w] = m_res; red[3][w] = m_pre; red[4][w] = m_full; }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        float m = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[threadIdx.x][i]);
+        atomicMax(reinterpret_cast<int *>(dev_max) + threadIdx.x, __float_as_int(m));
+    }
+}
+
+cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
+    const int64_t n_pad = ix.n_tiles * kTileE;
+    int64_t blocks = (n_pad * 32 + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    k_pack<<<(unsigned)blocks, 256, 0, st>>>(x, ix.n, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16, n_pad,
+                                             ix.rows, ix.pre32, ix.pre16, ix.mx, ix.dev_max, ix.ws.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_hn(const float *, int64_t, int, double, int32_t *, cudaStream_t) {
+    return cudaSuccess;  // the check is fused into k_pack and k_query_prep
+}
+
+// ------------------------------------------------------------------ queries
+// One warp per query.  Produces the query prefix in the scan precision, the
+// UMMA A-tile copy (BF16), |q| rounded up, and the Phase-2 slack
+//   E_q >= scan error + |q_minor| * max_i |x_i,minor| + binary64 rounding of the oracle,
+// rounded up to binary32.  Scan error:
+//   FP32 prefix: gamma_kp * |q_major| * max|x_major|  (recursive FMA summation, Higham Thm 3.1)
+//   BF16 prefix: |q_major| * max r(x) + r(q) * max|x^| + gamma' * |q^| * max|x^|,
+//     with r(.) the residual norm of the BF16 rounding and gamma' = (kp+2) 2^-20,
+//     a deliberately loose accumulation term for the tensor cores' FP32 adder.
+__global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q, int64_t nq, int64_t nq_pad,
+                                                    int k, double alpha, int prefix, int k_pad4, int k_pad16,
+                                                    const float *__restrict__ dev_max, float *__restrict__ qpre32,
+                                                    __nv_bfloat16 *__restrict__ qpre16, float *__restrict__ qeps,
+                                                    float *__restrict__ qnorm, int32_t *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq_pad) return;
+    const int c0 = lane * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < nq) v = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+    double maj2 = 0, min2 = 0, res2 = 0, pre2 = 0;
+    float pv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const double d = vv[t];
+        if (c0 + t < k) maj2 += d * d; else min2 += d * d;
+        pv[t] = (c0 + t < k) ? vv[t] : 0.f;
+    }
+    float4 p4 = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    if (prefix == HN_PREFIX_BF16) p4 = bf16_round4(p4);
+    const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const double r = (double)pv[t] - (double)pp[t];
+        res2 += r * r;
+        pre2 += (double)pp[t] * (double)pp[t];
+    }
+    if (c0 < k_pad4) reinterpret_cast<float4 *>(qpre32 + j * k_pad4)[lane] = p4;
+    if (prefix == HN_PREFIX_BF16 && c0 < k_pad16) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(p4.x, p4.y), hi = __floats2bfloat162_rn(p4.z, p4.w);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t *>(&lo);
+        pk.y = *reinterpret_cast<uint32_t *>(&hi);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(qpre16) + pre16_offset(j, c0, k_pad16)) = pk;
+    }
+    maj2 = warp_sum(maj2);
+    min2 = warp_sum(min2);
+    res2 = warp_sum(res2);
+    pre2 = warp_sum(pre2);
+    if (lane != 0 || j >= nq) return;
+    if (!hn_ok(maj2, min2, alpha)) atomicExch(status + ST_NOT_NORMALIZED, 1);
+    const double qmaj = sqrt_up(maj2), qmin = sqrt_up(min2), qres = sqrt_up(res2), qhat = sqrt_up(pre2);
+    const double xmin = dev_max[0], xmaj = dev_max[1], xres = dev_max[2], xhat = dev_max[3];
+    double scan;
+    if (prefix == HN_PREFIX_F32) {
+        const double g = k_pad4 * 0x1p-24 / (1.0 - k_pad4 * 0x1p-24);
+        scan = g * qmaj * xmaj;
+    } else {
+        const double g = (k_pad16 + 2) * 0x1p-20;
+        scan = qmaj * xres + qres * xhat + g * qhat * xhat;
+    }
+    // the oracle's own binary64 rounding: <= 128 * 2^-53 * |q| |x| < 1e-13 for unit vectors
+    const double e = (scan + qmin * xmin) * (1.0 + 1e-9) + 1e-12;
+    qeps[j] = __double2float_ru(e);
+    qnorm[j] = __double2float_ru(sqrt_up(maj2 + min2));
+}
+
+cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t st) {
+    const int64_t nq_pad = (nq + kTileQ - 1) / kTileQ * kTileQ;
+    const int64_t blocks = (nq_pad * 32 + 255) / 256;
+    k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
+                                                   ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qeps,
+                                                   ix.ws.qnorm, ix.ws.status);
+    return cudaGetLastError();
+}
+
+}  // namespace hn

@@ -1,0 +1,349 @@
+// Streaming prefix scan (Phase 1 / Phase 2 of Algorithm 1 on CUDA cores), the
+// Phase-1 threshold, the survivor rescore with binary64 near-tie resolution,
+// and the FP32 brute-force baseline.
+#include <math.h>
+
+#include "hn_internal.cuh"
+
+namespace hn {
+
+// ------------------------------------------------------------------ stream scan
+// CTA = 64 queries x a contiguous range of 256-entry tiles.  Thread (w, lane)
+// owns queries 8w..8w+7 and tile entries lane + 32j (j < 8), so every thread
+// holds an 8x8 block of prefix scores in registers.  Each score is the FMA
+// chain acc = fma(q_c, x_c, acc), c = 0..KT-1 from acc = 0 (zero padding adds
+// exact zeros), whose error is bounded by gamma_KT * sum |q_c x_c|.
+//   PHASE 1: per-query best (score, lowest index) -> atomicMax on key1[q].
+//   PHASE 2: every entry with score >= tau[q] is appended to q's survivor slots.
+// The same kernel with KT = 128 over the full rows is the brute-force baseline.
+constexpr int kSQ = 64;     // queries per CTA
+constexpr int kSE = 256;    // entries per tile
+constexpr int kKC = 16;     // prefix columns staged per step
+
+template <int KT, bool BF16, int PHASE>
+__global__ void __launch_bounds__(256, 2)
+k_stream_scan(const float *__restrict__ e32, const __nv_bfloat16 *__restrict__ e16, int64_t n, int64_t n_tiles,
+              int64_t tiles_per_cta, const float *__restrict__ qpre, int64_t nq, const float *__restrict__ tau,
+              unsigned long long *__restrict__ key1, int32_t *__restrict__ bucket, int32_t *__restrict__ count,
+              int cap) {
+    constexpr int KC = KT < kKC ? KT : kKC;
+    __shared__ float sq[KT][kSQ];
+    __shared__ float se[KC][kSE];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * kSQ;
+    for (int i = tid; i < kSQ * KT; i += 256) {
+        const int qq = i / KT, c = i % KT;
+        sq[c][qq] = (q0 + qq < nq) ? qpre[(q0 + qq) * KT + c] : 0.f;
+    }
+    float thr[8], best[8];
+    uint32_t bidx[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t qg = q0 + w * 8 + i;
+        thr[i] = (PHASE == 2 && qg < nq) ? tau[qg] : INFINITY;
+        best[i] = -INFINITY;
+        bidx[i] = 0xFFFFFFFFu;
+    }
+    const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_cta;
+    const int64_t t_end = min64(n_tiles, t_begin + tiles_per_cta);
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        const int64_t e = t * kSE + tid;  // entry staged by this thread
+#pragma unroll 1
+        for (int c0 = 0; c0 < KT; c0 += KC) {
+            __syncthreads();
+            if (BF16) {
+#pragma unroll
+                for (int c = 0; c < KC; c += 8) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(
+                        reinterpret_cast<const char *>(e16) + pre16_offset(e, c0 + c, KT));
+                    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 f = __bfloat1622float2(h[u]);
+                        se[c + 2 * u][tid] = f.x;
+                        se[c + 2 * u + 1][tid] = f.y;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < KC; c += 4) {
+                    const float4 f = *reinterpret_cast<const float4 *>(e32 + e * KT + c0 + c);
+                    se[c][tid] = f.x;
+                    se[c + 1][tid] = f.y;
+                    se[c + 2][tid] = f.z;
+                    se[c + 3][tid] = f.w;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                float a[8], b[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = sq[c0 + c][w * 8 + i];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) b[j] = se[c][lane + 32 * j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+        }
+        const int64_t ebase = t * kSE + lane;
+        const bool tail = (t + 1) * kSE > n;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float m = acc[i][0];
+#pragma unroll
+            for (int j = 1; j < 8; ++j) m = fmaxf(m, acc[i][j]);
+            if (PHASE == 1) {
+                if (m > best[i] || tail) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t ei = ebase + 32 * j;
+                        if (ei < n && acc[i][j] > best[i]) { best[i] = acc[i][j]; bidx[i] = (uint32_t)ei; }
+                    }
+                }
+            } else {
+                if (m >= thr[i]) {
+                    const int64_t qg = q0 + w * 8 + i;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int64_t ei = ebase + 32 * j;
+                        if (ei < n && acc[i][j] >= thr[i]) {
+                            const int slot = atomicAdd(count + qg, 1);
+                            if (slot < cap) bucket[qg * cap + slot] = (int32_t)ei;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (PHASE == 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            unsigned long long kbest = bidx[i] == 0xFFFFFFFFu ? 0ull : pack_best(best[i], bidx[i]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, kbest, o);
+                kbest = other > kbest ? other : kbest;
+            }
+            const int64_t qg = q0 + w * 8 + i;
+            if (lane == 0 && qg < nq && kbest) atomicMax(key1 + qg, kbest);
+        }
+    }
+}
+
+template <int KT, bool BF16>
+static cudaError_t stream_scan_kt(const float *e32, const __nv_bfloat16 *e16, int64_t n, int64_t n_tiles,
+                                  const float *qpre, int64_t nq, int phase, const Workspace &ws, cudaStream_t st) {
+    const int64_t qt = (nq + kSQ - 1) / kSQ;
+    // enough CTAs for ~8 per SM; consecutive CTAs share an entry range (L2 reuse)
+    int64_t splits = (148 * 8 + qt - 1) / qt;
+    splits = max64(1, min64(splits, n_tiles));
+    const int64_t tpc = (n_tiles + splits - 1) / splits;
+    splits = (n_tiles + tpc - 1) / tpc;
+    if (qt > 0x7FFFFFFF || splits > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)qt, (unsigned)splits);
+    if (phase == 1)
+        k_stream_scan<KT, BF16, 1><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
+                                                         ws.bucket, ws.count, ws.bucket_cap);
+    else
+        k_stream_scan<KT, BF16, 2><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
+                                                         ws.bucket, ws.count, ws.bucket_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
+    const Workspace &ws = ix.ws;
+    if (ix.prefix == HN_PREFIX_BF16) {
+        switch (ix.k_pad16) {
+            case 16: return stream_scan_kt<16, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 32: return stream_scan_kt<32, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 64: return stream_scan_kt<64, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+        }
+    } else {
+        switch (ix.k_pad4) {
+            case 8: return stream_scan_kt<8, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 16: return stream_scan_kt<16, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 32: return stream_scan_kt<32, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 64: return stream_scan_kt<64, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ threshold
+// Algorithm 1, step 2: the Phase-1 winner b is scored in full,
+//   T_q = <q, x_b>  (binary64, dimension order: the oracle's own value),
+// a certified lower bound on the final maximum.  The Phase-2 prefix threshold is
+//   tau_q = round_down(T_q - E_q),
+// so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  entry cannot win.
+__global__ void k_seed_threshold(const float *__restrict__ rows, const float *__restrict__ q, int64_t nq,
+                                 const unsigned long long *__restrict__ key1, const float *__restrict__ qeps,
+                                 float *__restrict__ tau, int32_t *__restrict__ count) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    count[j] = 0;
+    const unsigned long long kb = key1[j];
+    if (kb == 0ull) { tau[j] = -INFINITY; return; }   // no candidate: keep everything
+    const uint32_t b = best_idx(kb);
+    const float *x = rows + (int64_t)b * kD;
+    const float *qq = q + j * kD;
+    double s = 0.0;
+    for (int c = 0; c < kD; ++c) s = fma((double)qq[c], (double)x[c], s);
+    tau[j] = __double2float_rd(__dsub_rd(s, (double)qeps[j]));
+}
+
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, cudaStream_t st) {
+    k_seed_threshold<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(ix.rows, q, nq, ix.ws.key1, ix.ws.qeps,
+                                                                   ix.ws.tau, ix.ws.count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ rescore
+// One warp per query.  For every survivor i: FP32 128-dim score (lane l owns
+// dims 4l..4l+3, then a butterfly sum), error <= eps_r = gamma_128 |q| max|x|
+// (any summation order of 128 terms).  The winner w.r.t. the oracle's binary64
+// value must lie in the band  fp32_i >= best_fp32 - 2 eps_r;  band members are
+// re-scored in binary64 in dimension order (bit-identical to the oracle) and
+// the (score desc, index asc) maximum is the answer.  The band is kept in
+// lane-distributed registers (<= 32 members); a larger band falls back to
+// binary64 for every survivor of that query.
+__device__ inline double dot64_seq(const float *__restrict__ a, const float *__restrict__ b) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < kD; ++c) s = fma((double)a[c], (double)b[c], s);
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows, const float *__restrict__ q,
+                                                 int64_t nq, const int32_t *__restrict__ bucket,
+                                                 const int32_t *__restrict__ count, int cap,
+                                                 const float *__restrict__ qnorm, float xnorm_max,
+                                                 int64_t *__restrict__ out_idx, double *__restrict__ out_sim,
+                                                 int32_t *__restrict__ status, long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    const int cnt = count[j];
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SURVIVORS), (unsigned long long)cnt);
+        atomicMax(reinterpret_cast<unsigned long long *>(counters + CT_MAXSURV), (unsigned long long)cnt);
+    }
+    if (cnt > cap) {  // survivors were dropped: the host re-runs with more slots
+        if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
+        return;
+    }
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float eps = __fmul_ru(__fmul_ru(qnorm[j], xnorm_max), 128 * 0x1p-24 / (1 - 128 * 0x1p-24) + 1e-12f);
+    const float band = __fmul_ru(2.f, eps);
+    const int32_t *bk = bucket + j * (int64_t)cap;
+    float best32 = -INFINITY;
+    float cval = -INFINITY;   // band member held by this lane
+    int32_t cidx = -1;
+    int ncand = 0;
+    bool spill = false;
+    for (int s0 = 0; s0 < cnt; s0 += 4) {
+        float part[4];
+        int32_t id[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            id[u] = (s0 + u < cnt) ? bk[s0 + u] : -1;
+            float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (id[u] >= 0) xv = reinterpret_cast<const float4 *>(rows + (int64_t)id[u] * kD)[lane];
+            part[u] = fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w)));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (id[u] < 0) continue;
+            const float v = part[u];
+            if (v > best32) {
+                // new FP32 best: keep only band members still within 2 eps_r of it
+                best32 = v;
+                const bool keep = lane < ncand && cval >= __fsub_rd(best32, band);
+                const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                const int nk = __popc(mk);
+                unsigned rest = mk;  // clear the `lane` lowest set bits: the next one is member #lane
+                for (int p = 0; p < lane && rest; ++p) rest &= rest - 1;
+                const int src = rest ? __ffs(rest) - 1 : 0;
+                const float nv = __shfl_sync(0xffffffffu, cval, src);
+                const int32_t ni = __shfl_sync(0xffffffffu, cidx, src);
+                cval = lane < nk ? nv : -INFINITY;
+                cidx = lane < nk ? ni : -1;
+                ncand = nk;
+            }
+            if (v >= __fsub_rd(best32, band)) {
+                if (ncand < 32) {
+                    if (lane == ncand) { cval = v; cidx = id[u]; }
+                    ++ncand;
+                } else {
+                    spill = true;
+                }
+            }
+        }
+    }
+    double bs = -INFINITY;
+    int64_t bi = -1;
+    if (!spill) {
+        if (lane < ncand) { bs = dot64_seq(q + j * kD, rows + (int64_t)cidx * kD); bi = cidx; }
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)ncand);
+    } else {
+        for (int s = lane; s < cnt; s += 32) {
+            const int32_t id = bk[s];
+            const double v = dot64_seq(q + j * kD, rows + (int64_t)id * kD);
+            if (v > bs || (v == bs && id < bi)) { bs = v; bi = id; }
+        }
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || os > bs || (os == bs && oi < bi))) { bs = os; bi = oi; }
+    }
+    if (lane == 0) {
+        out_idx[j] = bi;
+        out_sim[j] = bs;
+    }
+}
+
+cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
+                           cudaStream_t st) {
+    const int64_t blocks = (nq * 32 + 255) / 256;
+    k_rescore<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
+                                                ix.ws.qnorm, ix.host_max[4], out_idx, out_sim, ix.ws.status,
+                                                ix.ws.counters);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ brute force
+__global__ void k_brute_finish(const unsigned long long *__restrict__ key1, int64_t nq, int64_t *out_idx,
+                               double *out_sim) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    out_idx[j] = (int64_t)best_idx(key1[j]);
+    out_sim[j] = (double)best_score(key1[j]);
+}
+
+cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
+                              cudaStream_t st) {
+    // rows are [n][128]; the last tile reads up to n_tiles*256 rows, so the
+    // master copy is allocated with that padding (zeros).
+    cudaError_t e = cudaMemsetAsync(ix.ws.key1, 0, sizeof(unsigned long long) * nq, st);
+    if (e != cudaSuccess) return e;
+    e = stream_scan_kt<128, false>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, ix.ws, st);
+    if (e != cudaSuccess) return e;
+    k_brute_finish<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(ix.ws.key1, nq, out_idx, out_sim);
+    return cudaGetLastError();
+}
+
+}  // namespace hn

@@ -1,7 +1,296 @@
-// tcgen05 dense prefix scan (placeholder until the tensor-core kernel lands).
+// Dense prefix scan on the 5th-generation tensor cores (tcgen05), Phase 1 and
+// Phase 2 of Algorithm 1 (§3.3) for a BF16 major prefix.
+//
+// For a tile of 128 queries (A, K-major) and 256 database entries (B,
+// K-major) one tcgen05.mma per 16 prefix columns computes the 128 x 256 block
+// of prefix scores s~ = q^ . x^ with FP32 accumulation into tensor memory.
+// Products of two BF16 values are exact in FP32; the sum carries at most the
+// accumulation error bounded in the Phase-2 slack (hn_prep.cu).
+//
+// Persistent CTAs (one per SM, 10 warps):
+//   warp 0   producer: 1-D bulk copies of the query tile (once per work unit)
+//            and of each 8 KB entry tile into a ring of shared-memory stages;
+//   warp 1   allocates 512 TMEM columns; one lane issues the MMAs into one of
+//            two 256-column accumulators and commits them to mbarriers;
+//   warps 2-9 epilogue: TMEM -> registers (thread = query row, 128 columns per
+//            warp), a max over 32 columns per three-input max tree, then
+//              Phase 1: running best (score, lowest index), atomicMax per query;
+//              Phase 2: entries with s~ >= tau_q appended to q's survivor slots.
+// A work unit is (query tile, contiguous chunk of entry tiles); units are
+// numbered chunk-major so that the CTAs running together read the same entry
+// tiles, which then come from L2.
+// Every mbarrier wait gives up after 2 s of global time: the CTA raises a
+// shared abort flag, the others leave their loops, copies and MMAs in flight
+// are drained (again with a limit), TMEM is released and the status word
+// ST_TIMEOUT tells the host.
 #include "hn_internal.cuh"
+#include "hn_sm100.cuh"
 
 namespace hn {
-bool dense_scan_supported(const Index &) { return false; }
-cudaError_t launch_dense_scan(const Index &, int64_t, int, cudaStream_t) { return cudaErrorNotSupported; }
+using namespace sm100;
+
+constexpr int kDenseThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
+
+struct DenseParams {
+    const __nv_bfloat16 *pre16;   // entries, UMMA core-matrix order, n_tiles * 256 rows
+    const __nv_bfloat16 *qpre16;  // queries, same order, n_qt * 128 rows
+    int64_t n, n_tiles, nq;
+    int64_t n_qt, tiles_per_chunk, n_units;
+    const float *tau;
+    unsigned long long *key1;
+    int32_t *bucket, *count;
+    int32_t cap;
+    int32_t *status;
+};
+
+template <int KP>
+struct DenseCfg {
+    static constexpr uint32_t kB = kTileE * KP * 2;  // bytes of one entry tile
+    static constexpr uint32_t kA = kTileQ * KP * 2;  // bytes of one query tile
+    static constexpr int kStages = (96 * 1024) / kB;
+    static constexpr uint32_t kBarOff = kStages * kB + 2 * kA;
+    static constexpr int kBars = 2 * kStages + 9;
+    static constexpr uint32_t kSmem = kBarOff + kBars * 8 + 16;
+};
+
+__device__ __forceinline__ float max32(const float (&v)[32]) {
+    float a[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    a[10] = fmaxf(v[30], v[31]);
+    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+    return fmaxf(fmax3(b0, b1, b2), fmaxf(a[9], a[10]));
+}
+
+template <int KP, int PHASE>
+__global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DenseParams p) {
+    using C = DenseCfg<KP>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sB = smem;
+    uint8_t *sA = smem + C::kStages * C::kB;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
+    uint64_t *b_full = bars, *b_empty = bars + C::kStages;
+    uint64_t *a_full = bars + 2 * C::kStages, *a_empty = a_full + 2;
+    uint64_t *acc_full = a_empty + 2, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::kStages; ++i) {
+            mbar_init(smem_u32(&b_full[i]), 1);
+            mbar_init(smem_u32(&b_empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&a_full[i]), 1);
+            mbar_init(smem_u32(&a_empty[i]), 1);
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), kEpiWarps * 32);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t G = gridDim.x;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0;
+            uint32_t issued = 0;               // stages / A buffers that received a copy
+            uint32_t last_par = 0;             // parity of the last copy per stage / A buffer
+            bool ok = true;
+            for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
+                const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
+                const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
+                if (!(ok = mbar_wait(smem_u32(&a_empty[abuf]), aphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                mbar_arrive_expect_tx(smem_u32(&a_full[abuf]), C::kA);
+                bulk_g2s(smem_u32(sA + abuf * C::kA), p.qpre16 + qt * kTileQ * KP, C::kA, smem_u32(&a_full[abuf]));
+                issued |= 1u << (24 + abuf);
+                last_par = (last_par & ~(1u << (24 + abuf))) | (aphase << (24 + abuf));
+                if (++abuf == 2) { abuf = 0; aphase ^= 1; }
+                for (int64_t t = t0; t < t1; ++t) {
+                    if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                    mbar_arrive_expect_tx(smem_u32(&b_full[stage]), C::kB);
+                    bulk_g2s(smem_u32(sB + stage * C::kB), p.pre16 + t * kTileE * KP, C::kB, smem_u32(&b_full[stage]));
+                    issued |= 1u << stage;
+                    last_par = (last_par & ~(1u << stage)) | (sphase << stage);
+                    if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
+                }
+            }
+            // copies still in flight must land before this CTA's shared memory goes away
+            for (int s = 0; s < C::kStages; ++s)
+                if (issued & (1u << s)) mbar_drain(smem_u32(&b_full[s]), (last_par >> s) & 1, kWaitLimitNs);
+            for (int s = 0; s < 2; ++s)
+                if (issued & (1u << (24 + s))) mbar_drain(smem_u32(&a_full[s]), (last_par >> (24 + s)) & 1, kWaitLimitNs);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(kTileQ, kTileE);
+            uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, acc = 0, accphase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
+                const int64_t ch = u / p.n_qt;
+                const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
+                if (!(ok = mbar_wait(smem_u32(&a_full[abuf]), aphase, abort_flag, kWaitLimitNs))) break;
+                tc_fence_after();
+                const uint32_t a_addr = smem_u32(sA + abuf * C::kA);
+                for (int64_t t = t0; t < t1; ++t) {
+                    if (!(ok = mbar_wait(smem_u32(&acc_empty[acc]), accphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                    if (!(ok = mbar_wait(smem_u32(&b_full[stage]), sphase, abort_flag, kWaitLimitNs))) break;
+                    tc_fence_after();
+                    const uint32_t b_addr = smem_u32(sB + stage * C::kB);
+#pragma unroll
+                    for (int kk = 0; kk < KP / 16; ++kk) {
+                        // 16 columns = two core matrices along K, 128 B apart; 8-row groups KP*16 B apart
+                        const uint64_t ad = smem_desc(a_addr + kk * 256, 128, KP * 16);
+                        const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
+                        umma_bf16(tmem + acc * kTileE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                    umma_commit(smem_u32(&b_empty[stage]));
+                    umma_commit(smem_u32(&acc_full[acc]));
+                    if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
+                    if (++acc == 2) { acc = 0; accphase ^= 1; }
+                }
+                umma_commit(smem_u32(&a_empty[abuf]));
+                if (++abuf == 2) { abuf = 0; aphase ^= 1; }
+            }
+            // every MMA issued so far must finish before TMEM is released
+            umma_commit(smem_u32(drain));
+            mbar_drain(smem_u32(drain), 0, kWaitLimitNs);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;          // TMEM lanes this warp may read: 32*quarter ..
+        const int half = (warp - 2) >> 2;      // columns 128*half .. 128*half + 127
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        uint32_t acc = 0, accphase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
+            const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
+            const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
+            const int64_t q = qt * kTileQ + row;
+            const bool qvalid = q < p.nq;
+            const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
+            float best = -INFINITY;
+            int64_t bidx = -1;
+            for (int64_t t = t0; t < t1; ++t) {
+                if (!(ok = mbar_wait(smem_u32(&acc_full[acc]), accphase, abort_flag, kWaitLimitNs))) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    const int col0 = half * 128 + c * 32;
+                    float v[32];
+                    tmem_ld32(tmem + acc * kTileE + col0 + lane_addr, v);
+                    const float m = max32(v);
+                    const int64_t e0 = t * kTileE + col0;
+                    if (PHASE == 1) {
+                        if (m > best) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (v[i] > best && e0 + i < p.n) { best = v[i]; bidx = e0 + i; }
+                        }
+                    } else {
+                        if (m >= thr) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if (v[i] >= thr && e0 + i < p.n) {
+                                    const int slot = atomicAdd(p.count + q, 1);
+                                    if (slot < p.cap) p.bucket[q * p.cap + slot] = (int32_t)(e0 + i);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(&acc_empty[acc]));
+                if (++acc == 2) { acc = 0; accphase ^= 1; }
+            }
+            if (PHASE == 1 && qvalid && bidx >= 0) atomicMax(p.key1 + q, pack_best(best, (uint32_t)bidx));
+        }
+    }
+
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status + ST_TIMEOUT, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+static int g_num_sms = 0;
+
+static int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+bool dense_scan_supported(const Index &ix) {
+    return ix.prefix == HN_PREFIX_BF16 && (ix.k_pad16 == 16 || ix.k_pad16 == 32 || ix.k_pad16 == 64);
+}
+
+template <int KP, int PHASE>
+static cudaError_t launch_kp(const DenseParams &p, int grid, cudaStream_t st) {
+    using C = DenseCfg<KP>;
+    const int smem = (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_dense_scan<KP, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_dense_scan<KP, PHASE><<<grid, kDenseThreads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
+    if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
+    const Workspace &ws = ix.ws;
+    DenseParams p{};
+    p.pre16 = ix.pre16;
+    p.qpre16 = ws.qpre16;
+    p.n = ix.n;
+    p.n_tiles = ix.n_tiles;
+    p.nq = nq;
+    p.n_qt = (nq + kTileQ - 1) / kTileQ;
+    const int G = num_sms();
+    // about 32 units per CTA, chunk-major, so that the running CTAs share entry tiles in L2
+    int64_t chunks = (32ll * G + p.n_qt - 1) / p.n_qt;
+    chunks = max64(1, min64(chunks, ix.n_tiles));
+    p.tiles_per_chunk = (ix.n_tiles + chunks - 1) / chunks;
+    chunks = (ix.n_tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    p.n_units = p.n_qt * chunks;
+    p.tau = ws.tau;
+    p.key1 = ws.key1;
+    p.bucket = ws.bucket;
+    p.count = ws.count;
+    p.cap = ws.bucket_cap;
+    p.status = ws.status;
+    const int grid = (int)min64(G, p.n_units);
+    switch (ix.k_pad16) {
+        case 16: return phase == 1 ? launch_kp<16, 1>(p, grid, st) : launch_kp<16, 2>(p, grid, st);
+        case 32: return phase == 1 ? launch_kp<32, 1>(p, grid, st) : launch_kp<32, 2>(p, grid, st);
+        case 64: return phase == 1 ? launch_kp<64, 1>(p, grid, st) : launch_kp<64, 2>(p, grid, st);
+    }
+    return cudaErrorNotSupported;
+}
+
 }  // namespace hn

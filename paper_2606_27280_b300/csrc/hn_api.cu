@@ -37,6 +37,9 @@ static void free_ws(Workspace &ws) {
     cudaFree(ws.bucket);
     cudaFree(ws.count);
     cudaFree(ws.key1);
+    cudaFree(ws.cand);
+    ws.cand = nullptr;
+    ws.cand_cap = 0;
     cudaFree(ws.tau);
     cudaFree(ws.qpre32);
     cudaFree(ws.qpre16);
@@ -236,7 +239,7 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, int
     HN_CUDA(mark(1));
     HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s) : launch_stream_scan(ix, nq, 1, s));
     HN_CUDA(mark(2));
-    HN_CUDA(launch_seed_threshold(ix, q, nq, s));
+    HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, s));
     HN_CUDA(mark(3));
     HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
     HN_CUDA(mark(4));
@@ -281,6 +284,18 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     for (;;) {
         hn_status st = ensure_ws(ix, nq, cap);
         if (st != HN_OK) return st;
+        if (scan == HN_SCAN_DENSE) {
+            const int64_t slots = dense_cand_slots(ix, nq);
+            const int64_t need = ((nq + kTileQ - 1) / kTileQ * kTileQ) * slots;
+            if (need > ws.cand_cap) {
+                cudaFree(ws.cand);
+                ws.cand = nullptr;
+                ws.cand_cap = 0;
+                HN_CUDA(dalloc(&ws.cand, need));
+                ws.cand_cap = need;
+            }
+            ws.cand_slots = (int32_t)slots;
+        }
         HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
         HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
         st = run_search(ix, q, nq, scan, out_idx, out_sim, timing, s);

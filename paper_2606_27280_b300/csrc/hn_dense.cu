@@ -12,9 +12,9 @@
 //            and of each 8 KB entry tile into a ring of shared-memory stages;
 //   warp 1   allocates 512 TMEM columns; one lane issues the MMAs into one of
 //            two 256-column accumulators and commits them to mbarriers;
-//   warps 2-9 epilogue: TMEM -> registers (thread = query row, 128 columns per
-//            warp), a max over 32 columns per three-input max tree, then
-//              Phase 1: running best (score, lowest index), atomicMax per query;
+//   warps 2-17 epilogue (4 per SM sub-partition): TMEM -> registers (thread =
+//            query row, 64 accumulator columns per warp), one max tree, then
+//              Phase 1: running best score and its 64-entry segment per (query, chunk, segment);
 //              Phase 2: entries with s~ >= tau_q appended to q's survivor slots.
 // A work unit is (query tile, contiguous chunk of entry tiles); units are
 // numbered chunk-major so that the CTAs running together read the same entry
@@ -29,8 +29,8 @@
 namespace hn {
 using namespace sm100;
 
-constexpr int kDenseThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;  // 4 per SM sub-partition, 64 accumulator columns each
+constexpr int kDenseThreads = (2 + kEpiWarps) * 32;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
@@ -40,29 +40,38 @@ struct DenseParams {
     int64_t n, n_tiles, nq;
     int64_t n_qt, tiles_per_chunk, n_units;
     const float *tau;
-    unsigned long long *key1;
+    unsigned long long *cand;     // [nq][4 * chunks] Phase-1 (best score, segment id) per (query, chunk, column segment)
     int32_t *bucket, *count;
     int32_t cap;
     int32_t *status;
 };
 
+constexpr int kLcap = 32;  // Phase-2 survivors staged per epilogue thread before a flush
+
 template <int KP>
 struct DenseCfg {
     static constexpr uint32_t kB = kTileE * KP * 2;  // bytes of one entry tile
     static constexpr uint32_t kA = kTileQ * KP * 2;  // bytes of one query tile
-    static constexpr int kStages = (96 * 1024) / kB;
-    static constexpr uint32_t kBarOff = kStages * kB + 2 * kA;
+    static constexpr int kStages = (64 * 1024) / kB < 2 ? 2 : (64 * 1024) / kB;
+    static constexpr uint32_t kSurvOff = kStages * kB + 2 * kA;
+    static constexpr uint32_t kBarOff = kSurvOff + kLcap * kEpiWarps * 32 * 4;  // [kLcap][512] entry ids
     static constexpr int kBars = 2 * kStages + 9;
     static constexpr uint32_t kSmem = kBarOff + kBars * 8 + 16;
 };
 
-__device__ __forceinline__ float max32(const float (&v)[32]) {
-    float a[11];
+// Pairwise max tree over 64 scores (63 two-input max, depth 6, wide ILP):
+// g[k] = max of v[16k .. 16k+15], returns the max of all 64.
+__device__ __forceinline__ float max_tree64(const float (&v)[64], float (&g)[4]) {
+    float a[32], b[16], c[8];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-    a[10] = fmaxf(v[30], v[31]);
-    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
-    return fmaxf(fmax3(b0, b1, b2), fmaxf(a[9], a[10]));
+    for (int i = 0; i < 32; ++i) a[i] = fmaxf(v[2 * i], v[2 * i + 1]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) b[i] = fmaxf(a[2 * i], a[2 * i + 1]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) c[i] = fmaxf(b[2 * i], b[2 * i + 1]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = fmaxf(c[2 * i], c[2 * i + 1]);
+    return fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
 }
 
 template <int KP, int PHASE>
@@ -88,7 +97,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             mbar_init(smem_u32(&a_full[i]), 1);
             mbar_init(smem_u32(&a_empty[i]), 1);
             mbar_init(smem_u32(&acc_full[i]), 1);
-            mbar_init(smem_u32(&acc_empty[i]), kEpiWarps * 32);
+            mbar_init(smem_u32(&acc_empty[i]), kEpiWarps);  // one elected arrive per epilogue warp
         }
         mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
@@ -174,9 +183,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
     } else {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;          // TMEM lanes this warp may read: 32*quarter ..
-        const int half = (warp - 2) >> 2;      // columns 128*half .. 128*half + 127
+        const int seg = (warp - 2) >> 2;       // accumulator columns 64*seg .. 64*seg + 63
         const int row = quarter * 32 + lane;
+        const int et = threadIdx.x - 64;       // epilogue thread 0..511
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        uint32_t *sbuf = reinterpret_cast<uint32_t *>(smem + C::kSurvOff);  // [kLcap][512]
         uint32_t acc = 0, accphase = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
@@ -186,40 +197,57 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             const bool qvalid = q < p.nq;
             const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
             float best = -INFINITY;
-            int64_t bidx = -1;
+            int64_t bseg = -1;
+            int lc = 0;
+            // Phase 2: move this thread's staged survivors to its query's slots
+            auto flush = [&]() {
+                const int slot = atomicAdd(p.count + q, lc);
+                for (int j = 0; j < lc; ++j)
+                    if (slot + j < p.cap) p.bucket[q * p.cap + slot + j] = (int32_t)sbuf[j * 512 + et];
+                lc = 0;
+            };
             for (int64_t t = t0; t < t1; ++t) {
                 if (!(ok = mbar_wait(smem_u32(&acc_full[acc]), accphase, abort_flag, kWaitLimitNs))) break;
                 tc_fence_after();
-#pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
-                    const int col0 = half * 128 + c * 32;
-                    float v[32];
-                    tmem_ld32(tmem + acc * kTileE + col0 + lane_addr, v);
-                    const float m = max32(v);
-                    const int64_t e0 = t * kTileE + col0;
-                    if (PHASE == 1) {
-                        if (m > best) {
+                float v[64];
+                tmem_ld64(tmem + acc * kTileE + seg * 64 + lane_addr, v);
+                // the scores are in registers: hand the accumulator back to the MMA warp now
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+                if (++acc == 2) { acc = 0; accphase ^= 1; }
+                float g[4];
+                const float m = max_tree64(v, g);
+                const int64_t e0 = t * kTileE + seg * 64;
+                if (PHASE == 1) {
+                    // running best score and the 64-entry segment holding it; the entry
+                    // itself is recovered by the threshold kernel
+                    if (m > best && e0 < p.n) { best = m; bseg = t * 4 + seg; }
+                } else if (m >= thr) {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (v[i] > best && e0 + i < p.n) { best = v[i]; bidx = e0 + i; }
-                        }
-                    } else {
-                        if (m >= thr) {
+                    for (int k = 0; k < 4; ++k) {
+                        if (g[k] >= thr) {
+                            uint32_t mask = 0;
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                if (v[i] >= thr && e0 + i < p.n) {
-                                    const int slot = atomicAdd(p.count + q, 1);
-                                    if (slot < p.cap) p.bucket[q * p.cap + slot] = (int32_t)(e0 + i);
-                                }
+                            for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
+                            const int64_t ek = e0 + 16 * k;
+                            if (ek + 16 > p.n) mask &= ek >= p.n ? 0u : ((1u << (uint32_t)(p.n - ek)) - 1u);
+                            if (lc + __popc(mask) > kLcap) flush();
+                            while (mask) {
+                                const int i = __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                sbuf[lc * 512 + et] = (uint32_t)(ek + i);
+                                ++lc;
                             }
                         }
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(smem_u32(&acc_empty[acc]));
-                if (++acc == 2) { acc = 0; accphase ^= 1; }
             }
-            if (PHASE == 1 && qvalid && bidx >= 0) atomicMax(p.key1 + q, pack_best(best, (uint32_t)bidx));
+            // one writer per (query, chunk, segment): no atomics, every slot written
+            if (PHASE == 1 && qvalid)
+                p.cand[q * (4 * (p.n_units / p.n_qt)) + 4 * ch + seg] =
+                    bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
+            if (PHASE == 2 && lc > 0) flush();
         }
     }
 
@@ -241,6 +269,22 @@ static int num_sms() {
         if (g_num_sms <= 0) g_num_sms = 148;
     }
     return g_num_sms;
+}
+
+// About 32 work units per CTA, numbered chunk-major so that the running CTAs
+// share entry tiles in L2.
+static void dense_chunking(int64_t n_tiles, int64_t n_qt, int G, int64_t *tiles_per_chunk, int64_t *chunks) {
+    int64_t c = (32ll * G + n_qt - 1) / n_qt;
+    c = max64(1, min64(c, n_tiles));
+    const int64_t tpc = (n_tiles + c - 1) / c;
+    *tiles_per_chunk = tpc;
+    *chunks = (n_tiles + tpc - 1) / tpc;
+}
+
+int64_t dense_cand_slots(const Index &ix, int64_t nq) {
+    int64_t tpc = 0, chunks = 0;
+    dense_chunking(ix.n_tiles, (nq + kTileQ - 1) / kTileQ, num_sms(), &tpc, &chunks);
+    return 4 * chunks;
 }
 
 bool dense_scan_supported(const Index &ix) {
@@ -272,14 +316,11 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     p.nq = nq;
     p.n_qt = (nq + kTileQ - 1) / kTileQ;
     const int G = num_sms();
-    // about 32 units per CTA, chunk-major, so that the running CTAs share entry tiles in L2
-    int64_t chunks = (32ll * G + p.n_qt - 1) / p.n_qt;
-    chunks = max64(1, min64(chunks, ix.n_tiles));
-    p.tiles_per_chunk = (ix.n_tiles + chunks - 1) / chunks;
-    chunks = (ix.n_tiles + p.tiles_per_chunk - 1) / p.tiles_per_chunk;
+    int64_t chunks = 0;
+    dense_chunking(ix.n_tiles, p.n_qt, G, &p.tiles_per_chunk, &chunks);
     p.n_units = p.n_qt * chunks;
     p.tau = ws.tau;
-    p.key1 = ws.key1;
+    p.cand = ws.cand;
     p.bucket = ws.bucket;
     p.count = ws.count;
     p.cap = ws.bucket_cap;

@@ -61,7 +61,10 @@ struct Workspace {
     int32_t bucket_cap = 0;
     int32_t *bucket = nullptr;         // [q_cap][bucket_cap] survivor entry ids
     int32_t *count = nullptr;          // [q_cap] survivor counts (may exceed bucket_cap)
-    unsigned long long *key1 = nullptr;// [q_cap] Phase-1 best (score, index) key
+    unsigned long long *key1 = nullptr;// [q_cap] Phase-1 best (score, index) key (stream scan)
+    unsigned long long *cand = nullptr;// [q_cap][cand_slots] Phase-1 per-chunk bests (dense scan)
+    int64_t cand_cap = 0;              // allocated length of cand
+    int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
     float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
     __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles
@@ -115,11 +118,12 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t s);
 cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t s);
 cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
 cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
-cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, cudaStream_t s);
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, cudaStream_t s);
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                            double *out_sim, cudaStream_t s);
 cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                               double *out_sim, cudaStream_t s);
 bool dense_scan_supported(const Index &ix);
+int64_t dense_cand_slots(const Index &ix, int64_t nq);
 
 }  // namespace hn

@@ -178,30 +178,112 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 }
 
 // ------------------------------------------------------------------ threshold
-// Algorithm 1, step 2: the Phase-1 winner b is scored in full,
-//   T_q = <q, x_b>  (binary64, dimension order: the oracle's own value),
-// a certified lower bound on the final maximum.  The Phase-2 prefix threshold is
-//   tau_q = round_down(T_q - E_q),
-// so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  entry cannot win.
-__global__ void k_seed_threshold(const float *__restrict__ rows, const float *__restrict__ q, int64_t nq,
-                                 const unsigned long long *__restrict__ key1, const float *__restrict__ qeps,
-                                 float *__restrict__ tau, int32_t *__restrict__ count) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nq) return;
-    count[j] = 0;
-    const unsigned long long kb = key1[j];
-    if (kb == 0ull) { tau[j] = -INFINITY; return; }   // no candidate: keep everything
-    const uint32_t b = best_idx(kb);
-    const float *x = rows + (int64_t)b * kD;
-    const float *qq = q + j * kD;
-    double s = 0.0;
-    for (int c = 0; c < kD; ++c) s = fma((double)qq[c], (double)x[c], s);
-    tau[j] = __double2float_rd(__dsub_rd(s, (double)qeps[j]));
+// Algorithm 1, step 2, with more than one Phase-1 candidate.  Phase 1 leaves S
+// candidate keys (prefix score, id) per query: for the stream scan S = 1 and
+// the id is the best entry; for the dense scan S = 4 x chunks and the id names
+// a 64-entry segment (tile * 4 + segment) whose maximum prefix score is the key.
+// One warp per query takes the R best keys; for a segment it recomputes the 64
+// prefix scores from the stored prefixes (FP32 FMA) and keeps the best valid
+// entry.  Each chosen entry is scored in full in FP32 (lane l owns dims
+// 4l..4l+3), and
+//   T_q = max_j RD(fp32_j - eps_r) <= max_j <q, x_j> (binary64, the oracle's value)
+// is a certified lower bound on the final maximum (eps_r bounds the FP32 error
+// of a 128-term sum in any order).  Any entry is a valid candidate: the choice
+// only decides how tight T_q is.  The Phase-2 prefix threshold is
+//   tau_q = RD(T_q - E_q),
+// so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  the entry cannot win.
+constexpr int kSeedR = 4;
+
+__device__ inline float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, cudaStream_t st) {
-    k_seed_threshold<<<(unsigned)((nq + 127) / 128), 128, 0, st>>>(ix.rows, q, nq, ix.ws.key1, ix.ws.qeps,
-                                                                   ix.ws.tau, ix.ws.count);
+__device__ inline float rescore_eps(float qn, float xn_max) {
+    return __fmul_ru(__fmul_ru(qn, xn_max), 128 * 0x1p-24 / (1 - 128 * 0x1p-24) + 1e-12f);
+}
+
+// FP32 prefix score of entry e against the query prefix qp (BF16 values, k_pad16 wide)
+__device__ inline float prefix_score16(const __nv_bfloat16 *__restrict__ pre16, int64_t e, const float *qp, int kp) {
+    float s = 0.f;
+    for (int c = 0; c < kp; c += 8) {
+        const uint4 raw = *reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(pre16) + pre16_offset(e, c, kp));
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float2 f = __bfloat1622float2(h[u]);
+            s = fmaf(qp[c + 2 * u], f.x, s);
+            s = fmaf(qp[c + 2 * u + 1], f.y, s);
+        }
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict__ rows, const float *__restrict__ q,
+                                                        int64_t nq, int64_t n, const unsigned long long *__restrict__ cand,
+                                                        int S, int seg_entries, const __nv_bfloat16 *__restrict__ pre16,
+                                                        int kp, const float *__restrict__ qpre32,
+                                                        const float *__restrict__ qeps,
+                                                        const float *__restrict__ qnorm, float xnorm_max,
+                                                        float *__restrict__ tau, int32_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    if (lane == 0) count[j] = 0;
+    const unsigned long long *cj = cand + j * (int64_t)S;
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float *qp = qpre32 + j * kp;
+    const float eps_r = rescore_eps(qnorm[j], xnorm_max);
+    float t_low = -INFINITY;
+    unsigned long long taken = ~0ull;
+    for (int r = 0; r < kSeedR; ++r) {
+        unsigned long long km = 0;
+        for (int s = lane; s < S; s += 32) {
+            const unsigned long long k = cj[s];
+            if (k < taken && k > km) km = k;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, km, o);
+            km = other > km ? other : km;
+        }
+        if (km == 0ull) break;
+        taken = km;
+        int64_t e = best_idx(km);
+        if (seg_entries > 1) {
+            // best valid entry of the segment by recomputed prefix score (lowest index on ties)
+            const int64_t e0 = e * seg_entries;
+            unsigned long long kb = 0;
+            for (int i = lane; i < seg_entries; i += 32) {
+                const int64_t ei = e0 + i;
+                if (ei < n) {
+                    const unsigned long long kk = pack_best(prefix_score16(pre16, ei, qp, kp), (uint32_t)ei);
+                    kb = kk > kb ? kk : kb;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, kb, o);
+                kb = other > kb ? other : kb;
+            }
+            if (kb == 0ull) continue;
+            e = best_idx(kb);
+        }
+        const float4 xv = reinterpret_cast<const float4 *>(rows + e * kD)[lane];
+        const float sim = warp_sum_f(fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w))));
+        t_low = fmaxf(t_low, __fsub_rd(sim, eps_r));
+    }
+    if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+}
+
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, cudaStream_t st) {
+    const Workspace &ws = ix.ws;
+    const int64_t blocks = (nq * 32 + 255) / 256;
+    k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, dense ? ws.cand : ws.key1,
+                                                       dense ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
+                                                       ix.k_pad16, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4],
+                                                       ws.tau, ws.count);
     return cudaGetLastError();
 }
 
@@ -240,7 +322,7 @@ __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows,
         return;
     }
     const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
-    const float eps = __fmul_ru(__fmul_ru(qnorm[j], xnorm_max), 128 * 0x1p-24 / (1 - 128 * 0x1p-24) + 1e-12f);
+    const float eps = rescore_eps(qnorm[j], xnorm_max);
     const float band = __fmul_ru(2.f, eps);
     const int32_t *bk = bucket + j * (int64_t)cap;
     float best32 = -INFINITY;
@@ -248,11 +330,12 @@ __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows,
     int32_t cidx = -1;
     int ncand = 0;
     bool spill = false;
-    for (int s0 = 0; s0 < cnt; s0 += 4) {
-        float part[4];
-        int32_t id[4];
+    constexpr int U = 8;  // survivor rows in flight per warp
+    for (int s0 = 0; s0 < cnt; s0 += U) {
+        float part[U];
+        int32_t id[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             id[u] = (s0 + u < cnt) ? bk[s0 + u] : -1;
             float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
             if (id[u] >= 0) xv = reinterpret_cast<const float4 *>(rows + (int64_t)id[u] * kD)[lane];
@@ -261,9 +344,9 @@ __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows,
 #pragma unroll
         for (int o = 16; o; o >>= 1)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+            for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (id[u] < 0) continue;
             const float v = part[u];
             if (v > best32) {

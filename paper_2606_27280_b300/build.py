@@ -1,6 +1,8 @@
 """Build libhn.so (the CUDA library behind include/hn.h) in-tree for sm_103a.
 
-    python -m paper_2606_27280_b300.build [--force] [--verbose]
+    python paper_2606_27280_b300/build.py [--force] [--verbose]
+
+(run by path: importing the package would load the library being rebuilt)
 
 Each csrc/*.cu is compiled to an object under csrc/_build/ and linked into
 paper_2606_27280_b300/_lib/libhn.so with the CUDA runtime linked statically.

@@ -3,7 +3,7 @@
 Argument marshalling only: every step of normalisation, index packing and
 search runs in the library's CUDA kernels.  PyTorch supplies device memory
 and the current stream.  If libhn.so is missing this module raises on
-import; build it with ``python -m paper_2606_27280_b300.build``.
+import; build it with ``python paper_2606_27280_b300/build.py``.
 """
 from __future__ import annotations
 
@@ -69,10 +69,13 @@ SIGNATURES = {
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
-        raise ImportError(f"libhn.so not found at {path}; build it with `python -m paper_2606_27280_b300.build`")
+        raise ImportError(f"libhn.so not found at {path}; build it with `python paper_2606_27280_b300/build.py`")
     lib = ctypes.CDLL(path)
     for name, (args, res) in SIGNATURES.items():
-        fn = getattr(lib, name)
+        try:
+            fn = getattr(lib, name)
+        except AttributeError as e:
+            raise ImportError(f"{path} lacks {name}: rebuild with `python paper_2606_27280_b300/build.py`") from e
         fn.argtypes = args
         fn.restype = res
     return lib

@@ -177,6 +177,31 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
 hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx,
                         double *out_sim, void *stream);
 
+/*
+ * Allocation-free variant of hn_bruteforce (the paper has no counterpart; this
+ * is a deployment aid).  Same kernels and same results as hn_bruteforce, but
+ * its per-query scratch is a fixed array inside the library instead of memory
+ * allocated on demand, so the call itself allocates nothing.  It is meant for
+ * callers that must not allocate device memory while answering queries: a
+ * latency-critical thread (cudaMalloc may block and synchronise the device),
+ * a process whose device memory is owned by another allocator or capped by a
+ * fixed budget, or a deployment that forbids allocation after start-up.
+ *  - index, q, out_idx, out_sim: as for hn_bruteforce (built index, caller-owned
+ *    device buffers).  nq <= HN_STATIC_MAX_QUERIES, else HN_ERR_INVALID_ARG.
+ *  - The scratch holds HN_STATIC_MAX_QUERIES 8-byte keys (512 KiB) on every GPU
+ *    that loads the library, kept until the process exits.
+ *  - The first call on each device looks the scratch address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents; each
+ *    call clears the keys it uses before scanning.  Calls that overlap on the
+ *    GPU (e.g. on unordered streams) race and can return wrong answers: order them.
+ *  - Does not synchronise.
+ */
+#define HN_STATIC_MAX_QUERIES 65536
+hn_status hn_bruteforce_static(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx,
+                               double *out_sim, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

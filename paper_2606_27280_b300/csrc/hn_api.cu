@@ -110,6 +110,8 @@ struct hn_index {
     Index ix;
 };
 
+const Index *hn::index_state(const hn_index *h) { return h ? &h->ix : nullptr; }
+
 extern "C" {
 
 int32_t hn_version(void) { return (0 << 16) | 1; }

@@ -123,6 +123,11 @@ cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t 
                            double *out_sim, cudaStream_t s);
 cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                               double *out_sim, cudaStream_t s);
+// Brute force with a caller-provided per-query key array (nq entries, cleared here).
+cudaError_t launch_bruteforce_keys(const Index &ix, const float *q, int64_t nq, unsigned long long *keys,
+                                   int64_t *out_idx, double *out_sim, cudaStream_t s);
+// Device state of a built index (used by entry points outside hn_api.cu).
+const Index *index_state(const hn_index *h);
 bool dense_scan_supported(const Index &ix);
 int64_t dense_cand_slots(const Index &ix, int64_t nq);
 

@@ -429,4 +429,16 @@ cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64
     return cudaGetLastError();
 }
 
+cudaError_t launch_bruteforce_keys(const Index &ix, const float *q, int64_t nq, unsigned long long *keys,
+                                   int64_t *out_idx, double *out_sim, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * nq, st);
+    if (e != cudaSuccess) return e;
+    Workspace w = ix.ws;  // same scan, keys redirected to the caller's array
+    w.key1 = keys;
+    e = stream_scan_kt<128, false>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, w, st);
+    if (e != cudaSuccess) return e;
+    k_brute_finish<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(keys, nq, out_idx, out_sim);
+    return cudaGetLastError();
+}
+
 }  // namespace hn

@@ -64,7 +64,9 @@ SIGNATURES = {
     "hn_index_get_info": ([_vp, _vp], _i32),
     "hn_search_batch": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hn_bruteforce_static": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
 }
+STATIC_MAX_QUERIES = 65536
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:

@@ -1,0 +1,122 @@
+"""Binary64 oracle of the learned block proposal -- TEST INFRASTRUCTURE.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may use
+this module; the CUDA library never calls it.
+
+The proposal is the extension that seeds the threshold of Algorithm 1 (§3.3):
+an MLP maps a query's major prefix (the K-dim part of Eq. 1) to scores over
+database blocks; the blocks it ranks highest are scored first to obtain a good
+threshold.  The paper has no such network; this oracle fixes the arithmetic
+the GPU kernels must reproduce:
+
+    a1 = W1 x + b1,  h1 = gelu(a1)          W1: (H1, K)
+    a2 = W2 h1 + b2, h2 = gelu(a2)          W2: (H2, H1)
+    z  = W3 h2 + b3                         W3: (C, H2)
+    loss = mean_j [ logsumexp(z_j) - z_j[y_j] ]
+    gelu(a) = a * Phi(a) = 0.5 a (1 + erf(a / sqrt 2))     (exact GELU)
+
+with the analytic gradients of that loss, and one Adam step
+    m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
+    p <- p - lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+Parameters are kept as a dict of float64 arrays.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+_SQRT2 = math.sqrt(2.0)
+_INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
+
+PARAM_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def gelu(a):
+    return 0.5 * a * (1.0 + erf(a / _SQRT2))
+
+
+def gelu_grad(a):
+    """d/da [a Phi(a)] = Phi(a) + a phi(a)."""
+    return 0.5 * (1.0 + erf(a / _SQRT2)) + a * _INV_SQRT_2PI * np.exp(-0.5 * a * a)
+
+
+def init_params(dims, seed: int) -> dict:
+    """He-normal weights (std sqrt(2 / fan_in)), zero biases."""
+    k, h1, h2, c = dims
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.standard_normal((h1, k)) * math.sqrt(2.0 / k), "b1": np.zeros(h1),
+        "W2": rng.standard_normal((h2, h1)) * math.sqrt(2.0 / h1), "b2": np.zeros(h2),
+        "W3": rng.standard_normal((c, h2)) * math.sqrt(2.0 / h2), "b3": np.zeros(c),
+    }
+
+
+def forward(p: dict, x: np.ndarray):
+    x = np.asarray(x, np.float64)
+    a1 = x @ p["W1"].T + p["b1"]
+    h1 = gelu(a1)
+    a2 = h1 @ p["W2"].T + p["b2"]
+    h2 = gelu(a2)
+    z = h2 @ p["W3"].T + p["b3"]
+    return z, (x, a1, h1, a2, h2)
+
+
+def loss_and_grads(p: dict, x: np.ndarray, y: np.ndarray):
+    """Mean softmax cross-entropy over the batch and its gradient for every parameter."""
+    z, (x, a1, h1, a2, h2) = forward(p, x)
+    b = z.shape[0]
+    zmax = z.max(axis=1, keepdims=True)
+    e = np.exp(z - zmax)
+    s = e.sum(axis=1, keepdims=True)
+    lse = zmax[:, 0] + np.log(s[:, 0])
+    loss = float(np.mean(lse - z[np.arange(b), y]))
+    dz = e / s
+    dz[np.arange(b), y] -= 1.0
+    dz /= b
+    g = {"W3": dz.T @ h2, "b3": dz.sum(axis=0)}
+    dh2 = dz @ p["W3"]
+    da2 = dh2 * gelu_grad(a2)
+    g["W2"] = da2.T @ h1
+    g["b2"] = da2.sum(axis=0)
+    dh1 = da2 @ p["W2"]
+    da1 = dh1 * gelu_grad(a1)
+    g["W1"] = da1.T @ x
+    g["b1"] = da1.sum(axis=0)
+    return loss, g
+
+
+def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8) -> None:
+    for k in PARAM_ORDER:
+        m[k] = b1 * m[k] + (1 - b1) * g[k]
+        v[k] = b2 * v[k] + (1 - b2) * g[k] * g[k]
+        mh = m[k] / (1 - b1 ** t)
+        vh = v[k] / (1 - b2 ** t)
+        p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def topk(z: np.ndarray, k: int) -> np.ndarray:
+    """Indices of the k largest scores per row, by (score desc, index asc)."""
+    order = np.lexsort((np.broadcast_to(np.arange(z.shape[1]), z.shape), -z), axis=1)
+    return order[:, :k]
+
+
+def flatten(p: dict) -> np.ndarray:
+    return np.concatenate([p[k].ravel() for k in PARAM_ORDER])
+
+
+def unflatten(flat: np.ndarray, dims) -> dict:
+    k, h1, h2, c = dims
+    shapes = {"W1": (h1, k), "b1": (h1,), "W2": (h2, h1), "b2": (h2,), "W3": (c, h2), "b3": (c,)}
+    out, o = {}, 0
+    for name in PARAM_ORDER:
+        n = int(np.prod(shapes[name]))
+        out[name] = np.asarray(flat[o:o + n], np.float64).reshape(shapes[name])
+        o += n
+    return out
+
+
+def n_params(dims) -> int:
+    k, h1, h2, c = dims
+    return h1 * k + h1 + h2 * h1 + h2 + c * h2 + c

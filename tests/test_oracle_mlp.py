@@ -1,0 +1,94 @@
+"""Pins of the binary64 MLP oracle (the learned block proposal).
+
+The analytic gradient is checked against central finite differences of the
+loss (independent of the backward formulas), the loss against closed forms,
+GELU against its definition via math.erf, and Adam's first step against its
+closed form (lr * sign(g))."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_gelu_definition_and_derivative():
+    a = np.linspace(-6, 6, 121)
+    want = np.array([0.5 * t * (1 + math.erf(t / math.sqrt(2))) for t in a])
+    assert np.max(np.abs(mlp.gelu(a) - want)) < 1e-15
+    h = 1e-6
+    fd = (mlp.gelu(a + h) - mlp.gelu(a - h)) / (2 * h)
+    assert np.max(np.abs(mlp.gelu_grad(a) - fd)) < 1e-8
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0 and abs(mlp.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+
+
+def test_loss_uniform_logits_is_log_classes():
+    dims = (4, 6, 5, 7)
+    p = mlp.init_params(dims, 0)
+    for k in ("W3", "b3"):
+        p[k][:] = 0.0
+    x = np.random.default_rng(1).standard_normal((9, 4))
+    y = np.arange(9) % 7
+    loss, g = mlp.loss_and_grads(p, x, y)
+    assert abs(loss - math.log(7)) < 1e-14
+    # with W3 = 0 no gradient reaches the hidden layers
+    assert np.all(g["W1"] == 0) and np.all(g["W2"] == 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gradient_matches_finite_differences(seed):
+    dims = (5, 7, 6, 9)
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(dims, seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.3
+    x = rng.standard_normal((6, 5))
+    y = rng.integers(0, 9, 6)
+    _, g = mlp.loss_and_grads(p, x, y)
+    flat = mlp.flatten(p)
+    gflat = mlp.flatten(g)
+    h = 1e-6
+    idx = rng.choice(flat.size, 60, replace=False)
+    for i in idx:
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        lp, _ = mlp.loss_and_grads(mlp.unflatten(fp, dims), x, y)
+        lm, _ = mlp.loss_and_grads(mlp.unflatten(fm, dims), x, y)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, gflat[i])
+
+
+def test_adam_first_step_is_lr_sign():
+    dims = (3, 4, 4, 5)
+    p = mlp.init_params(dims, 3)
+    rng = np.random.default_rng(4)
+    g = {k: rng.standard_normal(v.shape) for k, v in p.items()}
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    p0 = {k: v.copy() for k, v in p.items()}
+    mlp.adam_step(p, g, m, v, t=1, lr=1e-3, eps=0.0)
+    for k in p:
+        assert np.allclose(p[k] - p0[k], -1e-3 * np.sign(g[k]), rtol=0, atol=1e-15)
+
+
+def test_topk_ties_by_index():
+    z = np.array([[1.0, 3.0, 3.0, 2.0, 3.0]])
+    assert list(mlp.topk(z, 3)[0]) == [1, 2, 4]
+
+
+def test_training_reduces_loss_on_separable_toy():
+    dims = (2, 16, 16, 4)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((256, 2))
+    y = (x[:, 0] > 0).astype(int) * 2 + (x[:, 1] > 0).astype(int)
+    p = mlp.init_params(dims, 6)
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v = {k: np.zeros_like(v) for k, v in p.items()}
+    l0, _ = mlp.loss_and_grads(p, x, y)
+    for t in range(1, 301):
+        _, g = mlp.loss_and_grads(p, x, y)
+        mlp.adam_step(p, g, m, v, t, lr=1e-2)
+    l1, _ = mlp.loss_and_grads(p, x, y)
+    z, _ = mlp.forward(p, x)
+    assert l1 < 0.2 * l0 and np.mean(np.argmax(z, 1) == y) > 0.95

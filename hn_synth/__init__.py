@@ -107,6 +107,16 @@ def _add_scaled(db: np.ndarray, cen: np.ndarray, centre_of: np.ndarray, s: np.fl
             list(ex.map(work, starts))
 
 
+def queries_from(db_raw: np.ndarray, nq: int, seed: int, query_noise: float = 0.10) -> tuple[np.ndarray, np.ndarray]:
+    """nq raw queries drawn like make_workload's (a random raw entry plus noise), from
+    streams of their own (e.g. training queries for the block proposal)."""
+    src = _gen(seed, _S_QPICK + 32).integers(0, db_raw.shape[0], size=nq, dtype=np.int64)
+    q = _normal_rows(seed, _S_QNOISE + 32, nq)
+    q *= np.float32(query_noise)
+    q += db_raw[src]
+    return q, src
+
+
 def uniform_queries(seed: int, nq: int) -> np.ndarray:
     """Unclustered standard-normal raw queries (no source entry), e.g. for training sets."""
     return _normal_rows(seed, _S_QNOISE + 16, nq)

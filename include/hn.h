@@ -63,14 +63,23 @@ typedef enum hn_scan {
 
 typedef struct hn_index_opts {
     int32_t prefix;       /* hn_prefix; default HN_PREFIX_F32 */
-    int32_t reserved[7];  /* must be zero */
+    int32_t n_blocks;     /* > 0: partition the entries into this many blocks for the learned
+                             proposal (1 <= n_blocks <= min(n, 2^20)); 0: no blocks */
+    int32_t kmeans_iters; /* Lloyd iterations of the block partition; 0 = 8 */
+    uint32_t seed;        /* reserved for partition seeding; currently unused, may be 0 */
+    int32_t reserved[4];  /* must be zero */
 } hn_index_opts;
+
+typedef struct hn_proposal hn_proposal;
 
 typedef struct hn_search_opts {
     int32_t scan;         /* hn_scan; default HN_SCAN_AUTO */
     int32_t bucket_cap;   /* survivor slots per query; 0 = library default (grown on overflow) */
     int32_t timing;       /* non-zero: time each step with CUDA events on `stream` (fills stats->ms_*) */
-    int32_t reserved[5];  /* must be zero */
+    int32_t seed_topk;    /* blocks the proposal contributes per query (with `seed`); 0 = 4 */
+    const hn_proposal *seed; /* NULL: plain search.  Otherwise the proposal's top blocks give the
+                                threshold and the Phase-1 scan is skipped (result unchanged) */
+    int32_t reserved[2];  /* must be zero */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */
@@ -86,8 +95,8 @@ typedef struct hn_search_stats {
     int32_t reserved;
     /* device time of each step of the last run, milliseconds (with opts->timing) */
     float ms_prep;          /* query prefix packing and slack computation */
-    float ms_phase1;        /* Phase-1 prefix scan (best prefix score per query) */
-    float ms_threshold;     /* full score of the Phase-1 winner -> threshold */
+    float ms_phase1;        /* Phase-1 prefix scan, or the proposal's inference when seeded */
+    float ms_threshold;     /* full score of the Phase-1 (or proposed) candidates -> threshold */
     float ms_phase2;        /* Phase-2 prefix scan with the bound test */
     float ms_rescore;       /* survivor rescore, binary64 near-ties, argmax */
     float ms_total;         /* whole search */
@@ -104,7 +113,28 @@ typedef struct hn_index_info {
     float major_norm_max;   /* max_i |x_i,major|, rounded up */
     float resid_norm_max;   /* max_i |x_i,major - prefix_i| (0 for HN_PREFIX_F32), rounded up */
     float prefix_norm_max;  /* max_i |prefix_i|, rounded up */
+    int32_t n_blocks;       /* block partition size (0: none) */
+    int32_t reserved;
 } hn_index_info;
+
+/* Options of hn_proposal_train (zero fields take the defaults in brackets). */
+typedef struct hn_train_opts {
+    int32_t hidden1, hidden2;   /* hidden widths [256, 256] */
+    int32_t epochs;             /* passes over the pairs [4] */
+    int32_t batch;              /* mini-batch rows [4096] */
+    float lr;                   /* Adam learning rate [1e-3]; beta1 0.9, beta2 0.999, eps 1e-8 */
+    uint32_t seed;              /* initial weights and shuffling [0] */
+    const hn_proposal *init;    /* non-NULL: continue training this network (weights, Adam state) */
+    int32_t reserved[2];        /* must be zero */
+} hn_train_opts;
+
+typedef struct hn_proposal_info {
+    int32_t k, hidden1, hidden2, n_blocks;
+    int64_t n_params;
+    int64_t steps;              /* Adam steps taken so far */
+    int32_t epochs;             /* epochs trained so far */
+    float last_loss;            /* mean cross-entropy of the last training batch */
+} hn_proposal_info;
 
 typedef struct hn_index hn_index;
 
@@ -166,6 +196,52 @@ hn_status hn_index_get_info(const hn_index *index, hn_index_info *info);
  */
 hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts,
                           int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
+
+/*
+ * Block partition of an index built with opts.n_blocks > 0 (device arrays, may be NULL):
+ * block_start[n_blocks + 1] (block b = sorted positions [start[b], start[b+1])),
+ * block_ids[n] (entry ids in block order), block_of[n] (block of each entry).
+ * Entries are sorted by nearest centre of a spherical k-means over the major
+ * prefixes, then cut into equal contiguous blocks.  Does not synchronise.
+ */
+hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *block_ids, int32_t *block_of,
+                          void *stream);
+
+/*
+ * Learned block proposal (an extension that seeds the threshold of Algorithm 1;
+ * the paper has no network).  An MLP  K -> hidden1 -> hidden2 -> n_blocks with
+ * exact GELU maps a query's major prefix to block scores; it is trained with
+ * softmax cross-entropy and Adam by this library's kernels on pairs
+ * (train_q[j], block of its nearest neighbour).  nn_block (npairs int32, device)
+ * gives the labels; NULL labels them with hn_search_batch (exact).
+ * train_q: npairs x 128 HN-normalised float32 (device).  Synchronises `stream`.
+ * Training runs in FP32 with FP32 master weights; inference uses the weights
+ * rounded to BF16 with FP32 accumulation.
+ */
+hn_status hn_proposal_train(const hn_index *index, const float *train_q, const int32_t *nn_block, int64_t npairs,
+                            const hn_train_opts *opts, hn_proposal **out, void *stream);
+
+/* Top-k blocks per query (out_blocks: nq x topk int32, device), by (score desc, block asc). */
+hn_status hn_proposal_infer(const hn_proposal *proposal, const float *q, int64_t nq, int32_t topk,
+                            int32_t *out_blocks, void *stream);
+
+hn_status hn_proposal_get_info(const hn_proposal *proposal, hn_proposal_info *info);
+
+/* Checkpoint: weights and Adam state in a flat binary file with a header. Synchronous. */
+hn_status hn_proposal_save(const hn_proposal *proposal, const char *path);
+hn_status hn_proposal_load(const char *path, hn_proposal **out);
+hn_status hn_proposal_destroy(hn_proposal *proposal);
+
+/*
+ * Verification entry point of the proposal's training kernels: mean softmax
+ * cross-entropy of a batch and its gradient w.r.t. all parameters, computed by
+ * the same forward and backward kernels hn_proposal_train uses.  params and
+ * grads: [W1 (h1 x k), b1, W2 (h2 x h1), b2, W3 (c x h2), b3] float32 (device);
+ * x: batch x k, y: batch int32 labels in [0, c).  *loss is written on the host.
+ * Synchronises `stream`.
+ */
+hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
+                           const int32_t *y, int32_t batch, float *loss, float *grads, void *stream);
 
 /*
  * Brute-force baseline (the denominator of the paper's speed-ups, §6.2): the

@@ -70,6 +70,9 @@ static void free_index(Index *ix) {
     cudaFree(ix->pre16);
     cudaFree(ix->mx);
     cudaFree(ix->dev_max);
+    cudaFree(ix->block_ids);
+    cudaFree(ix->block_of);
+    cudaFree(ix->block_start);
     delete ix;
 }
 
@@ -150,8 +153,11 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     hn_index_opts o{};
     if (opts) o = *opts;
     if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16) return fail(HN_ERR_INVALID_ARG, "bad prefix type");
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 4; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.n_blocks < 0 || o.n_blocks > n || o.n_blocks > (1 << 20))
+        return fail(HN_ERR_INVALID_ARG, "need 0 <= n_blocks <= min(n, 2^20)");
+    if (o.kmeans_iters < 0 || o.kmeans_iters > 1000) return fail(HN_ERR_INVALID_ARG, "need 0 <= kmeans_iters <= 1000");
     cudaStream_t s = (cudaStream_t)stream;
     hn_index *h = new hn_index();
     Index &ix = h->ix;
@@ -200,6 +206,14 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         hn_index_destroy(h);
         return fail(HN_ERR_NOT_NORMALIZED, "entry " + std::to_string(row) + " violates the HN norm identities");
     }
+    if (o.n_blocks > 0) {
+        e = build_blocks(ix, o.n_blocks, o.kmeans_iters ? o.kmeans_iters : 8, s);
+        if (e != cudaSuccess) {
+            hn_index_destroy(h);
+            return cuda_fail(e, "block partition");
+        }
+        ix.bytes += (int64_t)(2 * n + o.n_blocks + 1) * 4;
+    }
     *out = h;
     return HN_OK;
 }
@@ -226,22 +240,48 @@ hn_status hn_index_get_info(const hn_index *index, hn_index_info *info) {
     info->major_norm_max = ix.host_max[1];
     info->resid_norm_max = ix.host_max[2];
     info->prefix_norm_max = ix.host_max[3];
+    info->n_blocks = ix.n_blocks;
+    info->reserved = 0;
+    return HN_OK;
+}
+
+hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *block_ids, int32_t *block_of,
+                          void *stream) {
+    if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
+    const Index &ix = index->ix;
+    if (ix.n_blocks <= 0) return fail(HN_ERR_INVALID_ARG, "the index has no block partition");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (block_start)
+        HN_CUDA(cudaMemcpyAsync(block_start, ix.block_start, sizeof(int32_t) * (ix.n_blocks + 1),
+                                cudaMemcpyDeviceToDevice, s));
+    if (block_ids) HN_CUDA(cudaMemcpyAsync(block_ids, ix.block_ids, sizeof(int32_t) * ix.n, cudaMemcpyDeviceToDevice, s));
+    if (block_of) HN_CUDA(cudaMemcpyAsync(block_of, ix.block_of, sizeof(int32_t) * ix.n, cudaMemcpyDeviceToDevice, s));
     return HN_OK;
 }
 
 // One run of the search pipeline (Algorithm 1 on the GPU); 5 kernel launches.
 // With `timing`, events ev[0..5] bracket the steps on stream s.
-static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, int64_t *out_idx, double *out_sim,
-                            bool timing, cudaStream_t s) {
+// With a proposal (`seed`), its top blocks give the threshold and Phase 1 is skipped.
+static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
+                            int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s) {
     Workspace &ws = ix.ws;
     auto mark = [&](int i) { return timing ? cudaEventRecord(ws.ev[i], s) : cudaSuccess; };
     HN_CUDA(cudaMemsetAsync(ws.key1, 0, sizeof(unsigned long long) * nq, s));
     HN_CUDA(mark(0));
     HN_CUDA(launch_query_prep(ix, q, nq, s));
     HN_CUDA(mark(1));
-    HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s) : launch_stream_scan(ix, nq, 1, s));
-    HN_CUDA(mark(2));
-    HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, s));
+    if (seed) {
+        int32_t *blocks = nullptr;
+        hn_proposal *sp = const_cast<hn_proposal *>(seed);
+        HN_CUDA(proposal_scratch(sp, nq * topk, &blocks));
+        HN_CUDA(proposal_topk(sp, q, nq, topk, blocks, s));
+        HN_CUDA(mark(2));
+        HN_CUDA(launch_seed_blocks(ix, q, nq, blocks, topk, s));
+    } else {
+        HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s) : launch_stream_scan(ix, nq, 1, s));
+        HN_CUDA(mark(2));
+        HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, s));
+    }
     HN_CUDA(mark(3));
     HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
     HN_CUDA(mark(4));
@@ -257,9 +297,15 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     if (nq < 0 || nq > (int64_t)1 << 30) return fail(HN_ERR_INVALID_ARG, "need 0 <= nq <= 2^30");
     hn_search_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (o.bucket_cap < 0) return fail(HN_ERR_INVALID_ARG, "bucket_cap < 0");
+    const int topk = o.seed_topk ? o.seed_topk : 4;
+    if (o.seed) {
+        if (proposal_blocks(o.seed) != ix.n_blocks || proposal_k(o.seed) != ix.k)
+            return fail(HN_ERR_INVALID_ARG, "the proposal was not trained for this index's blocks");
+        if (topk < 1 || topk > 64 || topk > ix.n_blocks) return fail(HN_ERR_INVALID_ARG, "need 1 <= seed_topk <= 64");
+    }
     int scan = o.scan;
     if (scan == HN_SCAN_AUTO) scan = (ix.prefix == HN_PREFIX_BF16 && nq >= 1024 && dense_scan_supported(ix)) ? HN_SCAN_DENSE : HN_SCAN_STREAM;
     if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
@@ -300,9 +346,9 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
         }
         HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
         HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
-        st = run_search(ix, q, nq, scan, out_idx, out_sim, timing, s);
+        st = run_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s);
         if (st != HN_OK) return st;
-        kernels += 5;
+        kernels += o.seed ? 4 + 5 * (int32_t)((nq + 8191) / 8192) : 5;
         HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
         HN_CUDA(cudaStreamSynchronize(s));

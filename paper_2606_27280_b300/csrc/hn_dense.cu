@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             const bool qvalid = q < p.nq;
             const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
             float best = -INFINITY;
-            int64_t bseg = -1;
+            int32_t bseg = -1;
             int lc = 0;
             // Phase 2: move this thread's staged survivors to its query's slots
             auto flush = [&]() {
@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                     if (slot + j < p.cap) p.bucket[q * p.cap + slot + j] = (int32_t)sbuf[j * 512 + et];
                 lc = 0;
             };
-            for (int64_t t = t0; t < t1; ++t) {
+            // entry ids fit in 32 bits (n < 2^31 - 256 is enforced by hn_index_build)
+            const int32_t n32 = (int32_t)p.n;
+            for (int32_t t = (int32_t)t0; t < (int32_t)t1; ++t) {
                 if (!(ok = mbar_wait(smem_u32(&acc_full[acc]), accphase, abort_flag, kWaitLimitNs))) break;
                 tc_fence_after();
                 float v[64];
@@ -218,11 +220,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 if (++acc == 2) { acc = 0; accphase ^= 1; }
                 float g[4];
                 const float m = max_tree64(v, g);
-                const int64_t e0 = t * kTileE + seg * 64;
+                const int32_t e0 = t * kTileE + seg * 64;
                 if (PHASE == 1) {
                     // running best score and the 64-entry segment holding it; the entry
                     // itself is recovered by the threshold kernel
-                    if (m > best && e0 < p.n) { best = m; bseg = t * 4 + seg; }
+                    if (m > best && e0 < n32) { best = m; bseg = t * 4 + seg; }
                 } else if (m >= thr) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -230,8 +232,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                             uint32_t mask = 0;
 #pragma unroll
                             for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
-                            const int64_t ek = e0 + 16 * k;
-                            if (ek + 16 > p.n) mask &= ek >= p.n ? 0u : ((1u << (uint32_t)(p.n - ek)) - 1u);
+                            const int32_t ek = e0 + 16 * k;
+                            if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
                             if (lc + __popc(mask) > kLcap) flush();
                             while (mask) {
                                 const int i = __ffs(mask) - 1;

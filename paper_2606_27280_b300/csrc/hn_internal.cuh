@@ -53,8 +53,6 @@ __host__ __device__ inline uint32_t best_idx(unsigned long long k) {
 __host__ __device__ inline float best_score(unsigned long long k) { return key2f((uint32_t)(k >> 32)); }
 
 // ---------------------------------------------------------------- index
-struct QueryPrep;  // per-search query-side arrays (hn_search.cu)
-
 struct Workspace {
     // per-query scratch, sized for `q_cap` queries and `bucket_cap` survivors each
     int64_t q_cap = 0;
@@ -92,6 +90,10 @@ struct Index {
     float *mx = nullptr;             // [n] |x_minor| rounded up
     float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
+    int32_t n_blocks = 0;            // block partition for the learned proposal (0 = none)
+    int32_t *block_ids = nullptr;    // [n] entry ids in block order
+    int32_t *block_of = nullptr;     // [n] block of each entry
+    int32_t *block_start = nullptr;  // [n_blocks + 1]
     int64_t bytes = 0;
     Workspace ws;
 };
@@ -129,6 +131,14 @@ cudaError_t launch_bruteforce_keys(const Index &ix, const float *q, int64_t nq, 
 // Device state of a built index (used by entry points outside hn_api.cu).
 const Index *index_state(const hn_index *h);
 bool dense_scan_supported(const Index &ix);
+cudaError_t build_blocks(Index &ix, int n_blocks, int iters, cudaStream_t s);
+cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
+                               cudaStream_t s);
+// proposal helpers (hn_mlp.cu)
+cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, cudaStream_t s);
+cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);
+int32_t proposal_blocks(const hn_proposal *p);
+int32_t proposal_k(const hn_proposal *p);
 int64_t dense_cand_slots(const Index &ix, int64_t nq);
 
 }  // namespace hn

@@ -277,6 +277,80 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
     if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
 }
 
+// Threshold from the learned proposal: for each of the query's top-k blocks, the
+// entry of best prefix score (FP32 FMA over the stored prefix, lowest id on
+// ties) is scored in full; T_q and tau_q follow as for the Phase-1 candidates.
+__global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ rows, const float *__restrict__ q,
+                                                     int64_t nq, const float *__restrict__ pre32,
+                                                     const __nv_bfloat16 *__restrict__ pre16, int kp,
+                                                     const float *__restrict__ qpre32, const int32_t *__restrict__ blocks,
+                                                     int topk, const int32_t *__restrict__ block_start,
+                                                     const int32_t *__restrict__ block_ids, const float *__restrict__ qeps,
+                                                     const float *__restrict__ qnorm, float xnorm_max,
+                                                     float *__restrict__ tau, int32_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    if (lane == 0) count[j] = 0;
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float *qp = qpre32 + j * kp;
+    const float eps_r = rescore_eps(qnorm[j], xnorm_max);
+    float t_low = -INFINITY;
+    for (int r = 0; r < topk; ++r) {
+        const int32_t b = blocks[j * topk + r];
+        unsigned long long kb = 0;
+        for (int32_t p = block_start[b] + lane; p < block_start[b + 1]; p += 32) {
+            const int32_t e = block_ids[p];
+            float sc;
+            if (pre16) {
+                sc = prefix_score16(pre16, e, qp, kp);
+            } else {
+                sc = 0.f;
+                const float *xe = pre32 + (int64_t)e * kp;
+                for (int c = 0; c < kp; ++c) sc = fmaf(qp[c], xe[c], sc);
+            }
+            const unsigned long long kk = pack_best(sc, (uint32_t)e);
+            kb = kk > kb ? kk : kb;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, kb, o);
+            kb = other > kb ? other : kb;
+        }
+        if (kb == 0ull) continue;
+        const float4 xv = reinterpret_cast<const float4 *>(rows + (int64_t)best_idx(kb) * kD)[lane];
+        const float sim = warp_sum_f(fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w))));
+        t_low = fmaxf(t_low, __fsub_rd(sim, eps_r));
+    }
+    if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+}
+
+cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
+                               cudaStream_t st) {
+    const Workspace &ws = ix.ws;
+    const int64_t gblocks = (nq * 32 + 255) / 256;
+    const bool bf = ix.prefix == HN_PREFIX_BF16;
+    k_seed_blocks<<<(unsigned)gblocks, 256, 0, st>>>(ix.rows, q, nq, bf ? nullptr : ix.pre32, bf ? ix.pre16 : nullptr,
+                                                     bf ? ix.k_pad16 : ix.k_pad4, ws.qpre32, blocks, topk,
+                                                     ix.block_start, ix.block_ids, ws.qeps, ws.qnorm, ix.host_max[4],
+                                                     ws.tau, ws.count);
+    return cudaGetLastError();
+}
+
+// Phase-1 argmax of the stream scan over explicit FP32 arrays (k-means assignment).
+cudaError_t stream_argmax_f32(const float *db_pre, int64_t n_db, int64_t n_db_tiles, int kp, const float *q_pre,
+                              int64_t nq, unsigned long long *keys, cudaStream_t st) {
+    Workspace w{};
+    w.key1 = keys;
+    switch (kp) {
+        case 8: return stream_scan_kt<8, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 16: return stream_scan_kt<16, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 32: return stream_scan_kt<32, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 64: return stream_scan_kt<64, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, cudaStream_t st) {
     const Workspace &ws = ix.ws;
     const int64_t blocks = (nq * 32 + 255) / 256;

@@ -27,12 +27,25 @@ _STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_INVALID_ARG", 2: "HN_ERR_NOT_NORMALIZED"
 
 
 class IndexOpts(ctypes.Structure):
-    _fields_ = [("prefix", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("prefix", ctypes.c_int32), ("n_blocks", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
+                ("seed", ctypes.c_uint32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class SearchOpts(ctypes.Structure):
     _fields_ = [("scan", ctypes.c_int32), ("bucket_cap", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("hidden1", ctypes.c_int32), ("hidden2", ctypes.c_int32), ("epochs", ctypes.c_int32),
+                ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint32),
+                ("init", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
+
+
+class ProposalInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("hidden1", ctypes.c_int32), ("hidden2", ctypes.c_int32),
+                ("n_blocks", ctypes.c_int32), ("n_params", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("epochs", ctypes.c_int32), ("last_loss", ctypes.c_float)]
 
 
 class SearchStats(ctypes.Structure):
@@ -50,7 +63,8 @@ class IndexInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("prefix", ctypes.c_int32), ("k_pad", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("minor_norm_max", ctypes.c_float), ("major_norm_max", ctypes.c_float),
-                ("resid_norm_max", ctypes.c_float), ("prefix_norm_max", ctypes.c_float)]
+                ("resid_norm_max", ctypes.c_float), ("prefix_norm_max", ctypes.c_float),
+                ("n_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # exported symbol -> (argtypes, restype); the ABI test checks these against include/hn.h
@@ -64,6 +78,14 @@ SIGNATURES = {
     "hn_index_get_info": ([_vp, _vp], _i32),
     "hn_search_batch": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hn_index_blocks": ([_vp, _vp, _vp, _vp, _vp], _i32),
+    "hn_proposal_train": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hn_proposal_infer": ([_vp, _vp, _i64, _i32, _vp, _vp], _i32),
+    "hn_proposal_get_info": ([_vp, _vp], _i32),
+    "hn_proposal_save": ([_vp, ctypes.c_char_p], _i32),
+    "hn_proposal_load": ([ctypes.c_char_p, _vp], _i32),
+    "hn_proposal_destroy": ([_vp], _i32),
+    "hn_mlp_loss_grad": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
     "hn_bruteforce_static": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
 }
 STATIC_MAX_QUERIES = 65536
@@ -137,10 +159,11 @@ class SearchResult:
 class Index:
     """Owning handle of an hn_index (device memory held by libhn)."""
 
-    def __init__(self, x: torch.Tensor, k: int, alpha: float, prefix: int = PREFIX_F32, stream=None):
+    def __init__(self, x: torch.Tensor, k: int, alpha: float, prefix: int = PREFIX_F32, n_blocks: int = 0,
+                 kmeans_iters: int = 0, stream=None):
         x = _dev_f32(x, "x")
         self._h = ctypes.c_void_p()
-        opts = IndexOpts(prefix=int(prefix))
+        opts = IndexOpts(prefix=int(prefix), n_blocks=int(n_blocks), kmeans_iters=int(kmeans_iters))
         _check(_lib.hn_index_build(x.data_ptr(), x.shape[0], D, int(k), float(alpha), ctypes.byref(opts),
                                    ctypes.byref(self._h), _stream(stream)), "hn_index_build")
         self.k, self.alpha, self.prefix, self.n = int(k), float(alpha), int(prefix), x.shape[0]
@@ -167,18 +190,32 @@ class Index:
         _check(_lib.hn_index_get_info(self._h, ctypes.byref(inf)), "hn_index_get_info")
         return {name: getattr(inf, name) for name, _ in inf._fields_}
 
+    def blocks(self, stream=None):
+        """(block_start [B+1], block_ids [n], block_of [n]) int32 device tensors."""
+        b = self.info()["n_blocks"]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        start = torch.empty(b + 1, dtype=torch.int32, device=dev)
+        ids = torch.empty(self.n, dtype=torch.int32, device=dev)
+        of = torch.empty(self.n, dtype=torch.int32, device=dev)
+        _check(_lib.hn_index_blocks(self._h, start.data_ptr(), ids.data_ptr(), of.data_ptr(), _stream(stream)),
+               "hn_index_blocks")
+        return start, ids, of
+
     def search(self, q: torch.Tensor, scan: int = SCAN_AUTO, bucket_cap: int = 0, stats: bool = False,
                timing: bool = False,
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
+               proposal: "Proposal | None" = None, seed_topk: int = 0,
                stream=None) -> SearchResult:
-        """Exact 1-NN of every row of q (HN-normalised, float32, device)."""
+        """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
+        `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         if out_idx is None:
             out_idx = torch.empty(nq, dtype=torch.int64, device=q.device)
         if out_sim is None:
             out_sim = torch.empty(nq, dtype=torch.float64, device=q.device)
-        opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), timing=int(bool(timing)))
+        opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), timing=int(bool(timing)),
+                          seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None)
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),
                                     out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
@@ -194,3 +231,80 @@ class Index:
         _check(_lib.hn_bruteforce(self._h, q.data_ptr(), nq, out_idx.data_ptr(), out_sim.data_ptr(),
                                   _stream(stream)), "hn_bruteforce")
         return SearchResult(out_idx, out_sim, None)
+
+
+class Proposal:
+    """Owning handle of an hn_proposal: the learned block proposal MLP."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @classmethod
+    def train(cls, index: Index, train_q: torch.Tensor, labels: torch.Tensor | None = None, hidden1: int = 0,
+              hidden2: int = 0, epochs: int = 0, batch: int = 0, lr: float = 0.0, seed: int = 0,
+              init: "Proposal | None" = None, stream=None) -> "Proposal":
+        train_q = _dev_f32(train_q, "train_q")
+        if labels is not None:
+            if labels.dtype != torch.int32 or not labels.is_cuda or labels.numel() != train_q.shape[0]:
+                raise ValueError("labels must be a CUDA int32 tensor with one entry per query")
+            labels = labels.contiguous()
+        opts = TrainOpts(hidden1=hidden1, hidden2=hidden2, epochs=epochs, batch=batch, lr=lr, seed=seed,
+                         init=init._h.value if init is not None else None)
+        h = ctypes.c_void_p()
+        _check(_lib.hn_proposal_train(index._h, train_q.data_ptr(), labels.data_ptr() if labels is not None else None,
+                                      train_q.shape[0], ctypes.byref(opts), ctypes.byref(h), _stream(stream)),
+               "hn_proposal_train")
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str) -> "Proposal":
+        h = ctypes.c_void_p()
+        _check(_lib.hn_proposal_load(str(path).encode(), ctypes.byref(h)), "hn_proposal_load")
+        return cls(h)
+
+    def save(self, path: str) -> None:
+        _check(_lib.hn_proposal_save(self._h, str(path).encode()), "hn_proposal_save")
+
+    def info(self) -> dict:
+        inf = ProposalInfo()
+        _check(_lib.hn_proposal_get_info(self._h, ctypes.byref(inf)), "hn_proposal_get_info")
+        return {name: getattr(inf, name) for name, _ in inf._fields_}
+
+    def infer(self, q: torch.Tensor, topk: int, stream=None) -> torch.Tensor:
+        q = _dev_f32(q, "q")
+        out = torch.empty((q.shape[0], topk), dtype=torch.int32, device=q.device)
+        _check(_lib.hn_proposal_infer(self._h, q.data_ptr(), q.shape[0], int(topk), out.data_ptr(), _stream(stream)),
+               "hn_proposal_infer")
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.hn_proposal_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, stream=None):
+    """(mean cross-entropy, gradient) of the proposal MLP, from the library's training kernels."""
+    k, h1, h2, c = (int(v) for v in dims)
+    params = params.contiguous()
+    x = x.contiguous()
+    y = y.contiguous()
+    if params.dtype != torch.float32 or x.dtype != torch.float32 or y.dtype != torch.int32:
+        raise TypeError("params/x float32, y int32")
+    grads = torch.empty_like(params)
+    loss = ctypes.c_float()
+    _check(_lib.hn_mlp_loss_grad(params.data_ptr(), k, h1, h2, c, x.data_ptr(), y.data_ptr(), x.shape[0],
+                                 ctypes.byref(loss), grads.data_ptr(), _stream(stream)), "hn_mlp_loss_grad")
+    return loss.value, grads

@@ -42,7 +42,9 @@ def test_struct_sizes_match_header(hn):
     assert ctypes.sizeof(hn.IndexOpts) == 32
     assert ctypes.sizeof(hn.SearchOpts) == 32
     assert ctypes.sizeof(hn.SearchStats) == 80
-    assert ctypes.sizeof(hn.IndexInfo) == 56
+    assert ctypes.sizeof(hn.IndexInfo) == 64
+    assert ctypes.sizeof(hn.TrainOpts) == 40
+    assert ctypes.sizeof(hn.ProposalInfo) == 40
 
 
 def test_version(hn):

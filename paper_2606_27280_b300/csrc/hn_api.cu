@@ -43,6 +43,8 @@ static void free_ws(Workspace &ws) {
     cudaFree(ws.tau);
     cudaFree(ws.qpre32);
     cudaFree(ws.qpre16);
+    cudaFree(ws.qpre16h);
+    ws.qpre16h = nullptr;
     cudaFree(ws.qeps);
     cudaFree(ws.qnorm);
     ws.bucket = nullptr;
@@ -68,6 +70,7 @@ static void free_index(Index *ix) {
     cudaFree(ix->rows);
     cudaFree(ix->pre32);
     cudaFree(ix->pre16);
+    cudaFree(ix->pre16h);
     cudaFree(ix->mx);
     cudaFree(ix->dev_max);
     cudaFree(ix->block_ids);
@@ -90,6 +93,7 @@ static hn_status ensure_ws(Index &ix, int64_t nq, int32_t cap) {
     HN_CUDA(dalloc(&ws.tau, qc));
     HN_CUDA(dalloc(&ws.qpre32, (size_t)qc * ix.k_pad4));
     HN_CUDA(dalloc(&ws.qpre16, (size_t)qc * ix.k_pad16));
+    HN_CUDA(dalloc(&ws.qpre16h, (size_t)qc * ix.k_pad16));
     HN_CUDA(dalloc(&ws.qeps, qc));
     HN_CUDA(dalloc(&ws.qnorm, qc));
     ws.q_cap = qc;
@@ -184,6 +188,7 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         TRY(dalloc(&ix.pre32, (size_t)n_pad * ix.k_pad4));
     } else {
         TRY(dalloc(&ix.pre16, (size_t)n_pad * ix.k_pad16));
+        TRY(dalloc(&ix.pre16h, (size_t)n_pad * ix.k_pad16));
     }
     TRY(dalloc(&ix.mx, n));
     TRY(dalloc(&ix.dev_max, 8));
@@ -200,7 +205,7 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     TRY(cudaStreamSynchronize(s));
 #undef TRY
     ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
-               (ix.pre16 ? n_pad * ix.k_pad16 * 2 : 0) + n * 4;
+               (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) + n * 4;
     if (hs[ST_NOT_NORMALIZED]) {
         const int row = hs[ST_BAD_ROW];
         hn_index_destroy(h);

@@ -7,6 +7,11 @@
 // Products of two BF16 values are exact in FP32; the sum carries at most the
 // accumulation error bounded in the Phase-2 slack (hn_prep.cu).
 //
+// Phase 1 only looks for good threshold candidates (their full scores are
+// certified later), so it runs on an FP16 copy of the prefix with FP16
+// accumulation and reduces packed f16 pairs; Phase 2, the certified bound test,
+// runs on the BF16 prefix with FP32 accumulation.
+//
 // Persistent CTAs (one per SM, 10 warps):
 //   warp 0   producer: 1-D bulk copies of the query tile (once per work unit)
 //            and of each 8 KB entry tile into a ring of shared-memory stages;
@@ -35,8 +40,8 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
 struct DenseParams {
-    const __nv_bfloat16 *pre16;   // entries, UMMA core-matrix order, n_tiles * 256 rows
-    const __nv_bfloat16 *qpre16;  // queries, same order, n_qt * 128 rows
+    const void *pre;              // entries, UMMA core-matrix order, n_tiles * 256 rows (FP16 or BF16)
+    const void *qpre;             // queries, same order, n_qt * 128 rows
     int64_t n, n_tiles, nq;
     int64_t n_qt, tiles_per_chunk, n_units;
     const float *tau;
@@ -59,19 +64,26 @@ struct DenseCfg {
     static constexpr uint32_t kSmem = kBarOff + kBars * 8 + 16;
 };
 
-// Pairwise max tree over 64 scores (63 two-input max, depth 6, wide ILP):
-// g[k] = max of v[16k .. 16k+15], returns the max of all 64.
-__device__ __forceinline__ float max_tree64(const float (&v)[64], float (&g)[4]) {
-    float a[32], b[16], c[8];
+// Max of 16 consecutive scores, pairwise (15 two-input max, depth 4).
+__device__ __forceinline__ float max16(const float *v) {
+    float a[8], b[4];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = fmaxf(v[2 * i], v[2 * i + 1]);
+    for (int i = 0; i < 8; ++i) a[i] = fmaxf(v[2 * i], v[2 * i + 1]);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) b[i] = fmaxf(a[2 * i], a[2 * i + 1]);
+    for (int i = 0; i < 4; ++i) b[i] = fmaxf(a[2 * i], a[2 * i + 1]);
+    return fmaxf(fmaxf(b[0], b[1]), fmaxf(b[2], b[3]));
+}
+
+// Max of 64 f16 scores held as 32 packed pairs (31 packed max + 1), as a float.
+__device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
+    __half2 h[32];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) c[i] = fmaxf(b[2 * i], b[2 * i + 1]);
+    for (int i = 0; i < 32; ++i) h[i] = *reinterpret_cast<__half2 *>(&r[i]);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) g[i] = fmaxf(c[2 * i], c[2 * i + 1]);
-    return fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
+    for (int w = 16; w >= 1; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; ++i) h[i] = __hmax2(h[2 * i], h[2 * i + 1]);
+    return fmaxf(__low2float(h[0]), __high2float(h[0]));
 }
 
 template <int KP, int PHASE>
@@ -125,14 +137,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
                 if (!(ok = mbar_wait(smem_u32(&a_empty[abuf]), aphase ^ 1, abort_flag, kWaitLimitNs))) break;
                 mbar_arrive_expect_tx(smem_u32(&a_full[abuf]), C::kA);
-                bulk_g2s(smem_u32(sA + abuf * C::kA), p.qpre16 + qt * kTileQ * KP, C::kA, smem_u32(&a_full[abuf]));
+                bulk_g2s(smem_u32(sA + abuf * C::kA), static_cast<const char *>(p.qpre) + qt * C::kA, C::kA,
+                         smem_u32(&a_full[abuf]));
                 issued |= 1u << (24 + abuf);
                 last_par = (last_par & ~(1u << (24 + abuf))) | (aphase << (24 + abuf));
                 if (++abuf == 2) { abuf = 0; aphase ^= 1; }
                 for (int64_t t = t0; t < t1; ++t) {
                     if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, kWaitLimitNs))) break;
                     mbar_arrive_expect_tx(smem_u32(&b_full[stage]), C::kB);
-                    bulk_g2s(smem_u32(sB + stage * C::kB), p.pre16 + t * kTileE * KP, C::kB, smem_u32(&b_full[stage]));
+                    bulk_g2s(smem_u32(sB + stage * C::kB), static_cast<const char *>(p.pre) + t * C::kB, C::kB,
+                             smem_u32(&b_full[stage]));
                     issued |= 1u << stage;
                     last_par = (last_par & ~(1u << stage)) | (sphase << stage);
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
@@ -147,7 +161,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(kTileQ, kTileE);
+            // Phase 1: FP16 operands, FP16 accumulator; Phase 2: BF16 operands, FP32 accumulator
+            constexpr uint32_t idesc = PHASE == 1 ? idesc_f16_f16(kTileQ, kTileE) : idesc_bf16_f32(kTileQ, kTileE);
             uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, acc = 0, accphase = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
@@ -211,35 +226,46 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             for (int32_t t = (int32_t)t0; t < (int32_t)t1; ++t) {
                 if (!(ok = mbar_wait(smem_u32(&acc_full[acc]), accphase, abort_flag, kWaitLimitNs))) break;
                 tc_fence_after();
-                float v[64];
-                tmem_ld64(tmem + acc * kTileE + seg * 64 + lane_addr, v);
-                // the scores are in registers: hand the accumulator back to the MMA warp now
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
-                if (++acc == 2) { acc = 0; accphase ^= 1; }
-                float g[4];
-                const float m = max_tree64(v, g);
                 const int32_t e0 = t * kTileE + seg * 64;
                 if (PHASE == 1) {
+                    uint32_t r[32];
+                    tmem_ld64_f16(tmem + acc * kTileE + seg * 64 + lane_addr, r);
+                    // the scores are in registers: hand the accumulator back to the MMA warp now
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+                    if (++acc == 2) { acc = 0; accphase ^= 1; }
                     // running best score and the 64-entry segment holding it; the entry
                     // itself is recovered by the threshold kernel
+                    const float m = max64_f16(r);
                     if (m > best && e0 < n32) { best = m; bseg = t * 4 + seg; }
-                } else if (m >= thr) {
+                } else {
+                    float v[64];
+                    tmem_ld64(tmem + acc * kTileE + seg * 64 + lane_addr, v);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+                    if (++acc == 2) { acc = 0; accphase ^= 1; }
+                    float g[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (g[k] >= thr) {
-                            uint32_t mask = 0;
+                    for (int k = 0; k < 4; ++k) g[k] = max16(v + 16 * k);
+                    const float m = fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
+                    if (m >= thr) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
-                            const int32_t ek = e0 + 16 * k;
-                            if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
-                            if (lc + __popc(mask) > kLcap) flush();
-                            while (mask) {
-                                const int i = __ffs(mask) - 1;
-                                mask &= mask - 1;
-                                sbuf[lc * 512 + et] = (uint32_t)(ek + i);
-                                ++lc;
+                        for (int k = 0; k < 4; ++k) {
+                            if (g[k] >= thr) {
+                                uint32_t mask = 0;
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
+                                const int32_t ek = e0 + 16 * k;
+                                if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
+                                if (lc + __popc(mask) > kLcap) flush();
+                                while (mask) {
+                                    const int i = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    sbuf[lc * 512 + et] = (uint32_t)(ek + i);
+                                    ++lc;
+                                }
                             }
                         }
                     }
@@ -311,8 +337,8 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
     const Workspace &ws = ix.ws;
     DenseParams p{};
-    p.pre16 = ix.pre16;
-    p.qpre16 = ws.qpre16;
+    p.pre = phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
+    p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
     p.n = ix.n;
     p.n_tiles = ix.n_tiles;
     p.nq = nq;

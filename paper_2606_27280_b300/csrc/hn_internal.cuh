@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -66,6 +67,7 @@ struct Workspace {
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
     float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
     __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles
+    __half *qpre16h = nullptr;         // same in FP16 (dense Phase 1)
     float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
     float *qnorm = nullptr;            // [q_cap] |q| rounded up
     int32_t *status = nullptr;         // [8] device status words
@@ -87,6 +89,7 @@ struct Index {
     float *rows = nullptr;           // [n][128] FP32 master copy (full rescore)
     float *pre32 = nullptr;          // [n][k_pad4] FP32 prefix (HN_PREFIX_F32)
     __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
+    __half *pre16h = nullptr;        // FP16 copy of the same prefix (dense Phase 1 candidate search)
     float *mx = nullptr;             // [n] |x_minor| rounded up
     float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max

@@ -90,8 +90,8 @@ __device__ inline float4 bf16_round4(float4 v) {
 __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64_t n, int k, double alpha,
                                               int prefix, int k_pad4, int k_pad16, int64_t n_pad,
                                               float *__restrict__ rows, float *__restrict__ pre32,
-                                              __nv_bfloat16 *__restrict__ pre16, float *__restrict__ mx,
-                                              float *dev_max, int32_t *status) {
+                                              __nv_bfloat16 *__restrict__ pre16, __half *__restrict__ pre16h,
+                                              float *__restrict__ mx, float *dev_max, int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -130,6 +130,11 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             pk.x = *reinterpret_cast<uint32_t *>(&lo);
             pk.y = *reinterpret_cast<uint32_t *>(&hi);
             *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16) + pre16_offset(e, c0, k_pad16)) = pk;
+            __half2 hlo = __floats2half2_rn(pv[0], pv[1]), hhi = __floats2half2_rn(pv[2], pv[3]);
+            uint2 hk;
+            hk.x = *reinterpret_cast<uint32_t *>(&hlo);
+            hk.y = *reinterpret_cast<uint32_t *>(&hhi);
+            *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16h) + pre16_offset(e, c0, k_pad16)) = hk;
         }
         maj2 = warp_sum(maj2);
         min2 = warp_sum(min2);
@@ -168,7 +173,7 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
     int64_t blocks = (n_pad * 32 + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
     k_pack<<<(unsigned)blocks, 256, 0, st>>>(x, ix.n, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16, n_pad,
-                                             ix.rows, ix.pre32, ix.pre16, ix.mx, ix.dev_max, ix.ws.status);
+                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.mx, ix.dev_max, ix.ws.status);
     return cudaGetLastError();
 }
 
@@ -188,7 +193,8 @@ cudaError_t launch_check_hn(const float *, int64_t, int, double, int32_t *, cuda
 __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q, int64_t nq, int64_t nq_pad,
                                                     int k, double alpha, int prefix, int k_pad4, int k_pad16,
                                                     const float *__restrict__ dev_max, float *__restrict__ qpre32,
-                                                    __nv_bfloat16 *__restrict__ qpre16, float *__restrict__ qeps,
+                                                    __nv_bfloat16 *__restrict__ qpre16, __half *__restrict__ qpre16h,
+                                                    float *__restrict__ qeps,
                                                     float *__restrict__ qnorm, int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -221,6 +227,11 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         pk.x = *reinterpret_cast<uint32_t *>(&lo);
         pk.y = *reinterpret_cast<uint32_t *>(&hi);
         *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(qpre16) + pre16_offset(j, c0, k_pad16)) = pk;
+        __half2 hlo = __floats2half2_rn(pv[0], pv[1]), hhi = __floats2half2_rn(pv[2], pv[3]);
+        uint2 hk;
+        hk.x = *reinterpret_cast<uint32_t *>(&hlo);
+        hk.y = *reinterpret_cast<uint32_t *>(&hhi);
+        *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(qpre16h) + pre16_offset(j, c0, k_pad16)) = hk;
     }
     maj2 = warp_sum(maj2);
     min2 = warp_sum(min2);
@@ -248,7 +259,7 @@ cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaS
     const int64_t nq_pad = (nq + kTileQ - 1) / kTileQ * kTileQ;
     const int64_t blocks = (nq_pad * 32 + 255) / 256;
     k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
-                                                   ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qeps,
+                                                   ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
                                                    ix.ws.qnorm, ix.ws.status);
     return cudaGetLastError();
 }

@@ -181,9 +181,9 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // Algorithm 1, step 2, with more than one Phase-1 candidate.  Phase 1 leaves S
 // candidate keys (prefix score, id) per query: for the stream scan S = 1 and
 // the id is the best entry; for the dense scan S = 4 x chunks and the id names
-// a 64-entry segment (tile * 4 + segment) whose maximum prefix score is the key.
-// One warp per query takes the R best keys; for a segment it recomputes the 64
-// prefix scores from the stored prefixes (FP32 FMA) and keeps the best valid
+// a 64-entry segment (tile * 4 + segment) whose maximum (FP16) prefix score is
+// the key.  One warp per query takes the R best keys; for a segment it recomputes
+// the 64 prefix scores from the stored prefixes (FP32 FMA) and keeps the best valid
 // entry.  Each chosen entry is scored in full in FP32 (lane l owns dims
 // 4l..4l+3), and
 //   T_q = max_j RD(fp32_j - eps_r) <= max_j <q, x_j> (binary64, the oracle's value)

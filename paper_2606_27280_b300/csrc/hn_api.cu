@@ -82,7 +82,7 @@ static void free_index(Index *ix) {
 // Make the per-query scratch hold nq queries and `cap` survivor slots each.
 static hn_status ensure_ws(Index &ix, int64_t nq, int32_t cap) {
     Workspace &ws = ix.ws;
-    const int64_t nq_pad = (nq + kTileQ - 1) / kTileQ * kTileQ;
+    const int64_t nq_pad = (nq + kQPad - 1) / kQPad * kQPad;
     if (nq_pad <= ws.q_cap && cap <= ws.bucket_cap) return HN_OK;
     const int64_t qc = std::max(nq_pad, ws.q_cap);
     const int32_t bc = std::max(cap, ws.bucket_cap);
@@ -339,7 +339,7 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
         if (st != HN_OK) return st;
         if (scan == HN_SCAN_DENSE) {
             const int64_t slots = dense_cand_slots(ix, nq);
-            const int64_t need = ((nq + kTileQ - 1) / kTileQ * kTileQ) * slots;
+            const int64_t need = ((nq + kQPad - 1) / kQPad * kQPad) * slots;
             if (need > ws.cand_cap) {
                 cudaFree(ws.cand);
                 ws.cand = nullptr;

@@ -1,9 +1,11 @@
 // Dense prefix scan on the 5th-generation tensor cores (tcgen05), Phase 1 and
 // Phase 2 of Algorithm 1 (§3.3) for a BF16 major prefix.
 //
-// For a tile of 128 queries (A, K-major) and 256 database entries (B,
-// K-major) one tcgen05.mma per 16 prefix columns computes the 128 x 256 block
-// of prefix scores s~ = q^ . x^ with FP32 accumulation into tensor memory.
+// A work unit pairs 256 queries (two 128-row A tiles, K-major) with a stream
+// of 128-entry B tiles (K-major); per B tile two tcgen05.mma per 16 prefix
+// columns compute the 256 x 128 block of prefix scores s~ = q^ . x^ into tensor
+// memory.  Reusing every B tile for 256 queries halves the L2 -> shared-memory
+// traffic of 128-query tiles, which measured as the limiting stream.
 // Products of two BF16 values are exact in FP32; the sum carries at most the
 // accumulation error bounded in the Phase-2 slack (hn_prep.cu).
 //
@@ -12,12 +14,12 @@
 // accumulation and reduces packed f16 pairs; Phase 2, the certified bound test,
 // runs on the BF16 prefix with FP32 accumulation.
 //
-// Persistent CTAs (one per SM, 10 warps):
-//   warp 0   producer: 1-D bulk copies of the query tile (once per work unit)
-//            and of each 8 KB entry tile into a ring of shared-memory stages;
-//   warp 1   allocates 512 TMEM columns; one lane issues the MMAs into one of
-//            two 256-column accumulators and commits them to mbarriers;
-//   warps 2-17 epilogue (4 per SM sub-partition): TMEM -> registers (thread =
+// Persistent CTAs (one per SM, 19 warps):
+//   warp 0   producer: 1-D bulk copies of the 256-query unit (once per work unit)
+//            and of 16 KB stages of entry tiles into a ring in shared memory;
+//   warps 1-2 allocate 512 TMEM columns (warp 1); one lane each issues the MMAs of
+//            alternate tiles into its own 256-column accumulator and commits them;
+//   warps 3-18 epilogue (4 per SM sub-partition): TMEM -> registers (thread =
 //            query row, 64 accumulator columns per warp), one max tree, then
 //              Phase 1: running best score and its 64-entry segment per (query, chunk, segment);
 //              Phase 2: entries with s~ >= tau_q appended to q's survivor slots.
@@ -34,34 +36,53 @@
 namespace hn {
 using namespace sm100;
 
-constexpr int kEpiWarps = 16;  // 4 per SM sub-partition, 64 accumulator columns each
-constexpr int kDenseThreads = (2 + kEpiWarps) * 32;
+constexpr int kIssuers = 2;                      // MMA-issuing threads, one per accumulator buffer
+constexpr int kEpiWarps = 16;                    // 4 per SM sub-partition, 64 accumulator columns each
+constexpr int kEpiWarp0 = 1 + kIssuers;          // warp 0 producer, warps 1..kIssuers MMA, then epilogue
+constexpr int kDenseThreads = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
 struct DenseParams {
-    const void *pre;              // entries, UMMA core-matrix order, n_tiles * 256 rows (FP16 or BF16)
-    const void *qpre;             // queries, same order, n_qt * 128 rows
+    const void *pre;              // entries, UMMA core-matrix order, n_tiles * 128 rows (FP16 or BF16)
+    const void *qpre;             // queries, same order, n_qt * 256 rows
     int64_t n, n_tiles, nq;
     int64_t n_qt, tiles_per_chunk, n_units;
     const float *tau;
-    unsigned long long *cand;     // [nq][4 * chunks] Phase-1 (best score, segment id) per (query, chunk, column segment)
+    unsigned long long *cand;     // [nq][2 * chunks] Phase-1 (best score, segment id) per (query, chunk, entry half)
     int32_t *bucket, *count;
     int32_t cap;
     int32_t *status;
 };
 
 constexpr int kLcap = 32;  // Phase-2 survivors staged per epilogue thread before a flush
+constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
+constexpr int kDE = 128;   // entries per B tile (MMA N)
 
-template <int KP>
+// Measured on B300: one thread issues a 1-D bulk copy every ~350 cycles whatever
+// its size, and a tcgen05.commit costs ~220 cycles.  So a ring stage holds
+// several B tiles filled by one 16 KB copy, stages are released by the epilogue
+// with plain mbarrier arrivals (no commit), and two threads issue the MMAs, one
+// per accumulator buffer, each committing once per tile of its own.
+template <int KP, int PHASE>
 struct DenseCfg {
-    static constexpr uint32_t kB = kTileE * KP * 2;  // bytes of one entry tile
-    static constexpr uint32_t kA = kTileQ * KP * 2;  // bytes of one query tile
-    static constexpr int kStages = (64 * 1024) / kB < 2 ? 2 : (64 * 1024) / kB;
-    static constexpr uint32_t kSurvOff = kStages * kB + 2 * kA;
-    static constexpr uint32_t kBarOff = kSurvOff + kLcap * kEpiWarps * 32 * 4;  // [kLcap][512] entry ids
-    static constexpr int kBars = 2 * kStages + 9;
+    static constexpr uint32_t kB = kDE * KP * 2;                    // bytes of one entry tile
+    static constexpr int kTPS = kB >= 16384 ? 1 : 16384 / kB;       // entry tiles per stage
+    static constexpr uint32_t kStageBytes = kTPS * kB;
+    static constexpr uint32_t kA = kDQ * KP * 2;                    // bytes of one query unit
+    static constexpr uint32_t kSurvBytes = PHASE == 2 ? kLcap * kEpiWarps * 32 * 4 : 0;  // [kLcap][512] ids
+    // ring: 160 KB (Phase 1) / 128 KB (Phase 2), capped by what the 227 KB of shared
+    // memory leaves after the two query units, the survivor staging and the barriers
+    static constexpr uint32_t kRoom = 225 * 1024 - 2 * kA - kSurvBytes;
+    static constexpr uint32_t kWant = PHASE == 1 ? 160 * 1024 : 128 * 1024;
+    static constexpr uint32_t kRing = kWant < kRoom ? kWant : kRoom;
+    static constexpr int kStages = kRing / kStageBytes < 2 ? 2 : kRing / kStageBytes;
+    static constexpr uint32_t kSurvOff = kStages * kStageBytes + 2 * kA;
+    static constexpr uint32_t kBarOff = kSurvOff + kSurvBytes;
+    // b_full[S], b_empty[S], a_full[2], a_empty[2], acc_full[2], acc_empty[2], drain[kIssuers]
+    static constexpr int kBars = 2 * kStages + 8 + kIssuers;
     static constexpr uint32_t kSmem = kBarOff + kBars * 8 + 16;
+    static_assert(kSmem <= 232448, "dense scan shared memory above the 227 KB limit");
 };
 
 // Max of 16 consecutive scores, pairwise (15 two-input max, depth 4).
@@ -88,30 +109,30 @@ __device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
 
 template <int KP, int PHASE>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DenseParams p) {
-    using C = DenseCfg<KP>;
+    using C = DenseCfg<KP, PHASE>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
-    uint8_t *sA = smem + C::kStages * C::kB;
+    uint8_t *sA = smem + C::kStages * C::kStageBytes;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kBarOff);
     uint64_t *b_full = bars, *b_empty = bars + C::kStages;
     uint64_t *a_full = bars + 2 * C::kStages, *a_empty = a_full + 2;
     uint64_t *acc_full = a_empty + 2, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + kIssuers);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::kStages; ++i) {
             mbar_init(smem_u32(&b_full[i]), 1);
-            mbar_init(smem_u32(&b_empty[i]), 1);
+            mbar_init(smem_u32(&b_empty[i]), C::kTPS);  // one arrival per tile of the stage
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&a_full[i]), 1);
-            mbar_init(smem_u32(&a_empty[i]), 1);
+            mbar_init(smem_u32(&a_empty[i]), kIssuers);  // every issuer commits at the end of a unit
             mbar_init(smem_u32(&acc_full[i]), 1);
             mbar_init(smem_u32(&acc_empty[i]), kEpiWarps);  // one elected arrive per epilogue warp
         }
-        mbar_init(smem_u32(drain), 1);
+        for (int i = 0; i < kIssuers; ++i) mbar_init(smem_u32(&drain[i]), 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -129,8 +150,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0;
-            uint32_t issued = 0;               // stages / A buffers that received a copy
-            uint32_t last_par = 0;             // parity of the last copy per stage / A buffer
+            int64_t b_issued = 0, a_issued = 0;  // copies issued into the B ring / A buffers
             bool ok = true;
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
                 const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
@@ -139,31 +159,37 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 mbar_arrive_expect_tx(smem_u32(&a_full[abuf]), C::kA);
                 bulk_g2s(smem_u32(sA + abuf * C::kA), static_cast<const char *>(p.qpre) + qt * C::kA, C::kA,
                          smem_u32(&a_full[abuf]));
-                issued |= 1u << (24 + abuf);
-                last_par = (last_par & ~(1u << (24 + abuf))) | (aphase << (24 + abuf));
+                ++a_issued;
                 if (++abuf == 2) { abuf = 0; aphase ^= 1; }
-                for (int64_t t = t0; t < t1; ++t) {
+                for (int64_t tt = t0; tt < t1; tt += C::kTPS) {
+                    const uint32_t bytes = (uint32_t)min64(C::kTPS, t1 - tt) * C::kB;
                     if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, kWaitLimitNs))) break;
-                    mbar_arrive_expect_tx(smem_u32(&b_full[stage]), C::kB);
-                    bulk_g2s(smem_u32(sB + stage * C::kB), static_cast<const char *>(p.pre) + t * C::kB, C::kB,
-                             smem_u32(&b_full[stage]));
-                    issued |= 1u << stage;
-                    last_par = (last_par & ~(1u << stage)) | (sphase << stage);
+                    mbar_arrive_expect_tx(smem_u32(&b_full[stage]), bytes);
+                    bulk_g2s(smem_u32(sB + stage * C::kStageBytes), static_cast<const char *>(p.pre) + tt * C::kB,
+                             bytes, smem_u32(&b_full[stage]));
+                    ++b_issued;
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
                 }
             }
-            // copies still in flight must land before this CTA's shared memory goes away
+            // copies still in flight must land before this CTA's shared memory goes away:
+            // slot s last received copy number c = s + kStages * lap, lap = (issued - 1 - s) / kStages,
+            // which completes phase `lap` of its barrier (parity lap & 1)
             for (int s = 0; s < C::kStages; ++s)
-                if (issued & (1u << s)) mbar_drain(smem_u32(&b_full[s]), (last_par >> s) & 1, kWaitLimitNs);
+                if (b_issued > s)
+                    mbar_drain(smem_u32(&b_full[s]), (uint32_t)(((b_issued - 1 - s) / C::kStages) & 1), kWaitLimitNs);
             for (int s = 0; s < 2; ++s)
-                if (issued & (1u << (24 + s))) mbar_drain(smem_u32(&a_full[s]), (last_par >> (24 + s)) & 1, kWaitLimitNs);
+                if (a_issued > s) mbar_drain(smem_u32(&a_full[s]), (uint32_t)(((a_issued - 1 - s) / 2) & 1), kWaitLimitNs);
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
+    } else if (warp <= kIssuers) {
+        // ------------------------------------------------------------ MMA issuers
+        // Issuer i handles the tiles with (tile counter % 2) == i, always into
+        // accumulator buffer i (256 columns: A tile `sub` in columns 128*sub ..).
         if (lane == 0) {
+            const uint32_t me = (uint32_t)(warp - 1);
             // Phase 1: FP16 operands, FP16 accumulator; Phase 2: BF16 operands, FP32 accumulator
-            constexpr uint32_t idesc = PHASE == 1 ? idesc_f16_f16(kTileQ, kTileE) : idesc_bf16_f32(kTileQ, kTileE);
-            uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, acc = 0, accphase = 0;
+            constexpr uint32_t idesc = PHASE == 1 ? idesc_f16_f16(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE);
+            uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, uses = 0;
+            uint64_t g = 0;  // tile counter of this CTA
             bool ok = true;
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
                 const int64_t ch = u / p.n_qt;
@@ -171,44 +197,61 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 if (!(ok = mbar_wait(smem_u32(&a_full[abuf]), aphase, abort_flag, kWaitLimitNs))) break;
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA + abuf * C::kA);
-                for (int64_t t = t0; t < t1; ++t) {
-                    if (!(ok = mbar_wait(smem_u32(&acc_empty[acc]), accphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                for (int64_t tt = t0; ok && tt < t1; tt += C::kTPS) {
+                    const int nt = (int)min64(C::kTPS, t1 - tt);
+                    // wait for every fill of the ring, even one holding none of this issuer's
+                    // tiles, so that the parity of the next wait on the slot cannot alias
                     if (!(ok = mbar_wait(smem_u32(&b_full[stage]), sphase, abort_flag, kWaitLimitNs))) break;
-                    tc_fence_after();
-                    const uint32_t b_addr = smem_u32(sB + stage * C::kB);
+                    for (int j = 0; j < nt; ++j, ++g) {
+                        if ((uint32_t)(g & 1) != me) continue;
+                        if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, kWaitLimitNs))) break;
+                        tc_fence_after();
+                        const uint32_t b_addr = smem_u32(sB + stage * C::kStageBytes + j * C::kB);
 #pragma unroll
-                    for (int kk = 0; kk < KP / 16; ++kk) {
-                        // 16 columns = two core matrices along K, 128 B apart; 8-row groups KP*16 B apart
-                        const uint64_t ad = smem_desc(a_addr + kk * 256, 128, KP * 16);
-                        const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
-                        umma_bf16(tmem + acc * kTileE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        for (int sub = 0; sub < kDQ / kTileQ; ++sub) {
+#pragma unroll
+                            for (int kk = 0; kk < KP / 16; ++kk) {
+                                // 16 columns = two core matrices along K, 128 B apart; 8-row groups KP*16 B
+                                // apart; A tile `sub` = query rows 128*sub .. 128*sub+127
+                                const uint64_t ad = smem_desc(a_addr + sub * kTileQ * KP * 2 + kk * 256, 128, KP * 16);
+                                const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
+                                umma_bf16(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                            }
+                        }
+                        umma_commit(smem_u32(&acc_full[me]));
+                        ++uses;
                     }
-                    umma_commit(smem_u32(&b_empty[stage]));
-                    umma_commit(smem_u32(&acc_full[acc]));
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
-                    if (++acc == 2) { acc = 0; accphase ^= 1; }
                 }
+                if (!ok) break;
                 umma_commit(smem_u32(&a_empty[abuf]));
                 if (++abuf == 2) { abuf = 0; aphase ^= 1; }
             }
             // every MMA issued so far must finish before TMEM is released
-            umma_commit(smem_u32(drain));
-            mbar_drain(smem_u32(drain), 0, kWaitLimitNs);
+            umma_commit(smem_u32(&drain[me]));
+            mbar_drain(smem_u32(&drain[me]), 0, kWaitLimitNs);
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int quarter = warp & 3;          // TMEM lanes this warp may read: 32*quarter ..
-        const int seg = (warp - 2) >> 2;       // accumulator columns 64*seg .. 64*seg + 63
-        const int row = quarter * 32 + lane;
-        const int et = threadIdx.x - 64;       // epilogue thread 0..511
+        const int ew = warp - kEpiWarp0;         // 0 .. kEpiWarps-1
+        const int quarter = warp & 3;            // TMEM lanes this warp may read: 32*quarter ..
+        const int seg = ew >> 2;                 // accumulator columns 64*seg .. 64*seg + 63
+        const int sub = seg >> 1;                // query A tile of those columns
+        const int half = seg & 1;                // entry half of the B tile: entries 64*half ..
+        const int row = sub * kTileQ + quarter * 32 + lane;
+        const int et = ew * 32 + lane;           // epilogue thread 0..511
+        const bool releaser = ew == 0 && lane == 0;  // hands B stages back to the producer
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         uint32_t *sbuf = reinterpret_cast<uint32_t *>(smem + C::kSurvOff);  // [kLcap][512]
-        uint32_t acc = 0, accphase = 0;
+        uint32_t stage = 0, sphase = 0;
+        uint32_t g = 0;  // tile counter of this CTA: buffer g & 1, its use number g >> 1
         bool ok = true;
         for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
             const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
-            const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
-            const int64_t q = qt * kTileQ + row;
+            // tile and entry numbers fit in 32 bits (n < 2^31 - 256 is enforced by hn_index_build)
+            const int32_t t0 = (int32_t)(ch * p.tiles_per_chunk);
+            const int32_t t1 = (int32_t)min64(p.n_tiles, (int64_t)t0 + p.tiles_per_chunk);
+            const int64_t q = qt * kDQ + row;
             const bool qvalid = q < p.nq;
             const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
             float best = -INFINITY;
@@ -221,59 +264,67 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                     if (slot + j < p.cap) p.bucket[q * p.cap + slot + j] = (int32_t)sbuf[j * 512 + et];
                 lc = 0;
             };
-            // entry ids fit in 32 bits (n < 2^31 - 256 is enforced by hn_index_build)
             const int32_t n32 = (int32_t)p.n;
-            for (int32_t t = (int32_t)t0; t < (int32_t)t1; ++t) {
-                if (!(ok = mbar_wait(smem_u32(&acc_full[acc]), accphase, abort_flag, kWaitLimitNs))) break;
-                tc_fence_after();
-                const int32_t e0 = t * kTileE + seg * 64;
-                if (PHASE == 1) {
-                    uint32_t r[32];
-                    tmem_ld64_f16(tmem + acc * kTileE + seg * 64 + lane_addr, r);
-                    // the scores are in registers: hand the accumulator back to the MMA warp now
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
-                    if (++acc == 2) { acc = 0; accphase ^= 1; }
-                    // running best score and the 64-entry segment holding it; the entry
-                    // itself is recovered by the threshold kernel
-                    const float m = max64_f16(r);
-                    if (m > best && e0 < n32) { best = m; bseg = t * 4 + seg; }
-                } else {
-                    float v[64];
-                    tmem_ld64(tmem + acc * kTileE + seg * 64 + lane_addr, v);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
-                    if (++acc == 2) { acc = 0; accphase ^= 1; }
-                    float g[4];
+            const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
+            int32_t e0 = t0 * kDE + half * 64;    // first entry of this warp's 64 columns
+            for (int32_t tt = t0; ok && tt < t1; tt += C::kTPS) {
+                const int nt = t1 - tt < C::kTPS ? t1 - tt : C::kTPS;
+                for (int j = 0; j < nt; ++j, ++g, e0 += kDE) {
+                    const uint32_t buf = g & 1u;
+                    if (!(ok = mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag, kWaitLimitNs))) break;
+                    tc_fence_after();
+                    // this tile's MMAs are done with the stage; the last tile of a short stage
+                    // also arrives for the tiles the stage did not hold
+                    if (releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), j == nt - 1 ? 1 + C::kTPS - nt : 1);
+                    const int32_t t = tt + j;
+                    if (PHASE == 1) {
+                        uint32_t r[32];
+                        tmem_ld64_f16(tmem + buf * 256 + seg * 64 + lane_addr, r);
+                        // the scores are in registers: hand the accumulator back to the MMA warp now
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                        // running best score and the 64-entry segment holding it; the entry
+                        // itself is recovered by the threshold kernel
+                        const float m = max64_f16(r);
+                        if (m > best && (t < full_tiles || e0 < n32)) { best = m; bseg = t * 2 + half; }
+                    } else {
+                        float v[64];
+                        tmem_ld64(tmem + buf * 256 + seg * 64 + lane_addr, v);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                        float gm[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) g[k] = max16(v + 16 * k);
-                    const float m = fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
-                    if (m >= thr) {
+                        for (int k = 0; k < 4; ++k) gm[k] = max16(v + 16 * k);
+                        const float m = fmaxf(fmaxf(gm[0], gm[1]), fmaxf(gm[2], gm[3]));
+                        if (m >= thr) {
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (g[k] >= thr) {
-                                uint32_t mask = 0;
+                            for (int k = 0; k < 4; ++k) {
+                                if (gm[k] >= thr) {
+                                    uint32_t mask = 0;
 #pragma unroll
-                                for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
-                                const int32_t ek = e0 + 16 * k;
-                                if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
-                                if (lc + __popc(mask) > kLcap) flush();
-                                while (mask) {
-                                    const int i = __ffs(mask) - 1;
-                                    mask &= mask - 1;
-                                    sbuf[lc * 512 + et] = (uint32_t)(ek + i);
-                                    ++lc;
+                                    for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
+                                    const int32_t ek = e0 + 16 * k;
+                                    if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
+                                    if (lc + __popc(mask) > kLcap) flush();
+                                    while (mask) {
+                                        const int i = __ffs(mask) - 1;
+                                        mask &= mask - 1;
+                                        sbuf[lc * 512 + et] = (uint32_t)(ek + i);
+                                        ++lc;
+                                    }
                                 }
                             }
                         }
                     }
                 }
+                if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
             }
-            // one writer per (query, chunk, segment): no atomics, every slot written
+            if (!ok) break;
+            // one writer per (query, chunk, entry half): no atomics, every slot written
             if (PHASE == 1 && qvalid)
-                p.cand[q * (4 * (p.n_units / p.n_qt)) + 4 * ch + seg] =
+                p.cand[q * (2 * (p.n_units / p.n_qt)) + 2 * ch + half] =
                     bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
             if (PHASE == 2 && lc > 0) flush();
         }
@@ -311,8 +362,8 @@ static void dense_chunking(int64_t n_tiles, int64_t n_qt, int G, int64_t *tiles_
 
 int64_t dense_cand_slots(const Index &ix, int64_t nq) {
     int64_t tpc = 0, chunks = 0;
-    dense_chunking(ix.n_tiles, (nq + kTileQ - 1) / kTileQ, num_sms(), &tpc, &chunks);
-    return 4 * chunks;
+    dense_chunking(ix.n_tiles * (kTileE / kDE), (nq + kDQ - 1) / kDQ, num_sms(), &tpc, &chunks);
+    return 2 * chunks;
 }
 
 bool dense_scan_supported(const Index &ix) {
@@ -321,7 +372,7 @@ bool dense_scan_supported(const Index &ix) {
 
 template <int KP, int PHASE>
 static cudaError_t launch_kp(const DenseParams &p, int grid, cudaStream_t st) {
-    using C = DenseCfg<KP>;
+    using C = DenseCfg<KP, PHASE>;
     const int smem = (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
     static bool attr_set = false;
     if (!attr_set) {
@@ -340,12 +391,12 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     p.pre = phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
     p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
     p.n = ix.n;
-    p.n_tiles = ix.n_tiles;
+    p.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
     p.nq = nq;
-    p.n_qt = (nq + kTileQ - 1) / kTileQ;
+    p.n_qt = (nq + kDQ - 1) / kDQ;
     const int G = num_sms();
     int64_t chunks = 0;
-    dense_chunking(ix.n_tiles, p.n_qt, G, &p.tiles_per_chunk, &chunks);
+    dense_chunking(p.n_tiles, p.n_qt, G, &p.tiles_per_chunk, &chunks);
     p.n_units = p.n_qt * chunks;
     p.tau = ws.tau;
     p.cand = ws.cand;

@@ -14,7 +14,8 @@ namespace hn {
 
 constexpr int kD = 128;           // descriptor width (HardNet, §3.1)
 constexpr int kTileE = 256;       // entries per scan tile (dense kernel N dimension)
-constexpr int kTileQ = 128;       // queries per dense tile (UMMA M)
+constexpr int kTileQ = 128;       // queries per dense MMA (UMMA M)
+constexpr int kQPad = 256;        // query padding: the dense scan takes queries 256 at a time
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);

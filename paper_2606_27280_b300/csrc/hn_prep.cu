@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
 }
 
 cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t st) {
-    const int64_t nq_pad = (nq + kTileQ - 1) / kTileQ * kTileQ;
+    const int64_t nq_pad = (nq + kQPad - 1) / kQPad * kQPad;
     const int64_t blocks = (nq_pad * 32 + 255) / 256;
     k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
                                                    ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,

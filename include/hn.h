@@ -198,6 +198,67 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
                           int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
 
 /*
+ * Batched serving (an extension of the method; the paper searches one query
+ * at a time).  One call answers nb batches of queries, each against its own
+ * index; every batch's result is the same as hn_search_batch would give.
+ * Batches are grouped by index and each group's queries concatenated, so that
+ * small batches share the dense scan's work units; each group runs on a
+ * stream of its own.  With opts->use_graph (default 1) the whole set is
+ * captured once into a CUDA graph and the graph is replayed as long as the
+ * same batches come back (same indexes, query and output pointers and sizes,
+ * and no reallocation of the indexes' scratch in between).  Synchronises
+ * `stream` once (plus re-runs after a survivor overflow).  The call holds a
+ * process-wide lock; the indexes must not be used concurrently elsewhere.
+ */
+typedef struct hn_batch {
+    hn_index *index;      /* index to search */
+    const float *q;       /* nq x 128 HN-normalised float32 queries (device) */
+    int64_t nq;
+    int64_t *out_idx;     /* nq int64 (device) */
+    double *out_sim;      /* nq double (device) */
+} hn_batch;
+
+typedef struct hn_multi_opts {
+    int32_t use_graph;    /* capture and replay a CUDA graph [1] */
+    int32_t reserved[7];  /* must be zero */
+} hn_multi_opts;
+
+typedef struct hn_multi_stats {
+    int64_t n_queries;
+    int32_t n_batches, n_groups;
+    int32_t graph_replayed;  /* 1: an instantiated graph was replayed */
+    int32_t reruns;          /* re-runs after survivor-slot overflow */
+    float ms_total;          /* device time from the start of the set to its last batch */
+    float batch_ms_p50, batch_ms_p99, batch_ms_max;  /* time from the start to each batch's completion */
+    int32_t reserved;
+    int64_t survivors;       /* Phase-2 survivors over all batches */
+} hn_multi_stats;
+
+hn_status hn_search_multi(const hn_batch *batches, int32_t nb, const hn_multi_opts *opts, hn_multi_stats *stats,
+                          void *stream);
+
+/*
+ * Autotuner: times the streaming and dense scans of `index` on n_sizes batch
+ * sizes (the index's own first rows as queries) and stores in the index the
+ * smallest batch from which hn_search_batch's automatic choice takes the dense
+ * scan, and the dense work-unit granularity (units per SM: 8, 16, 32 or 64)
+ * that is fastest at the largest size.  Synchronises `stream`.
+ */
+#define HN_TUNE_MAX 16
+typedef struct hn_tune_result {
+    int32_t n_sizes;
+    int32_t dense_min_q;      /* chosen crossover (INT32_MAX: the dense scan never won) */
+    int32_t units_per_cta;    /* chosen dense work-unit granularity */
+    int32_t reserved;
+    int64_t sizes[HN_TUNE_MAX];
+    float ms_stream[HN_TUNE_MAX];
+    float ms_dense[HN_TUNE_MAX];   /* -1 when the index has no BF16 prefix */
+    float ms_units[4];             /* dense time at the largest size for 8, 16, 32, 64 units per SM */
+} hn_tune_result;
+
+hn_status hn_autotune(hn_index *index, const int64_t *sizes, int32_t n_sizes, hn_tune_result *out, void *stream);
+
+/*
  * Block partition of an index built with opts.n_blocks > 0 (device arrays, may be NULL):
  * block_start[n_blocks + 1] (block b = sorted positions [start[b], start[b+1])),
  * block_ids[n] (entry ids in block order), block_of[n] (block of each entry).

@@ -5,7 +5,7 @@ ctypes binding.  Importing this package loads the library and raises
 ImportError if it has not been built.
 """
 from .hn import (D, HNError, Index, PREFIX_BF16, PREFIX_F32, Proposal, SCAN_AUTO, SCAN_DENSE, SCAN_STREAM,
-                 SearchResult, mlp_loss_grad, normalize, version)
+                 SearchResult, mlp_loss_grad, normalize, search_multi, version)
 
 __all__ = ["D", "HNError", "Index", "PREFIX_BF16", "PREFIX_F32", "Proposal", "SCAN_AUTO", "SCAN_DENSE",
-           "SCAN_STREAM", "SearchResult", "mlp_loss_grad", "normalize", "version"]
+           "SCAN_STREAM", "SearchResult", "mlp_loss_grad", "normalize", "search_multi", "version"]

@@ -2,6 +2,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "hn_internal.cuh"
@@ -98,6 +99,7 @@ static hn_status ensure_ws(Index &ix, int64_t nq, int32_t cap) {
     HN_CUDA(dalloc(&ws.qnorm, qc));
     ws.q_cap = qc;
     ws.bucket_cap = bc;
+    ++ws.gen;
     return HN_OK;
 }
 
@@ -118,6 +120,7 @@ struct hn_index {
 };
 
 const Index *hn::index_state(const hn_index *h) { return h ? &h->ix : nullptr; }
+Index *hn::index_state_mut(hn_index *h) { return h ? &h->ix : nullptr; }
 
 extern "C" {
 
@@ -165,6 +168,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     cudaStream_t s = (cudaStream_t)stream;
     hn_index *h = new hn_index();
     Index &ix = h->ix;
+    static std::atomic<uint64_t> next_serial{1};
+    ix.serial = next_serial++;
     ix.n = n;
     ix.k = k;
     ix.alpha = alpha;
@@ -295,6 +300,74 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
     return HN_OK;
 }
 
+}  // extern "C"
+
+namespace hn {
+
+int pick_scan(const Index &ix, int64_t nq, int requested) {
+    if (requested != HN_SCAN_AUTO) return requested;
+    return (dense_scan_supported(ix) && nq >= ix.dense_min_q) ? HN_SCAN_DENSE : HN_SCAN_STREAM;
+}
+
+// Size the index's scratch for nq queries and `cap` survivor slots (may allocate).
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap) {
+    Workspace &ws = ix.ws;
+    hn_status st = ensure_ws(ix, nq, cap);
+    if (st != HN_OK) return st;
+    if (scan == HN_SCAN_DENSE) {
+        const int64_t slots = dense_cand_slots(ix, nq);
+        const int64_t need = ((nq + kQPad - 1) / kQPad * kQPad) * slots;
+        if (need > ws.cand_cap) {
+            cudaFree(ws.cand);
+            ws.cand = nullptr;
+            ws.cand_cap = 0;
+            HN_CUDA(dalloc(&ws.cand, need));
+            ws.cand_cap = need;
+            ++ws.gen;
+        }
+        ws.cand_slots = (int32_t)slots;
+    }
+    return HN_OK;
+}
+
+// Enqueue one search on stream s: allocation-free, synchronisation-free, so it can
+// be captured into a CUDA graph.  Status words and counters land in the pinned
+// host mirror ws.h_status once the stream has run.
+hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
+                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s) {
+    Workspace &ws = ix.ws;
+    HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
+    HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
+    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s);
+    if (st != HN_OK) return st;
+    HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    return HN_OK;
+}
+
+// After the stream has run: HN_OK, an error, or HN_ERR_OVERFLOW with *want_cap set.
+hn_status check_search(Index &ix, int64_t nq, int32_t *want_cap) {
+    Workspace &ws = ix.ws;
+    const long long *hc = reinterpret_cast<const long long *>(ws.h_status + 8);
+    ws.last_max = (int32_t)std::min<long long>(hc[CT_MAXSURV], 1 << 30);
+    if (ws.h_status[ST_NOT_NORMALIZED]) return fail(HN_ERR_NOT_NORMALIZED, "a query violates the HN norm identities");
+    if (ws.h_status[ST_TIMEOUT]) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
+    if (!ws.h_status[ST_OVERFLOW]) return HN_OK;
+    if (hc[CT_MAXSURV] >= (1 << 30)) return fail(HN_ERR_OVERFLOW, "survivor storage overflow");
+    const int64_t want = hc[CT_MAXSURV] + hc[CT_MAXSURV] / 8 + 32;
+    if ((int64_t)nq * want * 4 > ((int64_t)96 << 30)) return fail(HN_ERR_OVERFLOW, "survivor storage would exceed 96 GiB");
+    *want_cap = (int32_t)want;
+    return HN_ERR_OVERFLOW;
+}
+
+int32_t default_cap(const Index &ix) {
+    return std::max<int32_t>(std::max<int32_t>(256, ix.ws.bucket_cap), ix.ws.last_max + ix.ws.last_max / 4);
+}
+
+}  // namespace hn
+
+extern "C" {
+
 hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts, int64_t *out_idx,
                           double *out_sim, hn_search_stats *stats, void *stream) {
     if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
@@ -311,8 +384,7 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
             return fail(HN_ERR_INVALID_ARG, "the proposal was not trained for this index's blocks");
         if (topk < 1 || topk > 64 || topk > ix.n_blocks) return fail(HN_ERR_INVALID_ARG, "need 1 <= seed_topk <= 64");
     }
-    int scan = o.scan;
-    if (scan == HN_SCAN_AUTO) scan = (ix.prefix == HN_PREFIX_BF16 && nq >= 1024 && dense_scan_supported(ix)) ? HN_SCAN_DENSE : HN_SCAN_STREAM;
+    const int scan = pick_scan(ix, nq, o.scan);
     if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
     if (scan == HN_SCAN_DENSE && !dense_scan_supported(ix))
         return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 prefix index");
@@ -325,8 +397,7 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     if (nq == 0) return HN_OK;
     if (!q || !out_idx || !out_sim || !aligned16(q)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    int32_t cap = o.bucket_cap;
-    if (cap == 0) cap = std::max<int32_t>(std::max<int32_t>(256, ix.ws.bucket_cap), ix.ws.last_max + ix.ws.last_max / 4);
+    int32_t cap = o.bucket_cap ? o.bucket_cap : default_cap(ix);
     Workspace &ws = ix.ws;
     const bool timing = o.timing != 0;
     if (timing && !ws.ev_ready) {
@@ -335,34 +406,17 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     }
     int32_t reruns = 0, kernels = 0;
     for (;;) {
-        hn_status st = ensure_ws(ix, nq, cap);
+        hn_status st = prepare_search(ix, nq, scan, cap);
         if (st != HN_OK) return st;
-        if (scan == HN_SCAN_DENSE) {
-            const int64_t slots = dense_cand_slots(ix, nq);
-            const int64_t need = ((nq + kQPad - 1) / kQPad * kQPad) * slots;
-            if (need > ws.cand_cap) {
-                cudaFree(ws.cand);
-                ws.cand = nullptr;
-                ws.cand_cap = 0;
-                HN_CUDA(dalloc(&ws.cand, need));
-                ws.cand_cap = need;
-            }
-            ws.cand_slots = (int32_t)slots;
-        }
-        HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
-        HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
-        st = run_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s);
+        st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s);
         if (st != HN_OK) return st;
         kernels += o.seed ? 4 + 5 * (int32_t)((nq + 8191) / 8192) : 5;
-        HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
         HN_CUDA(cudaStreamSynchronize(s));
-        const long long *hc = reinterpret_cast<const long long *>(ws.h_status + 8);
-        ws.last_max = (int32_t)std::min<long long>(hc[CT_MAXSURV], 1 << 30);
-        if (ws.h_status[ST_NOT_NORMALIZED]) return fail(HN_ERR_NOT_NORMALIZED, "a query violates the HN norm identities");
-        if (ws.h_status[ST_TIMEOUT]) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
-        if (!ws.h_status[ST_OVERFLOW]) {
+        int32_t want = 0;
+        st = check_search(ix, nq, &want);
+        if (st == HN_OK) {
             if (stats) {
+                const long long *hc = reinterpret_cast<const long long *>(ws.h_status + 8);
                 stats->survivors = hc[CT_SURVIVORS];
                 stats->max_survivors = hc[CT_MAXSURV];
                 stats->fp64_rescored = hc[CT_FP64];
@@ -377,12 +431,10 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
             }
             return HN_OK;
         }
+        if (st != HN_ERR_OVERFLOW) return st;
         // survivors did not fit: grow the slots to the largest count seen and run again
-        if (reruns >= 2 || hc[CT_MAXSURV] >= (1 << 30))
-            return fail(HN_ERR_OVERFLOW, "survivor storage overflow after re-runs");
-        const int64_t want = hc[CT_MAXSURV] + hc[CT_MAXSURV] / 8 + 32;
-        if ((int64_t)nq * want * 4 > ((int64_t)96 << 30)) return fail(HN_ERR_OVERFLOW, "survivor storage would exceed 96 GiB");
-        cap = (int32_t)want;
+        if (reruns >= 2) return fail(HN_ERR_OVERFLOW, "survivor storage overflow after re-runs");
+        cap = want;
         ++reruns;
     }
 }

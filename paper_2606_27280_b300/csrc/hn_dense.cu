@@ -350,10 +350,10 @@ static int num_sms() {
     return g_num_sms;
 }
 
-// About 32 work units per CTA, numbered chunk-major so that the running CTAs
-// share entry tiles in L2.
-static void dense_chunking(int64_t n_tiles, int64_t n_qt, int G, int64_t *tiles_per_chunk, int64_t *chunks) {
-    int64_t c = (32ll * G + n_qt - 1) / n_qt;
+// About `upc` work units per CTA (autotuned, 32 by default), numbered chunk-major
+// so that the running CTAs share entry tiles in L2.
+static void dense_chunking(int64_t n_tiles, int64_t n_qt, int G, int upc, int64_t *tiles_per_chunk, int64_t *chunks) {
+    int64_t c = ((int64_t)upc * G + n_qt - 1) / n_qt;
     c = max64(1, min64(c, n_tiles));
     const int64_t tpc = (n_tiles + c - 1) / c;
     *tiles_per_chunk = tpc;
@@ -362,7 +362,7 @@ static void dense_chunking(int64_t n_tiles, int64_t n_qt, int G, int64_t *tiles_
 
 int64_t dense_cand_slots(const Index &ix, int64_t nq) {
     int64_t tpc = 0, chunks = 0;
-    dense_chunking(ix.n_tiles * (kTileE / kDE), (nq + kDQ - 1) / kDQ, num_sms(), &tpc, &chunks);
+    dense_chunking(ix.n_tiles * (kTileE / kDE), (nq + kDQ - 1) / kDQ, num_sms(), ix.units_per_cta, &tpc, &chunks);
     return 2 * chunks;
 }
 
@@ -371,16 +371,39 @@ bool dense_scan_supported(const Index &ix) {
 }
 
 template <int KP, int PHASE>
-static cudaError_t launch_kp(const DenseParams &p, int grid, cudaStream_t st) {
+static int dense_smem() {
     using C = DenseCfg<KP, PHASE>;
-    const int smem = (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_dense_scan<KP, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
+    return (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
+}
+
+template <int KP, int PHASE>
+static cudaError_t set_attr() {
+    return cudaFuncSetAttribute(k_dense_scan<KP, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                dense_smem<KP, PHASE>());
+}
+
+// Kernel attributes for every instantiation; called once before the first launch
+// (and before any stream capture, where attribute changes do not belong).
+cudaError_t dense_init() {
+    static cudaError_t done = cudaErrorNotReady;
+    if (done == cudaErrorNotReady) {
+        cudaError_t e = set_attr<16, 1>();
+        if (e == cudaSuccess) e = set_attr<16, 2>();
+        if (e == cudaSuccess) e = set_attr<32, 1>();
+        if (e == cudaSuccess) e = set_attr<32, 2>();
+        if (e == cudaSuccess) e = set_attr<64, 1>();
+        if (e == cudaSuccess) e = set_attr<64, 2>();
+        num_sms();
+        done = e;
     }
-    k_dense_scan<KP, PHASE><<<grid, kDenseThreads, smem, st>>>(p);
+    return done;
+}
+
+template <int KP, int PHASE>
+static cudaError_t launch_kp(const DenseParams &p, int grid, cudaStream_t st) {
+    cudaError_t e = dense_init();
+    if (e != cudaSuccess) return e;
+    k_dense_scan<KP, PHASE><<<grid, kDenseThreads, dense_smem<KP, PHASE>(), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -396,7 +419,7 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     p.n_qt = (nq + kDQ - 1) / kDQ;
     const int G = num_sms();
     int64_t chunks = 0;
-    dense_chunking(p.n_tiles, p.n_qt, G, &p.tiles_per_chunk, &chunks);
+    dense_chunking(p.n_tiles, p.n_qt, G, ix.units_per_cta, &p.tiles_per_chunk, &chunks);
     p.n_units = p.n_qt * chunks;
     p.tau = ws.tau;
     p.cand = ws.cand;

@@ -77,6 +77,7 @@ struct Workspace {
     int32_t last_max = 0;              // largest survivor count seen (sizing hint)
     cudaEvent_t ev[8] = {};            // step timers (created on first timed search)
     bool ev_ready = false;
+    uint64_t gen = 0;                  // bumped whenever the buffers above are reallocated
 };
 
 struct Index {
@@ -94,6 +95,9 @@ struct Index {
     float *mx = nullptr;             // [n] |x_minor| rounded up
     float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
+    uint64_t serial = 0;             // unique per built index (a freed index's address may be reused)
+    int32_t dense_min_q = 1024;      // smallest batch the AUTO scan sends to the dense kernel (autotuned)
+    int32_t units_per_cta = 32;      // dense work-unit granularity (autotuned)
     int32_t n_blocks = 0;            // block partition for the learned proposal (0 = none)
     int32_t *block_ids = nullptr;    // [n] entry ids in block order
     int32_t *block_of = nullptr;     // [n] block of each entry
@@ -115,6 +119,15 @@ __host__ __device__ inline int64_t pre16_offset(int64_t e, int c, int k_pad16) {
     return g * (int64_t)k_pad16 * 16 + (int64_t)(c >> 3) * 128 + r * 16 + (c & 7) * 2;
 }
 
+// search pipeline pieces (hn_api.cu), shared with the multi-batch path
+int pick_scan(const Index &ix, int64_t nq, int requested);
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap);
+hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
+                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s);
+hn_status check_search(Index &ix, int64_t nq, int32_t *want_cap);
+int32_t default_cap(const Index &ix);
+Index *index_state_mut(hn_index *h);
+
 // launches (defined in the .cu files)
 cudaError_t launch_normalize(const float *in, float *out, int64_t n, int k, double alpha,
                              int32_t *status, cudaStream_t s);
@@ -135,6 +148,7 @@ cudaError_t launch_bruteforce_keys(const Index &ix, const float *q, int64_t nq, 
 // Device state of a built index (used by entry points outside hn_api.cu).
 const Index *index_state(const hn_index *h);
 bool dense_scan_supported(const Index &ix);
+cudaError_t dense_init();
 cudaError_t build_blocks(Index &ix, int n_blocks, int iters, cudaStream_t s);
 cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
                                cudaStream_t s);

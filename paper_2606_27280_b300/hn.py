@@ -67,6 +67,32 @@ class IndexInfo(ctypes.Structure):
                 ("n_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Batch(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_void_p), ("q", ctypes.c_void_p), ("nq", ctypes.c_int64),
+                ("out_idx", ctypes.c_void_p), ("out_sim", ctypes.c_void_p)]
+
+
+class MultiOpts(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class MultiStats(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int64), ("n_batches", ctypes.c_int32), ("n_groups", ctypes.c_int32),
+                ("graph_replayed", ctypes.c_int32), ("reruns", ctypes.c_int32), ("ms_total", ctypes.c_float),
+                ("batch_ms_p50", ctypes.c_float), ("batch_ms_p99", ctypes.c_float), ("batch_ms_max", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("survivors", ctypes.c_int64)]
+
+
+TUNE_MAX = 16
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_sizes", ctypes.c_int32), ("dense_min_q", ctypes.c_int32), ("units_per_cta", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("sizes", ctypes.c_int64 * TUNE_MAX),
+                ("ms_stream", ctypes.c_float * TUNE_MAX), ("ms_dense", ctypes.c_float * TUNE_MAX),
+                ("ms_units", ctypes.c_float * 4)]
+
+
 # exported symbol -> (argtypes, restype); the ABI test checks these against include/hn.h
 _vp, _i64, _i32, _f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
 SIGNATURES = {
@@ -79,6 +105,8 @@ SIGNATURES = {
     "hn_search_batch": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "hn_index_blocks": ([_vp, _vp, _vp, _vp, _vp], _i32),
+    "hn_search_multi": ([_vp, _i32, _vp, _vp, _vp], _i32),
+    "hn_autotune": ([_vp, _vp, _i32, _vp, _vp], _i32),
     "hn_proposal_train": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "hn_proposal_infer": ([_vp, _vp, _i64, _i32, _vp, _vp], _i32),
     "hn_proposal_get_info": ([_vp, _vp], _i32),
@@ -189,6 +217,16 @@ class Index:
         inf = IndexInfo()
         _check(_lib.hn_index_get_info(self._h, ctypes.byref(inf)), "hn_index_get_info")
         return {name: getattr(inf, name) for name, _ in inf._fields_}
+
+    def autotune(self, sizes, stream=None) -> dict:
+        """Time the streaming and dense scans at these batch sizes; the index keeps the choices."""
+        sizes = [int(x) for x in sizes]
+        arr = (ctypes.c_int64 * len(sizes))(*sizes)
+        r = TuneResult()
+        _check(_lib.hn_autotune(self._h, arr, len(sizes), ctypes.byref(r), _stream(stream)), "hn_autotune")
+        n = r.n_sizes
+        return {"dense_min_q": r.dense_min_q, "units_per_cta": r.units_per_cta, "sizes": list(r.sizes[:n]),
+                "ms_stream": list(r.ms_stream[:n]), "ms_dense": list(r.ms_dense[:n]), "ms_units": list(r.ms_units)}
 
     def blocks(self, stream=None):
         """(block_start [B+1], block_ids [n], block_of [n]) int32 device tensors."""
@@ -308,3 +346,23 @@ def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, 
     _check(_lib.hn_mlp_loss_grad(params.data_ptr(), k, h1, h2, c, x.data_ptr(), y.data_ptr(), x.shape[0],
                                  ctypes.byref(loss), grads.data_ptr(), _stream(stream)), "hn_mlp_loss_grad")
     return loss.value, grads
+
+
+def search_multi(batches, use_graph: bool = True, stream=None) -> dict:
+    """Answer many batches in one call.  `batches`: list of (Index, q, out_idx, out_sim) with
+    q a (nq, 128) float32 CUDA tensor and the outputs int64 / float64 CUDA tensors of nq
+    entries.  Returns the call's statistics."""
+    arr = (Batch * max(1, len(batches)))()
+    keep = []
+    for i, (ix, q, oi, os_) in enumerate(batches):
+        q = _dev_f32(q, "q") if q.shape[0] else q
+        keep.append(q)
+        if oi.dtype != torch.int64 or os_.dtype != torch.float64 or oi.numel() != q.shape[0] or os_.numel() != q.shape[0]:
+            raise ValueError("outputs must be int64 / float64 tensors of nq entries")
+        arr[i] = Batch(index=ix._h.value, q=q.data_ptr() if q.numel() else None, nq=q.shape[0],
+                       out_idx=oi.data_ptr() if oi.numel() else None, out_sim=os_.data_ptr() if os_.numel() else None)
+    opts = MultiOpts(use_graph=int(bool(use_graph)))
+    st = MultiStats()
+    _check(_lib.hn_search_multi(arr, len(batches), ctypes.byref(opts), ctypes.byref(st), _stream(stream)),
+           "hn_search_multi")
+    return {name: getattr(st, name) for name, _ in st._fields_ if name != "reserved"}

@@ -45,6 +45,10 @@ def test_struct_sizes_match_header(hn):
     assert ctypes.sizeof(hn.IndexInfo) == 64
     assert ctypes.sizeof(hn.TrainOpts) == 40
     assert ctypes.sizeof(hn.ProposalInfo) == 40
+    assert ctypes.sizeof(hn.Batch) == 40
+    assert ctypes.sizeof(hn.MultiOpts) == 32
+    assert ctypes.sizeof(hn.MultiStats) == 56
+    assert ctypes.sizeof(hn.TuneResult) == 288
 
 
 def test_version(hn):
@@ -100,6 +104,14 @@ def test_search_host_checks(hn):
     assert hn._lib.hn_bruteforce(None, None, 4, None, None, None) == hn.ERR_INVALID_ARG
     assert hn._lib.hn_index_destroy(None) == hn.OK
     assert hn._lib.hn_index_get_info(None, None) == hn.ERR_INVALID_ARG
+
+
+def test_multi_and_autotune_host_checks(hn):
+    assert hn._lib.hn_search_multi(None, 3, None, None, None) == hn.ERR_INVALID_ARG
+    assert hn._lib.hn_search_multi(None, 0, None, None, None) == hn.OK
+    bad = (hn.Batch * 1)()
+    assert hn._lib.hn_search_multi(bad, 1, None, None, None) == hn.ERR_INVALID_ARG   # NULL index
+    assert hn._lib.hn_autotune(None, None, 1, None, None) == hn.ERR_INVALID_ARG
 
 
 def test_python_wrappers_reject_cpu_tensors(hn):

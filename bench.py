@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS))
+    ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS) + ["c4"])
     ap.add_argument("--prefix", default=None, choices=["f32", "bf16"])
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -157,7 +157,7 @@ def cpu_baseline(wl, c, budget_s: float = 12.0):
 def run_reference(args, rank: int):
     if rank != 0:
         return 0
-    wl, c = hn_synth.config_workload(args.workload)
+    wl, c = hn_synth.config_workload(args.workload if args.workload in hn_synth.CONFIGS else "c2")
     per_step, total_q = [], 0
     import oracle
     db = oracle.normalize(wl.db_raw, c["k"], c["alpha"])
@@ -209,6 +209,11 @@ def main():
     def barrier():
         if dist is not None:
             dist.barrier()
+
+    if args.workload == "c4":
+        return run_serving(args, hn, torch, world, rank, dist, barrier)
+    if args.workload == "c3":
+        return run_proposal(args, hn, torch, world, rank, dist, barrier)
 
     wl, c = hn_synth.config_workload(args.workload)
     k, alpha = c["k"], c["alpha"]
@@ -363,6 +368,143 @@ def main():
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+def _timed_steps(torch, stream, steps, fn, flush):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    out = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        out.append(fn())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], out
+
+
+def run_proposal(args, hn, torch, world, rank, dist, barrier):
+    """c3: the learned block proposal seeds the threshold (Phase 1 skipped), versus the plain search."""
+    c = dict(hn_synth.CONFIGS["c3"])
+    wl = hn_synth.make_workload(c["n"], c["nq"], c["n_centres"], c["seed"])
+    k, alpha = c["k"], c["alpha"]
+    stream = torch.cuda.current_stream()
+    db = hn.normalize(torch.from_numpy(wl.db_raw).cuda(), k, alpha)
+    t0 = time.perf_counter()
+    ix = hn.Index(db, k, alpha, prefix=hn.PREFIX_BF16, n_blocks=c["n_blocks"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    tq_raw, _ = hn_synth.queries_from(wl.db_raw, c["n_train"], seed=c["train_seed"])
+    tq = hn.normalize(torch.from_numpy(tq_raw).cuda(), k, alpha)
+    del db, tq_raw
+    t0 = time.perf_counter()
+    prop = hn.Proposal.train(ix, tq, seed=7)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del tq
+    q_raw = torch.from_numpy(wl.q_raw).cuda()
+    nq = q_raw.shape[0]
+    qn = torch.empty_like(q_raw)
+    oi = torch.empty(nq, dtype=torch.int64, device="cuda")
+    os_ = torch.empty(nq, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, kw in (("seeded", dict(proposal=prop, seed_topk=4)), ("plain", {})):
+        def step():
+            hn.normalize(q_raw, k, alpha, out=qn)
+            return ix.search(qn, out_idx=oi, out_sim=os_, timing=True, **kw)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        ms, outs = _timed_steps(torch, stream, args.steps, step, flush)
+        st = outs[-1].stats
+        res[name] = {"queries_per_s": nq * args.steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / args.steps,
+                     "survivor_frac": st["survivors"] / (nq * c["n"]),
+                     "phases_ms": {kk: st[kk] for kk in ("ms_prep", "ms_phase1", "ms_threshold", "ms_phase2",
+                                                         "ms_rescore")}}
+        res[name + "_idx"] = oi.clone()
+    same = bool(torch.equal(res.pop("seeded_idx"), res.pop("plain_idx")))
+    if rank == 0:
+        info = prop.info()
+        line = {"metric": "exact 1-NN queries/s (learned block proposal seed)", "value": res["seeded"]["queries_per_s"],
+                "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res["seeded"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": f"c3: N={c['n']}, Q={nq}, K={k}, alpha={alpha}, {c['n_blocks']} blocks, "
+                                       f"MLP {k}-256-256-{c['n_blocks']}, {c['n_train']} training pairs, top-4 seed"},
+                "seeded": res["seeded"], "plain": res["plain"], "identical_results": same,
+                "proposal": {"train_s": train_s, "final_loss": info["last_loss"], "steps": info["steps"]},
+                "index_build_s": build_s}
+        print(json.dumps(line), flush=True)
+    prop.close()
+    ix.close()
+    return 0
+
+
+def run_serving(args, hn, torch, world, rank, dist, barrier):
+    """c4: 256 uneven batches over 16 indexes, one graph-replayed hn_search_multi per step."""
+    cfg = hn_synth.SERVING
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    indexes, raws = [], []
+    for di, n in enumerate(cfg["db_sizes"]):
+        w = hn_synth.make_workload(n, 0, max(1, n // 5), seed=di + 1)
+        raws.append(w.db_raw)
+        raw_dev = torch.from_numpy(w.db_raw).cuda()
+        for k in cfg["ks"]:
+            for a in cfg["alphas"]:
+                x = hn.normalize(raw_dev, k, a)
+                indexes.append((hn.Index(x, k, a, prefix=hn.PREFIX_BF16), di, k, a))
+                del x
+        del raw_dev
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sizes = hn_synth.log_uniform_sizes(cfg["seed"], cfg["n_batches"], cfg["min_batch"], cfg["max_batch"])
+    pick = np.random.default_rng(cfg["seed"]).integers(0, len(indexes), cfg["n_batches"])
+    batches, raw_q = [], []
+    for b, (nq, g) in enumerate(zip(sizes, pick)):
+        ix, di, k, a = indexes[g]
+        qr, _ = hn_synth.queries_from(raws[di], int(nq), seed=10_000 + b)
+        qd = torch.from_numpy(qr).cuda()
+        raw_q.append((qd, k, a))
+        batches.append((ix, torch.empty_like(qd), torch.empty(int(nq), dtype=torch.int64, device="cuda"),
+                        torch.empty(int(nq), dtype=torch.float64, device="cuda")))
+    total_q = int(sizes.sum())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # queries reach a serving system already HN-normalised (HN is the descriptor
+    # network's last layer): normalise once, then time the multi-batch search
+    for (qd, k, a), (_, qn, _, _) in zip(raw_q, batches):
+        hn.normalize(qd, k, a, out=qn)
+
+    def step():
+        return hn.search_multi(batches, use_graph=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+        ms, outs = _timed_steps(torch, stream, args.steps, step, flush)
+    st = outs[-1]
+    if rank == 0:
+        line = {"metric": "exact 1-NN queries/s (batched serving, 256 uneven batches, 16 indexes)",
+                "value": world * total_q * args.steps / (sum(ms) / 1e3), "unit": "queries/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                "data": "synthetic",
+                "config": {"workload": "c4: 256 batches, sizes log-uniform 1..4096, databases N=100k/1M/4M/10M x "
+                                       "K in {8,16} x alpha in {1/32,1/8}, BF16 prefix",
+                           "queries_per_step": total_q, "n_indexes": len(indexes)},
+                "graph_replayed": st["graph_replayed"], "groups": st["n_groups"],
+                "batch_latency_ms": {"p50": st["batch_ms_p50"], "p99": st["batch_ms_p99"], "max": st["batch_ms_max"]},
+                "search_multi_ms": st["ms_total"], "survivors": st["survivors"],
+                "note": "step = one hn_search_multi over all 256 batches (queries HN-normalised beforehand); "
+                        "batch latency is measured from the start of the multi-search graph",
+                "clocks": clocks.summary(), "index_build_s": build_s}
+        print(json.dumps(line), flush=True)
+    for ix, *_ in indexes:
+        ix.close()
     return 0
 
 

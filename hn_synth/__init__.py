@@ -141,7 +141,16 @@ CONFIGS = {
     "c1": dict(n=1_000_000, nq=16_384, n_centres=200_000, k=16, alpha=1 / 8, seed=1),
     # reduced-precision prefix at N = 4M
     "c2": dict(n=4_000_000, nq=65_536, n_centres=800_000, k=16, alpha=1 / 8, seed=2),
+    # c2's data with 4,096 blocks for the learned proposal (1M training pairs from seed 1003)
+    "c3": dict(n=4_000_000, nq=65_536, n_centres=800_000, k=16, alpha=1 / 8, seed=2, n_blocks=4096,
+               n_train=1_000_000, train_seed=1003),
 }
+
+# Batched serving: 256 batches of log-uniform size in [1, 4096] over four databases
+# (N = 100k, 1M, 4M, 10M; centres N/5; seeds 1..4), each indexed for K in {8, 16} and
+# alpha in {1/32, 1/8}; every batch picks one of the 16 indexes uniformly.
+SERVING = dict(db_sizes=(100_000, 1_000_000, 4_000_000, 10_000_000), ks=(8, 16), alphas=(1 / 32, 1 / 8),
+               n_batches=256, min_batch=1, max_batch=4096, seed=4)
 
 
 def config_workload(name: str, n: int | None = None, nq: int | None = None) -> tuple[Workload, dict]:

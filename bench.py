@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS) + ["c4"])
-    ap.add_argument("--prefix", default=None, choices=["f32", "bf16"])
+    ap.add_argument("--prefix", default=None, choices=["f32", "bf16", "fp8"])
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
@@ -218,7 +218,7 @@ def main():
     wl, c = hn_synth.config_workload(args.workload)
     k, alpha = c["k"], c["alpha"]
     prefix_name = args.prefix or ("bf16" if args.workload == "c2" else "f32")
-    prefix = hn.PREFIX_BF16 if prefix_name == "bf16" else hn.PREFIX_F32
+    prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8}[prefix_name]
     scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE}[args.scan]
     stream = torch.cuda.current_stream()
 
@@ -308,8 +308,11 @@ def main():
     flops = 2.0 * nq * c["n"] * k_alg
     if st["scan"] == hn.SCAN_DENSE:
         peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+        src = f"{peak_src} bf16 sustained (cuBLAS)"
+        if prefix_name == "fp8":   # e4m3 operands: the bf16 figure x the nominal fp8/bf16 ratio 4.5/2.25
+            peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio)"
         roof = {"bound": "tensor", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained (cuBLAS)"}
+                "unit": "TFLOP/s", "peak_source": src}
     else:
         # CUDA-core FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
         smax = (clocks.summary().get("sm_max_mhz") or 2032.0)

@@ -51,14 +51,18 @@ typedef enum hn_status {
 /* Storage precision of the major prefix that the scan reads. */
 typedef enum hn_prefix {
     HN_PREFIX_F32 = 0,  /* binary32 prefix, scanned with FP32 FMA */
-    HN_PREFIX_BF16 = 1  /* bfloat16 prefix, scanned on the tensor cores (FP32 accumulation) */
+    HN_PREFIX_BF16 = 1, /* bfloat16 prefix, scanned on the tensor cores (FP32 accumulation) */
+    HN_PREFIX_FP8_E4M3 = 2 /* FP8 e4m3 prefix with a per-entry binary32 scale (a power of two, so
+                              that dequantisation is exact) and a per-entry rounding-error term;
+                              scanned on the tensor cores (FP32 accumulation) or dequantised on the
+                              CUDA cores.  K <= 64. */
 } hn_prefix;
 
 /* Which prefix-scan kernel runs (Phase 1 and Phase 2 of Algorithm 1). */
 typedef enum hn_scan {
     HN_SCAN_AUTO = 0,   /* pick by query count and prefix type */
     HN_SCAN_STREAM = 1, /* CUDA-core FMA scan streaming the prefix (any prefix type) */
-    HN_SCAN_DENSE = 2   /* tcgen05 tensor-core scan (HN_PREFIX_BF16 only) */
+    HN_SCAN_DENSE = 2   /* tcgen05 tensor-core scan (HN_PREFIX_BF16 and HN_PREFIX_FP8_E4M3) */
 } hn_scan;
 
 typedef struct hn_index_opts {
@@ -111,7 +115,8 @@ typedef struct hn_index_info {
     int64_t device_bytes;   /* device memory held by the index */
     float minor_norm_max;   /* max_i |x_i,minor| of the stored values, rounded up */
     float major_norm_max;   /* max_i |x_i,major|, rounded up */
-    float resid_norm_max;   /* max_i |x_i,major - prefix_i| (0 for HN_PREFIX_F32), rounded up */
+    float resid_norm_max;   /* max_i |x_i,major - prefix_i| (0 for HN_PREFIX_F32), rounded up;
+                               prefix_i = the dequantised stored prefix */
     float prefix_norm_max;  /* max_i |prefix_i|, rounded up */
     int32_t n_blocks;       /* block partition size (0: none) */
     int32_t reserved;

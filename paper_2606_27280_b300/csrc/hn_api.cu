@@ -5,6 +5,8 @@
 #include <atomic>
 #include <string>
 
+#include <cmath>
+
 #include "hn_internal.cuh"
 
 namespace hn {
@@ -72,6 +74,7 @@ static void free_index(Index *ix) {
     cudaFree(ix->pre32);
     cudaFree(ix->pre16);
     cudaFree(ix->pre16h);
+    cudaFree(ix->pre8);
     cudaFree(ix->mx);
     cudaFree(ix->dev_max);
     cudaFree(ix->block_ids);
@@ -159,7 +162,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     if (!x || !aligned16(x)) return fail(HN_ERR_INVALID_ARG, "null or unaligned x");
     hn_index_opts o{};
     if (opts) o = *opts;
-    if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16) return fail(HN_ERR_INVALID_ARG, "bad prefix type");
+    if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16 && o.prefix != HN_PREFIX_FP8_E4M3)
+        return fail(HN_ERR_INVALID_ARG, "bad prefix type");
     for (int i = 0; i < 4; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (o.n_blocks < 0 || o.n_blocks > n || o.n_blocks > (1 << 20))
@@ -175,7 +179,10 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     ix.alpha = alpha;
     ix.prefix = o.prefix;
     ix.k_pad16 = next_width(k, 16);
-    ix.k_pad4 = ix.prefix == HN_PREFIX_BF16 ? ix.k_pad16 : next_width(k, 8);
+    ix.k_pad4 = ix.prefix == HN_PREFIX_F32 ? next_width(k, 8) : ix.k_pad16;
+    // FP8: |q~_major| of an HN query is sqrt(1 - alpha) up to rounding; the per-entry
+    // error terms assume this bound (with margin) and the query slack covers any excess
+    ix.qt = std::nextafter((float)(std::sqrt(1.0 - alpha) * (1.0 + 1.0 / 64)), INFINITY);
     ix.n_tiles = (n + kTileE - 1) / kTileE;
     const int64_t n_pad = ix.n_tiles * kTileE;
     cudaError_t e = cudaSuccess;
@@ -191,6 +198,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     TRY(cudaMemsetAsync(ix.rows + n * kD, 0, (size_t)(n_pad - n) * kD * sizeof(float), s));
     if (ix.prefix == HN_PREFIX_F32) {
         TRY(dalloc(&ix.pre32, (size_t)n_pad * ix.k_pad4));
+    } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
+        TRY(dalloc(&ix.pre8, (size_t)(n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16)));
     } else {
         TRY(dalloc(&ix.pre16, (size_t)n_pad * ix.k_pad16));
         TRY(dalloc(&ix.pre16h, (size_t)n_pad * ix.k_pad16));
@@ -210,7 +219,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     TRY(cudaStreamSynchronize(s));
 #undef TRY
     ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
-               (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) + n * 4;
+               (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) +
+               (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) + n * 4;
     if (hs[ST_NOT_NORMALIZED]) {
         const int row = hs[ST_BAD_ROW];
         hn_index_destroy(h);
@@ -244,7 +254,7 @@ hn_status hn_index_get_info(const hn_index *index, hn_index_info *info) {
     info->k = ix.k;
     info->alpha = ix.alpha;
     info->prefix = ix.prefix;
-    info->k_pad = ix.prefix == HN_PREFIX_BF16 ? ix.k_pad16 : ix.k_pad4;
+    info->k_pad = ix.prefix == HN_PREFIX_F32 ? ix.k_pad4 : ix.k_pad16;
     info->device_bytes = ix.bytes;
     info->minor_norm_max = ix.host_max[0];
     info->major_norm_max = ix.host_max[1];
@@ -387,7 +397,7 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     const int scan = pick_scan(ix, nq, o.scan);
     if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
     if (scan == HN_SCAN_DENSE && !dense_scan_supported(ix))
-        return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 prefix index");
+        return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 or FP8 prefix index");
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->n_queries = nq;

@@ -14,6 +14,16 @@
 // accumulation and reduces packed f16 pairs; Phase 2, the certified bound test,
 // runs on the BF16 prefix with FP32 accumulation.
 //
+// FP8 index (F8): kind::f8f6f4 with e4m3 operands.  An entry tile holds kp
+// e4m3 bytes per entry plus its per-entry scales and error terms.  Each MMA
+// takes K = 32 bytes: the query side supplies 16 hi and 16 lo bytes of one
+// 16-column group, the entry side the same 16 bytes twice (its K-direction
+// core-matrix stride is 0), so acc = (hi + lo) . x^ costs no extra entry bytes.
+// The epilogue applies the per-entry scale and error term,
+//   Phase 2: u = fma(acc, s_i / 256, b_i) (packed FP32 pairs), tested against tau_q;
+//   Phase 1: FP16 product with s_i 2^11 (packed), max as for BF16;
+// it reads these from the stage, so every epilogue warp releases the stage.
+//
 // Persistent CTAs (one per SM, 19 warps):
 //   warp 0   producer: 1-D bulk copies of the 256-query unit (once per work unit)
 //            and of 16 KB stages of entry tiles into a ring in shared memory;
@@ -64,12 +74,12 @@ constexpr int kDE = 128;   // entries per B tile (MMA N)
 // several B tiles filled by one 16 KB copy, stages are released by the epilogue
 // with plain mbarrier arrivals (no commit), and two threads issue the MMAs, one
 // per accumulator buffer, each committing once per tile of its own.
-template <int KP, int PHASE>
+template <int KP, int PHASE, bool F8>
 struct DenseCfg {
-    static constexpr uint32_t kB = kDE * KP * 2;                    // bytes of one entry tile
+    static constexpr uint32_t kB = F8 ? (uint32_t)kF8TileBytes(KP) : kDE * KP * 2;  // bytes of one entry tile
     static constexpr int kTPS = kB >= 16384 ? 1 : 16384 / kB;       // entry tiles per stage
     static constexpr uint32_t kStageBytes = kTPS * kB;
-    static constexpr uint32_t kA = kDQ * KP * 2;                    // bytes of one query unit
+    static constexpr uint32_t kA = kDQ * KP * 2;                    // bytes of one query unit (FP8: hi + lo)
     static constexpr uint32_t kSurvBytes = PHASE == 2 ? kLcap * kEpiWarps * 32 * 4 : 0;  // [kLcap][512] ids
     // ring: 160 KB (Phase 1) / 128 KB (Phase 2), capped by what the 227 KB of shared
     // memory leaves after the two query units, the survivor staging and the barriers
@@ -107,9 +117,9 @@ __device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
     return fmaxf(__low2float(h[0]), __high2float(h[0]));
 }
 
-template <int KP, int PHASE>
+template <int KP, int PHASE, bool F8>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DenseParams p) {
-    using C = DenseCfg<KP, PHASE>;
+    using C = DenseCfg<KP, PHASE, F8>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
     uint8_t *sA = smem + C::kStages * C::kStageBytes;
@@ -124,7 +134,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::kStages; ++i) {
             mbar_init(smem_u32(&b_full[i]), 1);
-            mbar_init(smem_u32(&b_empty[i]), C::kTPS);  // one arrival per tile of the stage
+            // one arrival per tile of the stage (FP8: per tile and epilogue warp)
+            mbar_init(smem_u32(&b_empty[i]), F8 ? C::kTPS * kEpiWarps : C::kTPS);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&a_full[i]), 1);
@@ -187,7 +198,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
         if (lane == 0) {
             const uint32_t me = (uint32_t)(warp - 1);
             // Phase 1: FP16 operands, FP16 accumulator; Phase 2: BF16 operands, FP32 accumulator
-            constexpr uint32_t idesc = PHASE == 1 ? idesc_f16_f16(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE);
+            // FP8: e4m3 operands, FP16 (Phase 1) or FP32 (Phase 2) accumulator
+            constexpr uint32_t idesc = F8 ? (PHASE == 1 ? idesc_e4m3_f16(kTileQ, kDE) : idesc_e4m3_f32(kTileQ, kDE))
+                                          : (PHASE == 1 ? idesc_f16_f16(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE));
             uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, uses = 0;
             uint64_t g = 0;  // tile counter of this CTA
             bool ok = true;
@@ -211,11 +224,18 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                         for (int sub = 0; sub < kDQ / kTileQ; ++sub) {
 #pragma unroll
                             for (int kk = 0; kk < KP / 16; ++kk) {
-                                // 16 columns = two core matrices along K, 128 B apart; 8-row groups KP*16 B
-                                // apart; A tile `sub` = query rows 128*sub .. 128*sub+127
+                                // A: two core matrices along K, 128 B apart (BF16: 16 columns; FP8: the hi
+                                // and lo bytes of 16 columns); 8-row groups KP*16 B apart; A tile `sub` =
+                                // query rows 128*sub .. 128*sub+127
                                 const uint64_t ad = smem_desc(a_addr + sub * kTileQ * KP * 2 + kk * 256, 128, KP * 16);
-                                const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
-                                umma_bf16(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                if (F8) {
+                                    // entry side: the core matrix of columns 16kk.. read twice (K stride 0)
+                                    const uint64_t bd = smem_desc(b_addr + kk * 128, 0, KP * 8);
+                                    umma_f8(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                } else {
+                                    const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
+                                    umma_bf16(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                }
                             }
                         }
                         umma_commit(smem_u32(&acc_full[me]));
@@ -275,11 +295,31 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                     tc_fence_after();
                     // this tile's MMAs are done with the stage; the last tile of a short stage
                     // also arrives for the tiles the stage did not hold
-                    if (releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), j == nt - 1 ? 1 + C::kTPS - nt : 1);
+                    const uint32_t rel = j == nt - 1 ? 1 + C::kTPS - nt : 1;
+                    if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
                     const int32_t t = tt + j;
+                    // FP8: this warp's 64 per-entry scales / error terms in the stage
+                    const uint8_t *esc = smem + stage * C::kStageBytes + j * C::kB + (F8 ? f8_scale_off(KP) : 0);
                     if (PHASE == 1) {
                         uint32_t r[32];
                         tmem_ld64_f16(tmem + buf * 256 + seg * 64 + lane_addr, r);
+                        if (F8) {
+                            // FP16 products acc * (s_i 2^11), packed pairs
+                            const uint4 *h4 = reinterpret_cast<const uint4 *>(esc + 2 * kF8Tile * 4) + half * 8;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const uint4 hv = h4[i];
+                                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    __half2 a = *reinterpret_cast<__half2 *>(&r[4 * i + u]);
+                                    a = __hmul2(a, *reinterpret_cast<const __half2 *>(&hw[u]));
+                                    r[4 * i + u] = *reinterpret_cast<uint32_t *>(&a);
+                                }
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                        }
                         // the scores are in registers: hand the accumulator back to the MMA warp now
                         tc_fence_before();
                         __syncwarp();
@@ -294,6 +334,25 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                        if (F8) {
+                            // u = fma(acc, s_i / 256, b_i): one rounding, packed pairs
+                            const float4 *s4 = reinterpret_cast<const float4 *>(esc) + half * 16;
+                            const float4 *b4 = reinterpret_cast<const float4 *>(esc + kF8Tile * 4) + half * 16;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const float4 sv = s4[i], bv = b4[i];
+                                const float2 lo = __ffma2_rn(make_float2(v[4 * i], v[4 * i + 1]), make_float2(sv.x, sv.y),
+                                                             make_float2(bv.x, bv.y));
+                                const float2 hi = __ffma2_rn(make_float2(v[4 * i + 2], v[4 * i + 3]),
+                                                             make_float2(sv.z, sv.w), make_float2(bv.z, bv.w));
+                                v[4 * i] = lo.x;
+                                v[4 * i + 1] = lo.y;
+                                v[4 * i + 2] = hi.x;
+                                v[4 * i + 3] = hi.y;
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                        }
                         float gm[4];
 #pragma unroll
                         for (int k = 0; k < 4; ++k) gm[k] = max16(v + 16 * k);
@@ -367,19 +426,24 @@ int64_t dense_cand_slots(const Index &ix, int64_t nq) {
 }
 
 bool dense_scan_supported(const Index &ix) {
-    return ix.prefix == HN_PREFIX_BF16 && (ix.k_pad16 == 16 || ix.k_pad16 == 32 || ix.k_pad16 == 64);
+    return (ix.prefix == HN_PREFIX_BF16 || ix.prefix == HN_PREFIX_FP8_E4M3) &&
+           (ix.k_pad16 == 16 || ix.k_pad16 == 32 || ix.k_pad16 == 64);
 }
 
-template <int KP, int PHASE>
+template <int KP, int PHASE, bool F8>
 static int dense_smem() {
-    using C = DenseCfg<KP, PHASE>;
+    using C = DenseCfg<KP, PHASE, F8>;
     return (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
 }
 
-template <int KP, int PHASE>
-static cudaError_t set_attr() {
-    return cudaFuncSetAttribute(k_dense_scan<KP, PHASE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                dense_smem<KP, PHASE>());
+template <int KP, bool F8>
+static cudaError_t set_attr2() {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_scan<KP, 1, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         dense_smem<KP, 1, F8>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dense_scan<KP, 2, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dense_smem<KP, 2, F8>());
+    return e;
 }
 
 // Kernel attributes for every instantiation; called once before the first launch
@@ -387,23 +451,26 @@ static cudaError_t set_attr() {
 cudaError_t dense_init() {
     static cudaError_t done = cudaErrorNotReady;
     if (done == cudaErrorNotReady) {
-        cudaError_t e = set_attr<16, 1>();
-        if (e == cudaSuccess) e = set_attr<16, 2>();
-        if (e == cudaSuccess) e = set_attr<32, 1>();
-        if (e == cudaSuccess) e = set_attr<32, 2>();
-        if (e == cudaSuccess) e = set_attr<64, 1>();
-        if (e == cudaSuccess) e = set_attr<64, 2>();
+        cudaError_t e = set_attr2<16, false>();
+        if (e == cudaSuccess) e = set_attr2<32, false>();
+        if (e == cudaSuccess) e = set_attr2<64, false>();
+        if (e == cudaSuccess) e = set_attr2<16, true>();
+        if (e == cudaSuccess) e = set_attr2<32, true>();
+        if (e == cudaSuccess) e = set_attr2<64, true>();
         num_sms();
         done = e;
     }
     return done;
 }
 
-template <int KP, int PHASE>
-static cudaError_t launch_kp(const DenseParams &p, int grid, cudaStream_t st) {
+template <int KP, bool F8>
+static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStream_t st) {
     cudaError_t e = dense_init();
     if (e != cudaSuccess) return e;
-    k_dense_scan<KP, PHASE><<<grid, kDenseThreads, dense_smem<KP, PHASE>(), st>>>(p);
+    if (phase == 1)
+        k_dense_scan<KP, 1, F8><<<grid, kDenseThreads, dense_smem<KP, 1, F8>(), st>>>(p);
+    else
+        k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p);
     return cudaGetLastError();
 }
 
@@ -411,7 +478,10 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
     const Workspace &ws = ix.ws;
     DenseParams p{};
-    p.pre = phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
+    const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
+    // FP8: one tile array for both phases; the query operands differ (qpre16h: Phase-1 e4m3 of 16 q,
+    // qpre16: Phase-2 hi/lo e4m3 of 256 q)
+    p.pre = f8 ? (const void *)ix.pre8 : phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
     p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
     p.n = ix.n;
     p.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
@@ -429,9 +499,9 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     p.status = ws.status;
     const int grid = (int)min64(G, p.n_units);
     switch (ix.k_pad16) {
-        case 16: return phase == 1 ? launch_kp<16, 1>(p, grid, st) : launch_kp<16, 2>(p, grid, st);
-        case 32: return phase == 1 ? launch_kp<32, 1>(p, grid, st) : launch_kp<32, 2>(p, grid, st);
-        case 64: return phase == 1 ? launch_kp<64, 1>(p, grid, st) : launch_kp<64, 2>(p, grid, st);
+        case 16: return f8 ? launch_kp<16, true>(p, phase, grid, st) : launch_kp<16, false>(p, phase, grid, st);
+        case 32: return f8 ? launch_kp<32, true>(p, phase, grid, st) : launch_kp<32, false>(p, phase, grid, st);
+        case 64: return f8 ? launch_kp<64, true>(p, phase, grid, st) : launch_kp<64, false>(p, phase, grid, st);
     }
     return cudaErrorNotSupported;
 }

@@ -67,8 +67,9 @@ struct Workspace {
     int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
     float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
-    __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles
-    __half *qpre16h = nullptr;         // same in FP16 (dense Phase 1)
+    __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles (FP8 index:
+                                       //   the e4m3 hi/lo pairs of Phase 2, 2 * k_pad16 bytes a query)
+    __half *qpre16h = nullptr;         // same in FP16 (dense Phase 1; FP8 index: e4m3 hi, lo = 0)
     float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
     float *qnorm = nullptr;            // [q_cap] |q| rounded up
     int32_t *status = nullptr;         // [8] device status words
@@ -92,6 +93,8 @@ struct Index {
     float *pre32 = nullptr;          // [n][k_pad4] FP32 prefix (HN_PREFIX_F32)
     __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
     __half *pre16h = nullptr;        // FP16 copy of the same prefix (dense Phase 1 candidate search)
+    uint8_t *pre8 = nullptr;         // HN_PREFIX_FP8_E4M3: [n_tiles * 2] tiles of kF8TileBytes(k_pad16)
+    float qt = 0.f;                  // FP8: |q~_major| bound the per-entry error terms assume
     float *mx = nullptr;             // [n] |x_minor| rounded up
     float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
@@ -117,6 +120,25 @@ __host__ __device__ inline int64_t pre16_offset(int64_t e, int c, int k_pad16) {
     const int64_t g = e >> 3;
     const int r = (int)(e & 7);
     return g * (int64_t)k_pad16 * 16 + (int64_t)(c >> 3) * 128 + r * 16 + (c & 7) * 2;
+}
+
+// ---------------------------------------------------------------- FP8 prefix
+// An FP8 index stores the major prefix as e4m3 with a per-entry power-of-two scale
+// s_i (dequantisation x~ = s_i * x^ is exact), in 128-entry tiles:
+//   [128 x kp e4m3 values, UMMA core-matrix order: 8-entry groups of kp/16 core
+//    matrices of 8 rows x 16 bytes]
+//   [128 x float  s_i / kF8QScale]      (scale of the Phase-2 tensor-core product)
+//   [128 x float  b_i = RU(qt * r_i)]   (r_i = |x_i,major - x~_i|: per-entry error term)
+//   [128 x half   s_i * 2^11]           (scale of the Phase-1 FP16 product)
+constexpr int kF8Tile = 128;
+constexpr float kF8QScale = 256.f;   // Phase-2 query prefix scale (hi + lo e4m3 parts)
+constexpr float kF8QScale1 = 16.f;   // Phase-1 query prefix scale (FP16 accumulation stays finite)
+constexpr float kF8HScale = 2048.f;  // Phase-1 entry scale factor
+__host__ __device__ constexpr int64_t kF8TileBytes(int kp) { return (int64_t)kF8Tile * (kp + 10); }
+__host__ __device__ inline int64_t f8_scale_off(int kp) { return (int64_t)kF8Tile * kp; }
+// byte offset of (row r, byte column c) in a K-major UMMA tile whose rows hold `row_bytes` bytes
+__host__ __device__ inline int64_t umma8_offset(int64_t r, int c, int row_bytes) {
+    return (r >> 3) * (int64_t)row_bytes * 8 + (int64_t)(c >> 4) * 128 + (r & 7) * 16 + (c & 15);
 }
 
 // search pipeline pieces (hn_api.cu), shared with the multi-batch path

@@ -1,6 +1,8 @@
 // HN normalisation (Eq. 1), index packing (§6.1 SoA layout) and query preparation.
 #include <math.h>
 
+#include <cuda_fp8.h>
+
 #include "hn_internal.cuh"
 
 namespace hn {
@@ -82,6 +84,25 @@ __device__ inline float4 bf16_round4(float4 v) {
                        __bfloat162float(__float2bfloat16_rn(v.z)), __bfloat162float(__float2bfloat16_rn(v.w)));
 }
 
+// ------------------------------------------------------------------ FP8 e4m3
+// Per-entry scale of the FP8 prefix: the smallest power of two s with
+// amax / s <= 448 (the largest finite e4m3 value), so the largest component
+// uses the top binade of e4m3 and x~ = s * x^ is exact.  amax = 0 (padding) -> 1.
+__device__ inline float f8_entry_scale(float amax) {
+    if (!(amax > 0.f)) return 1.f;
+    int ex;
+    frexp((double)amax / 448.0, &ex);
+    double s = ldexp(1.0, ex);
+    if ((double)amax > 448.0 * s) s *= 2.0;
+    return (float)fmax(s, 0x1p-126);
+}
+__device__ inline uint8_t f8_encode(float v) {
+    return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ inline float f8_decode(uint8_t b) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3)));
+}
+
 // ------------------------------------------------------------------ index build
 // One warp per entry (grid-stride).  Lane l owns dimensions 4l..4l+3.  Writes
 // the FP32 master row, the prefix in the index precision, |x_minor| rounded up,
@@ -91,6 +112,7 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
                                               int prefix, int k_pad4, int k_pad16, int64_t n_pad,
                                               float *__restrict__ rows, float *__restrict__ pre32,
                                               __nv_bfloat16 *__restrict__ pre16, __half *__restrict__ pre16h,
+                                              uint8_t *__restrict__ pre8, float qt,
                                               float *__restrict__ mx, float *dev_max, int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -114,6 +136,19 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
         for (int j = 0; j < 4; ++j) pv[j] = (c0 + j < k) ? vv[j] : 0.f;
         float4 p4 = make_float4(pv[0], pv[1], pv[2], pv[3]);
         if (prefix == HN_PREFIX_BF16) p4 = bf16_round4(p4);
+        float sc = 1.f;
+        uint32_t f8 = 0;  // this lane's 4 e4m3 codes
+        if (prefix == HN_PREFIX_FP8_E4M3) {
+            sc = f8_entry_scale(warp_max(fmaxf(fmaxf(fabsf(pv[0]), fabsf(pv[1])), fmaxf(fabsf(pv[2]), fabsf(pv[3])))));
+            float dq[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint8_t b = f8_encode(pv[j] / sc);  // division by a power of two: exact
+                f8 |= (uint32_t)b << (8 * j);
+                dq[j] = f8_decode(b) * sc;                // exact
+            }
+            p4 = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        }
         const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
         double res2 = 0, pre2 = 0;
 #pragma unroll
@@ -136,10 +171,24 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             hk.y = *reinterpret_cast<uint32_t *>(&hhi);
             *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16h) + pre16_offset(e, c0, k_pad16)) = hk;
         }
+        uint8_t *tile8 = nullptr;
+        if (prefix == HN_PREFIX_FP8_E4M3) {
+            tile8 = pre8 + (e >> 7) * kF8TileBytes(k_pad16);
+            if (c0 < k_pad16) *reinterpret_cast<uint32_t *>(tile8 + umma8_offset(e & 127, c0, k_pad16)) = f8;
+        }
         maj2 = warp_sum(maj2);
         min2 = warp_sum(min2);
         res2 = warp_sum(res2);
         pre2 = warp_sum(pre2);
+        if (tile8 && lane == 0) {
+            // per-entry scale and error term b_i = RU(qt * r_i) (a product of two binary32 values is
+            // exact in binary64); padding rows get b = 0 and are never reported
+            float *sc2 = reinterpret_cast<float *>(tile8 + f8_scale_off(k_pad16));
+            const int r = (int)(e & 127);
+            sc2[r] = sc / kF8QScale;
+            sc2[kF8Tile + r] = e < n ? __double2float_ru((double)qt * (double)sqrt_up(res2)) : 0.f;
+            reinterpret_cast<__half *>(sc2 + 2 * kF8Tile)[r] = __float2half_rn(sc * kF8HScale);
+        }
         if (e < n) {
             const float umin = sqrt_up(min2), umaj = sqrt_up(maj2), ures = sqrt_up(res2);
             const float upre = sqrt_up(pre2), ufull = sqrt_up(maj2 + min2);
@@ -173,7 +222,8 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
     int64_t blocks = (n_pad * 32 + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
     k_pack<<<(unsigned)blocks, 256, 0, st>>>(x, ix.n, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16, n_pad,
-                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.mx, ix.dev_max, ix.ws.status);
+                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.pre8, ix.qt, ix.mx, ix.dev_max,
+                                             ix.ws.status);
     return cudaGetLastError();
 }
 
@@ -182,16 +232,20 @@ cudaError_t launch_check_hn(const float *, int64_t, int, double, int32_t *, cuda
 }
 
 // ------------------------------------------------------------------ queries
-// One warp per query.  Produces the query prefix in the scan precision, the
-// UMMA A-tile copy (BF16), |q| rounded up, and the Phase-2 slack
+// One warp per query.  Produces the query prefix in the scan precision (exact
+// FP32 for an FP8 index), the UMMA A-tile copies (BF16 and FP16, or the e4m3
+// operands of an FP8 index), |q| rounded up, and the Phase-2 slack
 //   E_q >= scan error + |q_minor| * max_i |x_i,minor| + binary64 rounding of the oracle,
 // rounded up to binary32.  Scan error:
 //   FP32 prefix: gamma_kp * |q_major| * max|x_major|  (recursive FMA summation, Higham Thm 3.1)
 //   BF16 prefix: |q_major| * max r(x) + r(q) * max|x^| + gamma' * |q^| * max|x^|,
 //     with r(.) the residual norm of the BF16 rounding and gamma' = (kp+2) 2^-20,
 //     a deliberately loose accumulation term for the tensor cores' FP32 adder.
+//   FP8 prefix: the per-query part of the bound derived below; the per-entry part
+//     b_i rides with the entry and is added inside the scan.
 __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q, int64_t nq, int64_t nq_pad,
                                                     int k, double alpha, int prefix, int k_pad4, int k_pad16,
+                                                    float qt,
                                                     const float *__restrict__ dev_max, float *__restrict__ qpre32,
                                                     __nv_bfloat16 *__restrict__ qpre16, __half *__restrict__ qpre16h,
                                                     float *__restrict__ qeps,
@@ -221,6 +275,42 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         pre2 += (double)pp[t] * (double)pp[t];
     }
     if (c0 < k_pad4) reinterpret_cast<float4 *>(qpre32 + j * k_pad4)[lane] = p4;
+    // FP8 index: Phase-2 A operand = e4m3 hi and lo parts of 256 q (q~ = (hi + lo) / 256 carries
+    // about 8 significant bits), Phase-1 A operand = e4m3 of 16 q with the lo slots zero.
+    // A row holds 2 * k_pad16 bytes: for every 16 prefix columns, 16 hi bytes then 16 lo bytes.
+    double rq2 = 0, hi2 = 0, lo2 = 0, qt2 = 0;
+    if (prefix == HN_PREFIX_FP8_E4M3) {
+        uint32_t hw = 0, lw = 0, h1 = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float a = pv[t] * kF8QScale;                   // exact
+            const uint8_t hb = f8_encode(a);
+            const float hf = f8_decode(hb);
+            const uint8_t lb = f8_encode(a - hf);                 // a - hf is exact
+            const float lf = f8_decode(lb);
+            hw |= (uint32_t)hb << (8 * t);
+            lw |= (uint32_t)lb << (8 * t);
+            h1 |= (uint32_t)f8_encode(pv[t] * kF8QScale1) << (8 * t);
+            const double qq = ((double)hf + (double)lf) / kF8QScale;  // exact
+            const double r = (double)pv[t] - qq;
+            rq2 += r * r;
+            hi2 += (double)hf * hf;
+            lo2 += (double)lf * lf;
+            qt2 += qq * qq;
+        }
+        if (c0 < k_pad16) {
+            const int bc = 32 * (c0 >> 4) + (c0 & 15);
+            uint8_t *a2 = reinterpret_cast<uint8_t *>(qpre16), *a1 = reinterpret_cast<uint8_t *>(qpre16h);
+            *reinterpret_cast<uint32_t *>(a2 + umma8_offset(j, bc, 2 * k_pad16)) = hw;
+            *reinterpret_cast<uint32_t *>(a2 + umma8_offset(j, bc + 16, 2 * k_pad16)) = lw;
+            *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc, 2 * k_pad16)) = h1;
+            *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc + 16, 2 * k_pad16)) = 0u;
+        }
+        rq2 = warp_sum(rq2);
+        hi2 = warp_sum(hi2);
+        lo2 = warp_sum(lo2);
+        qt2 = warp_sum(qt2);
+    }
     if (prefix == HN_PREFIX_BF16 && c0 < k_pad16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(p4.x, p4.y), hi = __floats2bfloat162_rn(p4.z, p4.w);
         uint2 pk;
@@ -245,6 +335,22 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     if (prefix == HN_PREFIX_F32) {
         const double g = k_pad4 * 0x1p-24 / (1.0 - k_pad4 * 0x1p-24);
         scan = g * qmaj * xmaj;
+    } else if (prefix == HN_PREFIX_FP8_E4M3) {
+        // With x~_i = s_i x^_i (exact), q~ = (hi + lo) / 256 and b_i = RU(qt r_i):
+        //   q.x_i = q~.x~_i + (q - q~).x_i + q~.(x_i - x~_i)
+        //        <= q~.x~_i + r(q) max|x_major| + |q~| r_i,      |q~| r_i <= b_i + (|q~| - qt)+ max r.
+        // The tensor-core scan forms u_i = fma(acc_i, s_i / 256, b_i) with acc_i = (hi + lo).x^_i
+        // summed from 2 kp exact products (accumulation error <= (2kp+2) 2^-20 Qa |x~_i|,
+        // Qa = (|hi| + |lo|) / 256, the same deliberately loose term as for BF16), one rounding;
+        // the CUDA-core scan forms RN(sum_d q_d x~_d + b_i) with the exact FP32 q (FMA chain
+        // error <= gamma_kp |q| |x~_i|).  One slack covers both.
+        const double qa = ((double)sqrt_up(hi2) + (double)sqrt_up(lo2)) / kF8QScale;
+        const double qtil = sqrt_up(qt2), rq = sqrt_up(rq2);
+        const double g = k_pad16 * 0x1p-24 / (1.0 - k_pad16 * 0x1p-24);
+        const double acc = fmax((2 * k_pad16 + 2) * 0x1p-20 * qa * xhat, g * qmaj * xhat);
+        const double excess = fmax(0.0, fmax(qtil, qmaj) - (double)qt) * xres;
+        const double u_round = 0x1p-23 * (fmax(qa, qmaj) * xhat * (1.0 + 0x1p-10) + (double)qt * xres);
+        scan = acc + rq * xmaj + excess + u_round;
     } else {
         const double g = (k_pad16 + 2) * 0x1p-20;
         scan = qmaj * xres + qres * xhat + g * qhat * xhat;
@@ -259,7 +365,7 @@ cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaS
     const int64_t nq_pad = (nq + kQPad - 1) / kQPad * kQPad;
     const int64_t blocks = (nq_pad * 32 + 255) / 256;
     k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
-                                                   ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
+                                                   ix.qt, ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
                                                    ix.ws.qnorm, ix.ws.status);
     return cudaGetLastError();
 }

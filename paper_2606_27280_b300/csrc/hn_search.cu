@@ -3,6 +3,8 @@
 // and the FP32 brute-force baseline.
 #include <math.h>
 
+#include <cuda_fp8.h>
+
 #include "hn_internal.cuh"
 
 namespace hn {
@@ -15,20 +17,26 @@ namespace hn {
 // exact zeros), whose error is bounded by gamma_KT * sum |q_c x_c|.
 //   PHASE 1: per-query best (score, lowest index) -> atomicMax on key1[q].
 //   PHASE 2: every entry with score >= tau[q] is appended to q's survivor slots.
+// FMT selects the stored prefix: 0 FP32, 1 BF16 (UMMA order), 2 FP8 e4m3 tiles,
+// dequantised exactly (x~ = s_i x^) while staging; in Phase 2 the FP8 score is
+// RN(acc + b_i) with the entry's error term b_i (see the FP8 slack in hn_prep.cu).
 // The same kernel with KT = 128 over the full rows is the brute-force baseline.
 constexpr int kSQ = 64;     // queries per CTA
 constexpr int kSE = 256;    // entries per tile
 constexpr int kKC = 16;     // prefix columns staged per step
 
-template <int KT, bool BF16, int PHASE>
+enum { FMT_F32 = 0, FMT_BF16 = 1, FMT_FP8 = 2 };
+
+template <int KT, int FMT, int PHASE>
 __global__ void __launch_bounds__(256, 2)
-k_stream_scan(const float *__restrict__ e32, const __nv_bfloat16 *__restrict__ e16, int64_t n, int64_t n_tiles,
+k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64_t n, int64_t n_tiles,
               int64_t tiles_per_cta, const float *__restrict__ qpre, int64_t nq, const float *__restrict__ tau,
               unsigned long long *__restrict__ key1, int32_t *__restrict__ bucket, int32_t *__restrict__ count,
               int cap) {
     constexpr int KC = KT < kKC ? KT : kKC;
     __shared__ float sq[KT][kSQ];
     __shared__ float se[KC][kSE];
+    __shared__ float sb[FMT == FMT_FP8 ? kSE : 1];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kSQ;
     for (int i = tid; i < kSQ * KT; i += 256) {
@@ -53,14 +61,31 @@ k_stream_scan(const float *__restrict__ e32, const __nv_bfloat16 *__restrict__ e
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
         const int64_t e = t * kSE + tid;  // entry staged by this thread
+        const uint8_t *tile8 = FMT == FMT_FP8
+                                   ? static_cast<const uint8_t *>(e16) + (e >> 7) * kF8TileBytes(KT) : nullptr;
+        float esc = 1.f;
+        if (FMT == FMT_FP8) {
+            const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(KT));
+            esc = sc2[e & 127] * kF8QScale;  // exact: powers of two
+            if (PHASE == 2) sb[tid] = sc2[kF8Tile + (e & 127)];
+        }
 #pragma unroll 1
         for (int c0 = 0; c0 < KT; c0 += KC) {
             __syncthreads();
-            if (BF16) {
+            if (FMT == FMT_FP8) {
+                const uint4 raw = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, c0, KT));
+                const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
+                    se[2 * u][tid] = f.x * esc;
+                    se[2 * u + 1][tid] = f.y * esc;
+                }
+            } else if (FMT == FMT_BF16) {
 #pragma unroll
                 for (int c = 0; c < KC; c += 8) {
                     const uint4 raw = *reinterpret_cast<const uint4 *>(
-                        reinterpret_cast<const char *>(e16) + pre16_offset(e, c0 + c, KT));
+                        static_cast<const char *>(e16) + pre16_offset(e, c0 + c, KT));
                     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -95,6 +120,15 @@ k_stream_scan(const float *__restrict__ e32, const __nv_bfloat16 *__restrict__ e
         }
         const int64_t ebase = t * kSE + lane;
         const bool tail = (t + 1) * kSE > n;
+        if (FMT == FMT_FP8 && PHASE == 2) {
+            float b[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) b[j] = sb[lane + 32 * j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += b[j];
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float m = acc[i][0];
@@ -138,8 +172,8 @@ k_stream_scan(const float *__restrict__ e32, const __nv_bfloat16 *__restrict__ e
     }
 }
 
-template <int KT, bool BF16>
-static cudaError_t stream_scan_kt(const float *e32, const __nv_bfloat16 *e16, int64_t n, int64_t n_tiles,
+template <int KT, int FMT>
+static cudaError_t stream_scan_kt(const float *e32, const void *e16, int64_t n, int64_t n_tiles,
                                   const float *qpre, int64_t nq, int phase, const Workspace &ws, cudaStream_t st) {
     const int64_t qt = (nq + kSQ - 1) / kSQ;
     // enough CTAs for ~8 per SM; consecutive CTAs share an entry range (L2 reuse)
@@ -150,10 +184,10 @@ static cudaError_t stream_scan_kt(const float *e32, const __nv_bfloat16 *e16, in
     if (qt > 0x7FFFFFFF || splits > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)qt, (unsigned)splits);
     if (phase == 1)
-        k_stream_scan<KT, BF16, 1><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
+        k_stream_scan<KT, FMT, 1><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
                                                          ws.bucket, ws.count, ws.bucket_cap);
     else
-        k_stream_scan<KT, BF16, 2><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
+        k_stream_scan<KT, FMT, 2><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
                                                          ws.bucket, ws.count, ws.bucket_cap);
     return cudaGetLastError();
 }
@@ -162,16 +196,23 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
     const Workspace &ws = ix.ws;
     if (ix.prefix == HN_PREFIX_BF16) {
         switch (ix.k_pad16) {
-            case 16: return stream_scan_kt<16, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 32: return stream_scan_kt<32, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 64: return stream_scan_kt<64, true>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 16: return stream_scan_kt<16, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 32: return stream_scan_kt<32, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 64: return stream_scan_kt<64, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+        }
+    } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
+        // exact FP32 query prefix (k_pad16 wide) against the dequantised FP8 prefix
+        switch (ix.k_pad16) {
+            case 16: return stream_scan_kt<16, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 32: return stream_scan_kt<32, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 64: return stream_scan_kt<64, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
         }
     } else {
         switch (ix.k_pad4) {
-            case 8: return stream_scan_kt<8, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 16: return stream_scan_kt<16, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 32: return stream_scan_kt<32, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 64: return stream_scan_kt<64, false>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 8: return stream_scan_kt<8, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 16: return stream_scan_kt<16, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 32: return stream_scan_kt<32, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 64: return stream_scan_kt<64, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
         }
     }
     return cudaErrorInvalidValue;
@@ -202,6 +243,21 @@ __device__ inline float warp_sum_f(float v) {
 
 __device__ inline float rescore_eps(float qn, float xn_max) {
     return __fmul_ru(__fmul_ru(qn, xn_max), 128 * 0x1p-24 / (1 - 128 * 0x1p-24) + 1e-12f);
+}
+
+// FP32 prefix score of entry e read from its master row: qp is zero beyond k, so
+// the minor coordinates the loop also reads contribute exact zeros (FP8 index)
+__device__ inline float prefix_score_rows(const float *__restrict__ rows, int64_t e, const float *qp, int kp) {
+    const float *x = rows + e * kD;
+    float s = 0.f;
+    for (int c = 0; c < kp; c += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(x + c);
+        s = fmaf(qp[c], v.x, s);
+        s = fmaf(qp[c + 1], v.y, s);
+        s = fmaf(qp[c + 2], v.z, s);
+        s = fmaf(qp[c + 3], v.w, s);
+    }
+    return s;
 }
 
 // FP32 prefix score of entry e against the query prefix qp (BF16 values, k_pad16 wide)
@@ -258,7 +314,8 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
             for (int i = lane; i < seg_entries; i += 32) {
                 const int64_t ei = e0 + i;
                 if (ei < n) {
-                    const unsigned long long kk = pack_best(prefix_score16(pre16, ei, qp, kp), (uint32_t)ei);
+                    const float sc = pre16 ? prefix_score16(pre16, ei, qp, kp) : prefix_score_rows(rows, ei, qp, kp);
+                    const unsigned long long kk = pack_best(sc, (uint32_t)ei);
                     kb = kk > kb ? kk : kb;
                 }
             }
@@ -304,6 +361,8 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
             float sc;
             if (pre16) {
                 sc = prefix_score16(pre16, e, qp, kp);
+            } else if (!pre32) {
+                sc = prefix_score_rows(rows, e, qp, kp);
             } else {
                 sc = 0.f;
                 const float *xe = pre32 + (int64_t)e * kp;
@@ -329,9 +388,8 @@ cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, cons
                                cudaStream_t st) {
     const Workspace &ws = ix.ws;
     const int64_t gblocks = (nq * 32 + 255) / 256;
-    const bool bf = ix.prefix == HN_PREFIX_BF16;
-    k_seed_blocks<<<(unsigned)gblocks, 256, 0, st>>>(ix.rows, q, nq, bf ? nullptr : ix.pre32, bf ? ix.pre16 : nullptr,
-                                                     bf ? ix.k_pad16 : ix.k_pad4, ws.qpre32, blocks, topk,
+    // FP32 and BF16 indexes score candidates on their stored prefix, an FP8 index on its master rows
+    k_seed_blocks<<<(unsigned)gblocks, 256, 0, st>>>(ix.rows, q, nq, ix.pre32, ix.pre16, ix.k_pad4, ws.qpre32, blocks, topk,
                                                      ix.block_start, ix.block_ids, ws.qeps, ws.qnorm, ix.host_max[4],
                                                      ws.tau, ws.count);
     return cudaGetLastError();
@@ -343,10 +401,10 @@ cudaError_t stream_argmax_f32(const float *db_pre, int64_t n_db, int64_t n_db_ti
     Workspace w{};
     w.key1 = keys;
     switch (kp) {
-        case 8: return stream_scan_kt<8, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
-        case 16: return stream_scan_kt<16, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
-        case 32: return stream_scan_kt<32, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
-        case 64: return stream_scan_kt<64, false>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 8: return stream_scan_kt<8, FMT_F32>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 16: return stream_scan_kt<16, FMT_F32>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 32: return stream_scan_kt<32, FMT_F32>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
+        case 64: return stream_scan_kt<64, FMT_F32>(db_pre, nullptr, n_db, n_db_tiles, q_pre, nq, 1, w, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -356,7 +414,7 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     const int64_t blocks = (nq * 32 + 255) / 256;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, dense ? ws.cand : ws.key1,
                                                        dense ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
-                                                       ix.k_pad16, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4],
+                                                       ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4],
                                                        ws.tau, ws.count);
     return cudaGetLastError();
 }
@@ -497,7 +555,7 @@ cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64
     // master copy is allocated with that padding (zeros).
     cudaError_t e = cudaMemsetAsync(ix.ws.key1, 0, sizeof(unsigned long long) * nq, st);
     if (e != cudaSuccess) return e;
-    e = stream_scan_kt<128, false>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, ix.ws, st);
+    e = stream_scan_kt<128, FMT_F32>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, ix.ws, st);
     if (e != cudaSuccess) return e;
     k_brute_finish<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(ix.ws.key1, nq, out_idx, out_sim);
     return cudaGetLastError();
@@ -509,7 +567,7 @@ cudaError_t launch_bruteforce_keys(const Index &ix, const float *q, int64_t nq, 
     if (e != cudaSuccess) return e;
     Workspace w = ix.ws;  // same scan, keys redirected to the caller's array
     w.key1 = keys;
-    e = stream_scan_kt<128, false>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, w, st);
+    e = stream_scan_kt<128, FMT_F32>(ix.rows, nullptr, ix.n, ix.n_tiles, q, nq, 1, w, st);
     if (e != cudaSuccess) return e;
     k_brute_finish<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(keys, nq, out_idx, out_sim);
     return cudaGetLastError();

@@ -193,3 +193,8 @@ def test_config1_full_size_sampled(hn):
 def test_config2_full_size_sampled_bf16(hn):
     st = _sampled_parity(hn, "c2", prefix=1, scan=0, n_sample=128)
     assert st["n_queries"] == 65536
+
+
+def test_config2_full_size_sampled_fp8(hn):
+    st = _sampled_parity(hn, "c2", prefix=2, scan=0, n_sample=128)
+    assert st["n_queries"] == 65536 and st["scan"] == 2

@@ -83,7 +83,13 @@ typedef struct hn_search_opts {
     int32_t seed_topk;    /* blocks the proposal contributes per query (with `seed`); 0 = 4 */
     const hn_proposal *seed; /* NULL: plain search.  Otherwise the proposal's top blocks give the
                                 threshold and the Phase-1 scan is skipped (result unchanged) */
-    int32_t reserved[2];  /* must be zero */
+    int32_t soft;         /* 0: exact search.  1: soft ANN mode (the threshold relaxation of §7): the
+                             admissible minor bound alpha of the skip test becomes beta, i.e. the
+                             stored-norm minor bound is scaled by beta / alpha; beta = alpha is the
+                             exact search, smaller beta prunes more and may miss the true neighbour;
+                             the best fully scored threshold candidate always stays a candidate (as
+                             Algorithm 1 keeps its Phase-1 winner).  1-NN only (hn_search_batch) */
+    float beta;           /* with soft = 1: 0 <= beta <= alpha (else HN_ERR_INVALID_ARG) */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */
@@ -201,6 +207,24 @@ hn_status hn_index_get_info(const hn_index *index, hn_index_info *info);
  */
 hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts,
                           int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
+
+/*
+ * Exact top-k search (an extension of the problem statement of §3.3, which asks
+ * for the single nearest neighbour): for every query the k entries of largest
+ * binary64 inner product <q_j, x_i> (as defined for hn_search_batch), in the order
+ * (similarity descending, index ascending), so that rank 0 is hn_search_batch's
+ * answer.  out_idx[j * k + r] and out_sim[j * k + r] (nq * k int64 / double) give
+ * rank r of query j.  Requires 1 <= k <= min(32, n).
+ * Steps: Algorithm 1 with the threshold T_q certified for the k-th best (the k-th
+ * largest of the lower bounds of k distinct fully scored Phase-1 candidates; an
+ * entry whose bound is below T_q cannot be among the k best), the same Phase-2
+ * bound test, FP32 rescore of the survivors, and binary64 scores for every survivor
+ * within the FP32 error band of the k-th FP32 score.  opts as for hn_search_batch;
+ * opts->seed (the proposal) and opts->soft are not supported for k > 1 (HN_ERR_UNSUPPORTED).
+ * Errors, scratch storage and synchronisation as for hn_search_batch.
+ */
+hn_status hn_search_topk(hn_index *index, const float *q, int64_t nq, int32_t k, const hn_search_opts *opts,
+                         int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
 
 /*
  * Batched serving (an extension of the method; the paper searches one query

@@ -283,12 +283,13 @@ hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *
 // With `timing`, events ev[0..5] bracket the steps on stream s.
 // With a proposal (`seed`), its top blocks give the threshold and Phase 1 is skipped.
 static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
-                            int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s) {
+                            int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn,
+                            float minor_scale) {
     Workspace &ws = ix.ws;
     auto mark = [&](int i) { return timing ? cudaEventRecord(ws.ev[i], s) : cudaSuccess; };
     HN_CUDA(cudaMemsetAsync(ws.key1, 0, sizeof(unsigned long long) * nq, s));
     HN_CUDA(mark(0));
-    HN_CUDA(launch_query_prep(ix, q, nq, s));
+    HN_CUDA(launch_query_prep(ix, q, nq, minor_scale, s));
     HN_CUDA(mark(1));
     if (seed) {
         int32_t *blocks = nullptr;
@@ -296,16 +297,18 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         HN_CUDA(proposal_scratch(sp, nq * topk, &blocks));
         HN_CUDA(proposal_topk(sp, q, nq, topk, blocks, s));
         HN_CUDA(mark(2));
-        HN_CUDA(launch_seed_blocks(ix, q, nq, blocks, topk, s));
+        HN_CUDA(launch_seed_blocks(ix, q, nq, blocks, topk, minor_scale < 1.f, s));
     } else {
-        HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s) : launch_stream_scan(ix, nq, 1, s));
+        HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s)
+                                      : launch_stream_scan(ix, nq, 1, s, nn > 1 ? ws.cand : nullptr));
         HN_CUDA(mark(2));
-        HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, s));
+        HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, nn, minor_scale < 1.f, s));
     }
     HN_CUDA(mark(3));
     HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
     HN_CUDA(mark(4));
-    HN_CUDA(launch_rescore(ix, q, nq, out_idx, out_sim, s));
+    HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s)
+                   : launch_rescore(ix, q, nq, out_idx, out_sim, s));
     HN_CUDA(mark(5));
     return HN_OK;
 }
@@ -320,12 +323,13 @@ int pick_scan(const Index &ix, int64_t nq, int requested) {
 }
 
 // Size the index's scratch for nq queries and `cap` survivor slots (may allocate).
-hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap) {
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn) {
     Workspace &ws = ix.ws;
     hn_status st = ensure_ws(ix, nq, cap);
     if (st != HN_OK) return st;
-    if (scan == HN_SCAN_DENSE) {
-        const int64_t slots = dense_cand_slots(ix, nq);
+    if (scan == HN_SCAN_DENSE || nn > 1) {
+        // candidate keys: dense segments, or one entry per stream-scan entry range (top-k)
+        const int64_t slots = scan == HN_SCAN_DENSE ? dense_cand_slots(ix, nq) : stream_cand_slots(ix, nq);
         const int64_t need = ((nq + kQPad - 1) / kQPad * kQPad) * slots;
         if (need > ws.cand_cap) {
             cudaFree(ws.cand);
@@ -344,11 +348,11 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap) {
 // be captured into a CUDA graph.  Status words and counters land in the pinned
 // host mirror ws.h_status once the stream has run.
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
-                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s) {
+                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn, float minor_scale) {
     Workspace &ws = ix.ws;
     HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
     HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
-    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s);
+    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
     if (st != HN_OK) return st;
     HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -376,23 +380,29 @@ int32_t default_cap(const Index &ix) {
 
 }  // namespace hn
 
-extern "C" {
-
-hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts, int64_t *out_idx,
-                          double *out_sim, hn_search_stats *stats, void *stream) {
+// hn_search_batch (nn = 1) and hn_search_topk (nn = k): validation, scratch sizing,
+// the search pipeline, overflow re-runs and statistics.
+static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn, const hn_search_opts *opts,
+                             int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream) {
     if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
     Index &ix = index->ix;
     if (nq < 0 || nq > (int64_t)1 << 30) return fail(HN_ERR_INVALID_ARG, "need 0 <= nq <= 2^30");
+    if (nn < 1 || nn > 32 || nn > ix.n) return fail(HN_ERR_INVALID_ARG, "need 1 <= k <= min(32, n)");
     hn_search_opts o{};
     if (opts) o = *opts;
-    for (int i = 0; i < 2; ++i)
-        if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.soft != 0 && o.soft != 1) return fail(HN_ERR_INVALID_ARG, "soft must be 0 or 1");
+    if (o.soft && !(o.beta >= 0.f && (double)o.beta <= ix.alpha * (1.0 + 1e-6)))
+        return fail(HN_ERR_INVALID_ARG, "soft mode needs 0 <= beta <= alpha");
+    if (o.soft && nn > 1) return fail(HN_ERR_UNSUPPORTED, "the soft mode serves the 1-NN search only");
+    // soft ANN mode: the minor bound scaled by beta / alpha <= 1 (alpha = 0: no minor part at all)
+    const float minor_scale = o.soft && ix.alpha > 0 ? (float)std::min(1.0, (double)o.beta / ix.alpha) : 1.f;
     if (o.bucket_cap < 0) return fail(HN_ERR_INVALID_ARG, "bucket_cap < 0");
     const int topk = o.seed_topk ? o.seed_topk : 4;
     if (o.seed) {
         if (proposal_blocks(o.seed) != ix.n_blocks || proposal_k(o.seed) != ix.k)
             return fail(HN_ERR_INVALID_ARG, "the proposal was not trained for this index's blocks");
         if (topk < 1 || topk > 64 || topk > ix.n_blocks) return fail(HN_ERR_INVALID_ARG, "need 1 <= seed_topk <= 64");
+        if (nn > 1) return fail(HN_ERR_UNSUPPORTED, "the proposal seeds the 1-NN search only");
     }
     const int scan = pick_scan(ix, nq, o.scan);
     if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
@@ -416,9 +426,9 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
     }
     int32_t reruns = 0, kernels = 0;
     for (;;) {
-        hn_status st = prepare_search(ix, nq, scan, cap);
+        hn_status st = prepare_search(ix, nq, scan, cap, nn);
         if (st != HN_OK) return st;
-        st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s);
+        st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
         if (st != HN_OK) return st;
         kernels += o.seed ? 4 + 5 * (int32_t)((nq + 8191) / 8192) : 5;
         HN_CUDA(cudaStreamSynchronize(s));
@@ -447,6 +457,18 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
         cap = want;
         ++reruns;
     }
+}
+
+extern "C" {
+
+hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts, int64_t *out_idx,
+                          double *out_sim, hn_search_stats *stats, void *stream) {
+    return search_impl(index, q, nq, 1, opts, out_idx, out_sim, stats, stream);
+}
+
+hn_status hn_search_topk(hn_index *index, const float *q, int64_t nq, int32_t k, const hn_search_opts *opts,
+                         int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream) {
+    return search_impl(index, q, nq, k, opts, out_idx, out_sim, stats, stream);
 }
 
 hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,

@@ -143,9 +143,11 @@ __host__ __device__ inline int64_t umma8_offset(int64_t r, int c, int row_bytes)
 
 // search pipeline pieces (hn_api.cu), shared with the multi-batch path
 int pick_scan(const Index &ix, int64_t nq, int requested);
-hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap);
+// nn: neighbours per query (1: the 1-NN; 2..32: exact top-nn, outputs [nq][nn])
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn = 1);
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
-                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s);
+                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn = 1,
+                         float minor_scale = 1.f);
 hn_status check_search(Index &ix, int64_t nq, int32_t *want_cap);
 int32_t default_cap(const Index &ix);
 Index *index_state_mut(hn_index *h);
@@ -156,10 +158,20 @@ cudaError_t launch_normalize(const float *in, float *out, int64_t n, int k, doub
 cudaError_t launch_check_hn(const float *x, int64_t n, int k, double alpha, int32_t *status,
                             cudaStream_t s);
 cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t s);
-cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t s);
-cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
+// minor_scale: 1 for the exact search; beta / alpha in the soft ANN mode
+cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, float minor_scale, cudaStream_t s);
+// cand != NULL (Phase 1): one best entry per entry range into cand[q][stream_cand_slots], else key1
+cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s,
+                               unsigned long long *cand = nullptr);
+int64_t stream_cand_slots(const Index &ix, int64_t nq);
 cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t s);
-cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, cudaStream_t s);
+// kk: the threshold certifies the kk-th best similarity (1 for the 1-NN)
+// keep_best (soft ANN mode): the best scored candidate is put into survivor slot 0
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, int kk, bool keep_best,
+                                  cudaStream_t s);
+// Exact top-kk of every query from its Phase-2 survivors (1 <= kk <= 32): out_idx/out_sim [nq][kk].
+cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
+                                double *out_sim, cudaStream_t s);
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                            double *out_sim, cudaStream_t s);
 cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
@@ -173,7 +185,7 @@ bool dense_scan_supported(const Index &ix);
 cudaError_t dense_init();
 cudaError_t build_blocks(Index &ix, int n_blocks, int iters, cudaStream_t s);
 cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
-                               cudaStream_t s);
+                               bool keep_best, cudaStream_t s);
 // proposal helpers (hn_mlp.cu)
 cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, cudaStream_t s);
 cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);

@@ -245,7 +245,7 @@ cudaError_t launch_check_hn(const float *, int64_t, int, double, int32_t *, cuda
 //     b_i rides with the entry and is added inside the scan.
 __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q, int64_t nq, int64_t nq_pad,
                                                     int k, double alpha, int prefix, int k_pad4, int k_pad16,
-                                                    float qt,
+                                                    float qt, float minor_scale,
                                                     const float *__restrict__ dev_max, float *__restrict__ qpre32,
                                                     __nv_bfloat16 *__restrict__ qpre16, __half *__restrict__ qpre16h,
                                                     float *__restrict__ qeps,
@@ -356,16 +356,17 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         scan = qmaj * xres + qres * xhat + g * qhat * xhat;
     }
     // the oracle's own binary64 rounding: <= 128 * 2^-53 * |q| |x| < 1e-13 for unit vectors
-    const double e = (scan + qmin * xmin) * (1.0 + 1e-9) + 1e-12;
+    // (soft ANN mode: minor_scale = beta / alpha < 1 relaxes the minor bound; 1 is exact)
+    const double e = (scan + (double)minor_scale * qmin * xmin) * (1.0 + 1e-9) + 1e-12;
     qeps[j] = __double2float_ru(e);
     qnorm[j] = __double2float_ru(sqrt_up(maj2 + min2));
 }
 
-cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, cudaStream_t st) {
+cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, float minor_scale, cudaStream_t st) {
     const int64_t nq_pad = (nq + kQPad - 1) / kQPad * kQPad;
     const int64_t blocks = (nq_pad * 32 + 255) / 256;
     k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
-                                                   ix.qt, ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
+                                                   ix.qt, minor_scale, ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
                                                    ix.ws.qnorm, ix.ws.status);
     return cudaGetLastError();
 }

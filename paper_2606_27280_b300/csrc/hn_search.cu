@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256, 2)
 k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64_t n, int64_t n_tiles,
               int64_t tiles_per_cta, const float *__restrict__ qpre, int64_t nq, const float *__restrict__ tau,
               unsigned long long *__restrict__ key1, int32_t *__restrict__ bucket, int32_t *__restrict__ count,
-              int cap) {
+              int cap, unsigned long long *__restrict__ cand) {
     constexpr int KC = KT < kKC ? KT : kKC;
     __shared__ float sq[KT][kSQ];
     __shared__ float se[KC][kSE];
@@ -167,52 +167,71 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                 kbest = other > kbest ? other : kbest;
             }
             const int64_t qg = q0 + w * 8 + i;
-            if (lane == 0 && qg < nq && kbest) atomicMax(key1 + qg, kbest);
+            // top-1: the query's best entry; top-k: one best entry per entry range (CTA column)
+            if (lane == 0 && qg < nq) {
+                if (cand) cand[qg * (int64_t)gridDim.y + blockIdx.y] = kbest;
+                else if (kbest) atomicMax(key1 + qg, kbest);
+            }
         }
     }
 }
 
-template <int KT, int FMT>
-static cudaError_t stream_scan_kt(const float *e32, const void *e16, int64_t n, int64_t n_tiles,
-                                  const float *qpre, int64_t nq, int phase, const Workspace &ws, cudaStream_t st) {
+// Entry ranges (CTA columns) of the stream scan for nq queries: enough CTAs for ~8 per
+// SM; consecutive CTAs share an entry range (L2 reuse).
+static void stream_split(int64_t n_tiles, int64_t nq, int64_t *splits_out, int64_t *tpc_out) {
     const int64_t qt = (nq + kSQ - 1) / kSQ;
-    // enough CTAs for ~8 per SM; consecutive CTAs share an entry range (L2 reuse)
     int64_t splits = (148 * 8 + qt - 1) / qt;
     splits = max64(1, min64(splits, n_tiles));
     const int64_t tpc = (n_tiles + splits - 1) / splits;
-    splits = (n_tiles + tpc - 1) / tpc;
+    *splits_out = (n_tiles + tpc - 1) / tpc;
+    *tpc_out = tpc;
+}
+
+int64_t stream_cand_slots(const Index &ix, int64_t nq) {
+    int64_t splits = 0, tpc = 0;
+    stream_split(ix.n_tiles, nq, &splits, &tpc);
+    return splits;
+}
+
+template <int KT, int FMT>
+static cudaError_t stream_scan_kt(const float *e32, const void *e16, int64_t n, int64_t n_tiles,
+                                  const float *qpre, int64_t nq, int phase, const Workspace &ws, cudaStream_t st,
+                                  unsigned long long *cand = nullptr) {
+    const int64_t qt = (nq + kSQ - 1) / kSQ;
+    int64_t splits = 0, tpc = 0;
+    stream_split(n_tiles, nq, &splits, &tpc);
     if (qt > 0x7FFFFFFF || splits > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((unsigned)qt, (unsigned)splits);
     if (phase == 1)
         k_stream_scan<KT, FMT, 1><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
-                                                         ws.bucket, ws.count, ws.bucket_cap);
+                                                         ws.bucket, ws.count, ws.bucket_cap, cand);
     else
         k_stream_scan<KT, FMT, 2><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
-                                                         ws.bucket, ws.count, ws.bucket_cap);
+                                                         ws.bucket, ws.count, ws.bucket_cap, nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
+cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st, unsigned long long *cand) {
     const Workspace &ws = ix.ws;
     if (ix.prefix == HN_PREFIX_BF16) {
         switch (ix.k_pad16) {
-            case 16: return stream_scan_kt<16, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 32: return stream_scan_kt<32, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 64: return stream_scan_kt<64, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 16: return stream_scan_kt<16, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 32: return stream_scan_kt<32, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 64: return stream_scan_kt<64, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
         }
     } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
         // exact FP32 query prefix (k_pad16 wide) against the dequantised FP8 prefix
         switch (ix.k_pad16) {
-            case 16: return stream_scan_kt<16, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 32: return stream_scan_kt<32, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 64: return stream_scan_kt<64, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 16: return stream_scan_kt<16, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 32: return stream_scan_kt<32, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 64: return stream_scan_kt<64, FMT_FP8>(nullptr, ix.pre8, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
         }
     } else {
         switch (ix.k_pad4) {
-            case 8: return stream_scan_kt<8, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 16: return stream_scan_kt<16, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 32: return stream_scan_kt<32, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
-            case 64: return stream_scan_kt<64, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st);
+            case 8: return stream_scan_kt<8, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 16: return stream_scan_kt<16, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 32: return stream_scan_kt<32, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+            case 64: return stream_scan_kt<64, FMT_F32>(ix.pre32, nullptr, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
         }
     }
     return cudaErrorInvalidValue;
@@ -220,19 +239,22 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 
 // ------------------------------------------------------------------ threshold
 // Algorithm 1, step 2, with more than one Phase-1 candidate.  Phase 1 leaves S
-// candidate keys (prefix score, id) per query: for the stream scan S = 1 and
-// the id is the best entry; for the dense scan S = 4 x chunks and the id names
-// a 64-entry segment (tile * 4 + segment) whose maximum (FP16) prefix score is
-// the key.  One warp per query takes the R best keys; for a segment it recomputes
-// the 64 prefix scores from the stored prefixes (FP32 FMA) and keeps the best valid
-// entry.  Each chosen entry is scored in full in FP32 (lane l owns dims
-// 4l..4l+3), and
-//   T_q = max_j RD(fp32_j - eps_r) <= max_j <q, x_j> (binary64, the oracle's value)
-// is a certified lower bound on the final maximum (eps_r bounds the FP32 error
-// of a 128-term sum in any order).  Any entry is a valid candidate: the choice
-// only decides how tight T_q is.  The Phase-2 prefix threshold is
+// candidate keys (prefix score, id) per query: for the stream scan S = 1 (top-1)
+// or one per entry range (top-k), the id being an entry; for the dense scan
+// S = 2 x chunks and the id names a 64-entry segment (128-entry tile * 2 + half)
+// whose maximum (FP16) prefix score is the key.  One warp per query takes the
+// R = max(4, kk) best keys; for a segment it recomputes the 64 prefix scores from
+// the stored prefixes (FP32 FMA) and keeps the best valid entry, so the R entries
+// are distinct.  Each chosen entry is scored in full in FP32 (lane l owns dims
+// 4l..4l+3), giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j>
+// (binary64, the oracle's value; eps_r bounds the FP32 error of a 128-term sum in
+// any order).  T_q is the kk-th largest of these bounds (the largest for the
+// 1-NN): at least kk entries score >= T_q, so the kk-th best similarity is >= T_q
+// (-inf when fewer than kk entries were found).  Any entry is a valid candidate:
+// the choice only decides how tight T_q is.  The Phase-2 prefix threshold is
 //   tau_q = RD(T_q - E_q),
-// so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  the entry cannot win.
+// so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  the entry cannot
+// be among the kk best.
 constexpr int kSeedR = 4;
 
 __device__ inline float warp_sum_f(float v) {
@@ -281,19 +303,23 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                                                         int S, int seg_entries, const __nv_bfloat16 *__restrict__ pre16,
                                                         int kp, const float *__restrict__ qpre32,
                                                         const float *__restrict__ qeps,
-                                                        const float *__restrict__ qnorm, float xnorm_max,
-                                                        float *__restrict__ tau, int32_t *__restrict__ count) {
+                                                        const float *__restrict__ qnorm, float xnorm_max, int kk,
+                                                        float *__restrict__ tau, int32_t *__restrict__ count,
+                                                        int32_t *__restrict__ bucket, int cap, int keep_best) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= nq) return;
     if (lane == 0) count[j] = 0;
     const unsigned long long *cj = cand + j * (int64_t)S;
+    const int R = kk > kSeedR ? kk : kSeedR;
+    float lb = -INFINITY;  // lane r: the bound of the entry found in round r
+    int64_t lb_e = -1;     // and that entry
+    int found = 0;
     const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
     const float *qp = qpre32 + j * kp;
     const float eps_r = rescore_eps(qnorm[j], xnorm_max);
-    float t_low = -INFINITY;
     unsigned long long taken = ~0ull;
-    for (int r = 0; r < kSeedR; ++r) {
+    for (int r = 0; r < R; ++r) {
         unsigned long long km = 0;
         for (int s = lane; s < S; s += 32) {
             const unsigned long long k = cj[s];
@@ -315,8 +341,8 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                 const int64_t ei = e0 + i;
                 if (ei < n) {
                     const float sc = pre16 ? prefix_score16(pre16, ei, qp, kp) : prefix_score_rows(rows, ei, qp, kp);
-                    const unsigned long long kk = pack_best(sc, (uint32_t)ei);
-                    kb = kk > kb ? kk : kb;
+                    const unsigned long long key = pack_best(sc, (uint32_t)ei);
+                    kb = key > kb ? key : kb;
                 }
             }
 #pragma unroll
@@ -329,9 +355,38 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
         }
         const float4 xv = reinterpret_cast<const float4 *>(rows + e * kD)[lane];
         const float sim = warp_sum_f(fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w))));
-        t_low = fmaxf(t_low, __fsub_rd(sim, eps_r));
+        if (lane == found) { lb = __fsub_rd(sim, eps_r); lb_e = e; }
+        ++found;
+    }
+    // the kk-th largest bound: the lane whose value has exactly kk-1 larger ones (ties by lane)
+    float t_low = -INFINITY;
+    if (found >= kk) {
+        int rank = 0;
+        for (int o = 0; o < found; ++o) {
+            const float v = __shfl_sync(0xffffffffu, lb, o);
+            rank += (v > lb || (v == lb && o < lane)) ? 1 : 0;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, lane < found && rank == kk - 1);
+        t_low = __shfl_sync(0xffffffffu, lb, __ffs(hit) - 1);
     }
     if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+    if (keep_best && found > 0) {
+        // soft ANN mode: the relaxed bound may prune every entry, the scored candidates
+        // included; like Algorithm 1's Phase-1 winner, the best candidate is always kept
+        // (survivor slot 0; Phase 2 appends after it)
+        float bv = lb;
+        int64_t be = lb_e;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int64_t oe = __shfl_xor_sync(0xffffffffu, be, o);
+            if (oe >= 0 && (be < 0 || ov > bv || (ov == bv && oe < be))) { bv = ov; be = oe; }
+        }
+        if (lane == 0 && be >= 0 && cap > 0) {
+            bucket[j * (int64_t)cap] = (int32_t)be;
+            count[j] = 1;
+        }
+    }
 }
 
 // Threshold from the learned proposal: for each of the query's top-k blocks, the
@@ -344,7 +399,8 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
                                                      int topk, const int32_t *__restrict__ block_start,
                                                      const int32_t *__restrict__ block_ids, const float *__restrict__ qeps,
                                                      const float *__restrict__ qnorm, float xnorm_max,
-                                                     float *__restrict__ tau, int32_t *__restrict__ count) {
+                                                     float *__restrict__ tau, int32_t *__restrict__ count,
+                                                     int32_t *__restrict__ bucket, int cap, int keep_best) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= nq) return;
@@ -353,6 +409,7 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
     const float *qp = qpre32 + j * kp;
     const float eps_r = rescore_eps(qnorm[j], xnorm_max);
     float t_low = -INFINITY;
+    int64_t t_e = -1;  // the entry giving t_low
     for (int r = 0; r < topk; ++r) {
         const int32_t b = blocks[j * topk + r];
         unsigned long long kb = 0;
@@ -379,19 +436,26 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
         if (kb == 0ull) continue;
         const float4 xv = reinterpret_cast<const float4 *>(rows + (int64_t)best_idx(kb) * kD)[lane];
         const float sim = warp_sum_f(fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w))));
-        t_low = fmaxf(t_low, __fsub_rd(sim, eps_r));
+        const float lbv = __fsub_rd(sim, eps_r);
+        if (lbv > t_low) { t_low = lbv; t_e = best_idx(kb); }
     }
-    if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+    if (lane == 0) {
+        tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+        if (keep_best && t_e >= 0 && cap > 0) {  // soft ANN mode: keep the best candidate (see above)
+            bucket[j * (int64_t)cap] = (int32_t)t_e;
+            count[j] = 1;
+        }
+    }
 }
 
 cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
-                               cudaStream_t st) {
+                               bool keep_best, cudaStream_t st) {
     const Workspace &ws = ix.ws;
     const int64_t gblocks = (nq * 32 + 255) / 256;
     // FP32 and BF16 indexes score candidates on their stored prefix, an FP8 index on its master rows
     k_seed_blocks<<<(unsigned)gblocks, 256, 0, st>>>(ix.rows, q, nq, ix.pre32, ix.pre16, ix.k_pad4, ws.qpre32, blocks, topk,
                                                      ix.block_start, ix.block_ids, ws.qeps, ws.qnorm, ix.host_max[4],
-                                                     ws.tau, ws.count);
+                                                     ws.tau, ws.count, ws.bucket, ws.bucket_cap, keep_best ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -409,13 +473,16 @@ cudaError_t stream_argmax_f32(const float *db_pre, int64_t n_db, int64_t n_db_ti
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, cudaStream_t st) {
+cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, int kk, bool keep_best,
+                                  cudaStream_t st) {
     const Workspace &ws = ix.ws;
     const int64_t blocks = (nq * 32 + 255) / 256;
-    k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, dense ? ws.cand : ws.key1,
-                                                       dense ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
-                                                       ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4],
-                                                       ws.tau, ws.count);
+    // candidates: dense segments, or (top-k) the stream scan's per-range entries, or its best entry
+    const bool multi = dense || kk > 1;
+    k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
+                                                       multi ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
+                                                       ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
+                                                       ws.tau, ws.count, ws.bucket, ws.bucket_cap, keep_best ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -529,6 +596,163 @@ __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows,
         out_idx[j] = bi;
         out_sim[j] = bs;
     }
+}
+
+// Exact top-kk (1 <= kk <= 32), one warp per query.  Pass 1 finds f_k, the kk-th
+// largest FP32 score among the survivors (lane r holds the r-th largest value).
+// Every entry of the exact top-kk has binary64 score >= f_k - eps_r (kk survivors
+// score at least that), so its FP32 score is >= f_k - 2 eps_r: pass 2 scores the
+// survivors in that band in binary64 in dimension order (the oracle's value) and the
+// kk largest by (score desc, index asc) are the answer.  Band members sit two per
+// lane (<= 64); a larger band falls back to binary64 for every survivor.
+__device__ inline bool topk_before(double s, int64_t i, double s2, int64_t i2) {
+    return i2 < 0 || (i >= 0 && (s > s2 || (s == s2 && i < i2)));
+}
+
+__global__ void __launch_bounds__(256) k_rescore_topk(const float *__restrict__ rows, const float *__restrict__ q,
+                                                      int64_t nq, const int32_t *__restrict__ bucket,
+                                                      const int32_t *__restrict__ count, int cap,
+                                                      const float *__restrict__ qnorm, float xnorm_max, int kk,
+                                                      int64_t *__restrict__ out_idx, double *__restrict__ out_sim,
+                                                      int32_t *__restrict__ status, long long *__restrict__ counters) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    const int cnt = count[j];
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SURVIVORS), (unsigned long long)cnt);
+        atomicMax(reinterpret_cast<unsigned long long *>(counters + CT_MAXSURV), (unsigned long long)cnt);
+    }
+    if (cnt > cap) {  // survivors were dropped: the host re-runs with more slots
+        if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
+        return;
+    }
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float eps = rescore_eps(qnorm[j], xnorm_max);
+    const float band = __fmul_ru(2.f, eps);
+    const int32_t *bk = bucket + j * (int64_t)cap;
+    constexpr int U = 8;  // survivor rows in flight per warp
+    // FP32 scores of survivors s0 .. s0+U-1 (warp-uniform after the butterfly)
+    auto scores = [&](int s0, float (&part)[U], int32_t (&id)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            id[u] = (s0 + u < cnt) ? bk[s0 + u] : -1;
+            float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (id[u] >= 0) xv = reinterpret_cast<const float4 *>(rows + (int64_t)id[u] * kD)[lane];
+            part[u] = fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w)));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+    };
+    // pass 1: the kk largest FP32 scores, descending over lanes 0 .. kk-1
+    float top = -INFINITY;
+    int filled = 0;
+    for (int s0 = 0; s0 < cnt; s0 += U) {
+        float part[U];
+        int32_t id[U];
+        scores(s0, part, id);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (id[u] < 0) continue;
+            const float v = part[u];
+            const float kth = __shfl_sync(0xffffffffu, top, kk - 1);
+            if (filled < kk || v > kth) {
+                const int p = __popc(__ballot_sync(0xffffffffu, lane < filled && top >= v));
+                const float up = __shfl_up_sync(0xffffffffu, top, 1);
+                if (lane > p && lane < kk) top = up;
+                if (lane == p) top = v;
+                filled = filled < kk ? filled + 1 : kk;
+            }
+        }
+    }
+    const float fk = filled >= kk ? __shfl_sync(0xffffffffu, top, kk - 1) : -INFINITY;
+    const float lo = fk == -INFINITY ? -INFINITY : __fsub_rd(fk, band);
+    // pass 2: band members, member m at lane m % 32, slot m / 32
+    int32_t m0 = -1, m1 = -1;
+    int nm = 0;
+    bool spill = false;
+    for (int s0 = 0; s0 < cnt; s0 += U) {
+        float part[U];
+        int32_t id[U];
+        scores(s0, part, id);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (id[u] < 0 || part[u] < lo) continue;
+            if (nm < 64) {
+                if (lane == (nm & 31)) {
+                    if (nm < 32) m0 = id[u]; else m1 = id[u];
+                }
+                ++nm;
+            } else {
+                spill = true;
+            }
+        }
+    }
+    const float *qj = q + j * kD;
+    double prev_s = INFINITY;
+    int64_t prev_i = -1;
+    if (!spill) {
+        double v0 = -INFINITY, v1 = -INFINITY;
+        if (m0 >= 0) v0 = dot64_seq(qj, rows + (int64_t)m0 * kD);
+        if (m1 >= 0) v1 = dot64_seq(qj, rows + (int64_t)m1 * kD);
+        bool t0 = m0 < 0, t1 = m1 < 0;  // taken (or empty)
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)nm);
+        for (int r = 0; r < kk; ++r) {
+            double bs = -INFINITY;
+            int64_t bi = -1;
+            if (!t0) { bs = v0; bi = m0; }
+            if (!t1 && topk_before(v1, m1, bs, bi)) { bs = v1; bi = m1; }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
+            }
+            if (!t0 && bi == m0) t0 = true;
+            else if (!t1 && bi == m1) t1 = true;
+            if (lane == 0) {
+                out_idx[j * kk + r] = bi;
+                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+            }
+        }
+    } else {
+        // more than 64 band members: binary64 for every survivor, one rank per sweep
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt * kk);
+        for (int r = 0; r < kk; ++r) {
+            double bs = -INFINITY;
+            int64_t bi = -1;
+            for (int t = lane; t < cnt; t += 32) {
+                const int32_t id = bk[t];
+                const double v = dot64_seq(qj, rows + (int64_t)id * kD);
+                // eligible: after the previous rank in (score desc, index asc) order
+                if (prev_i >= 0 && !topk_before(prev_s, prev_i, v, id)) continue;
+                if (topk_before(v, id, bs, bi)) { bs = v; bi = id; }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
+            }
+            prev_s = bs;
+            prev_i = bi;
+            if (lane == 0) {
+                out_idx[j * kk + r] = bi;
+                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+            }
+        }
+    }
+}
+
+cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
+                                double *out_sim, cudaStream_t st) {
+    const int64_t blocks = (nq * 32 + 255) / 256;
+    k_rescore_topk<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
+                                                     ix.ws.qnorm, ix.host_max[4], kk, out_idx, out_sim, ix.ws.status,
+                                                     ix.ws.counters);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,

@@ -33,7 +33,8 @@ class IndexOpts(ctypes.Structure):
 
 class SearchOpts(ctypes.Structure):
     _fields_ = [("scan", ctypes.c_int32), ("bucket_cap", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
+                ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("soft", ctypes.c_int32),
+                ("beta", ctypes.c_float)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -103,6 +104,7 @@ SIGNATURES = {
     "hn_index_destroy": ([_vp], _i32),
     "hn_index_get_info": ([_vp, _vp], _i32),
     "hn_search_batch": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _i32),
+    "hn_search_topk": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "hn_index_blocks": ([_vp, _vp, _vp, _vp, _vp], _i32),
     "hn_search_multi": ([_vp, _i32, _vp, _vp, _vp], _i32),
@@ -242,10 +244,12 @@ class Index:
     def search(self, q: torch.Tensor, scan: int = SCAN_AUTO, bucket_cap: int = 0, stats: bool = False,
                timing: bool = False,
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
-               proposal: "Proposal | None" = None, seed_topk: int = 0,
+               proposal: "Proposal | None" = None, seed_topk: int = 0, beta: float | None = None,
                stream=None) -> SearchResult:
         """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
-        `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped."""
+        `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped.
+        `beta` (0 <= beta <= alpha) selects the soft ANN mode: alpha in the skip test becomes
+        beta (beta = alpha is exact)."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         if out_idx is None:
@@ -253,11 +257,27 @@ class Index:
         if out_sim is None:
             out_sim = torch.empty(nq, dtype=torch.float64, device=q.device)
         opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), timing=int(bool(timing)),
-                          seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None)
+                          seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None,
+                          soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0)
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),
                                     out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
                                     _stream(stream)), "hn_search_batch")
+        return SearchResult(out_idx, out_sim, st.as_dict() if st is not None else None)
+
+    def search_topk(self, q: torch.Tensor, k: int, scan: int = SCAN_AUTO, bucket_cap: int = 0,
+                    stats: bool = False, stream=None) -> SearchResult:
+        """Exact top-k of every row of q: idx / sim of shape (nq, k), by similarity
+        descending then index ascending (rank 0 = the 1-NN)."""
+        q = _dev_f32(q, "q")
+        nq = q.shape[0]
+        out_idx = torch.empty((nq, k), dtype=torch.int64, device=q.device)
+        out_sim = torch.empty((nq, k), dtype=torch.float64, device=q.device)
+        opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap))
+        st = SearchStats() if stats else None
+        _check(_lib.hn_search_topk(self._h, q.data_ptr(), nq, int(k), ctypes.byref(opts), out_idx.data_ptr(),
+                                   out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
+                                   _stream(stream)), "hn_search_topk")
         return SearchResult(out_idx, out_sim, st.as_dict() if st is not None else None)
 
     def bruteforce(self, q: torch.Tensor, stream=None) -> SearchResult:

@@ -188,10 +188,25 @@ def cpu_baseline(wl, c, budget_s: float = 12.0):
             "seconds": dt}
 
 
+def default_prefix(workload: str) -> str:
+    return "bf16" if workload == "c2" else "f32"
+
+
+def workload_config(workload: str, c: dict, prefix_name: str, world: int) -> dict:
+    """The `config` of a bench line; the reference arm prints the same one."""
+    k, alpha, nq = c["k"], c["alpha"], c["nq"]
+    return {"workload": f"{workload}: N={c['n']} entries, Q={nq} queries per step, D=128, K={k}, "
+                        f"alpha={alpha}, {c['n_centres']} centres, {prefix_name} prefix",
+            "n": c["n"], "queries_per_step": nq, "k": k, "alpha": alpha, "prefix": prefix_name,
+            "parallelism": f"replicated index, {world} GPU(s), independent query batches",
+            "l2": "flushed before every timed step (256 MiB write); index 2 GiB > L2"}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return 0
-    wl, c = hn_synth.config_workload(args.workload if args.workload in hn_synth.CONFIGS else "c2")
+    workload = args.workload if args.workload in ("c0", "c1", "c2") else "c2"
+    wl, c = hn_synth.config_workload(workload)
     per_step, total_q = [], 0
     import oracle
     db = oracle.normalize(wl.db_raw, c["k"], c["alpha"])
@@ -212,11 +227,10 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": "exact 1-NN queries/s", "value": value, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": c["n"], "queries_per_step": m, "k": c["k"],
-                       "alpha": c["alpha"], "d": 128},
+            "config": workload_config(workload, c, args.prefix or default_prefix(workload), args.gpus),
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{m} queries per step against all {c['n']} entries (binary64 exhaustive "
-                                       f"search incl. query normalisation)"},
+                             "sample": f"{m} of the {c['nq']} queries per step against all {c['n']} entries "
+                                       f"(binary64 exhaustive search incl. query normalisation)"},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -253,7 +267,7 @@ def main():
 
     wl, c = hn_synth.config_workload(args.workload)
     k, alpha = c["k"], c["alpha"]
-    prefix_name = args.prefix or ("bf16" if args.workload == "c2" else "f32")
+    prefix_name = args.prefix or default_prefix(args.workload)
     prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8}[prefix_name]
     scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE}[args.scan]
     stream = torch.cuda.current_stream()
@@ -367,11 +381,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prefix_name,
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: N={c['n']} entries, Q={nq} queries per step, D=128, K={k}, "
-                               f"alpha={alpha}, {c['n_centres']} centres, {prefix_name} prefix",
-                   "n": c["n"], "queries_per_step": nq, "k": k, "alpha": alpha, "prefix": prefix_name,
-                   "parallelism": f"replicated index, {world} GPU(s), independent query batches",
-                   "l2": "flushed before every timed step (256 MiB write); index 2 GiB > L2"},
+        "config": workload_config(args.workload, c, prefix_name, world),
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * 128 * 4,
                 "d2h_bytes_per_step": nq * (8 + 8)},

@@ -188,6 +188,23 @@ def cpu_baseline(wl, c, budget_s: float = 12.0):
             "seconds": dt}
 
 
+def rank_queries(wl, c: dict, rank: int) -> np.ndarray:
+    """The query batch of one rank: the workload's own queries on rank 0, further batches
+    drawn the same way from seeded streams of their own on the other ranks (weak scaling:
+    every rank answers a full, different batch against its own copy of the index)."""
+    if rank == 0:
+        return wl.q_raw
+    return hn_synth.queries_from(wl.db_raw, c["nq"], seed=c["seed"] * 7919 + rank)[0]
+
+
+def max_over_ranks(torch, t_local: float, dist, device: str) -> float:
+    """The slowest rank's time (seconds); the job's throughput divides all ranks' work by it."""
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def default_prefix(workload: str) -> str:
     return "bf16" if workload == "c2" else "f32"
 
@@ -283,7 +300,7 @@ def main():
     del db_raw, db
     info = ix.info()
 
-    q_host = torch.from_numpy(wl.q_raw).pin_memory()
+    q_host = torch.from_numpy(rank_queries(wl, c, rank)).pin_memory()
     q_raw = q_host.cuda()
     nq = q_raw.shape[0]
     q_norm = torch.empty_like(q_raw)
@@ -314,11 +331,7 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_local = sum(ms) / 1e3
-    t_all = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    t_max = float(t_all.item())
+    t_max = max_over_ranks(torch, sum(ms) / 1e3, dist, "cuda")
     value = world * nq * args.steps / t_max
 
     # ---- end to end through the public API: pinned host raw queries in, results out
@@ -339,11 +352,8 @@ def main():
         e2e_ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_t = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3
-    e2e_all = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(e2e_all, op=dist.ReduceOp.MAX)
-    e2e_value = world * nq * args.steps / float(e2e_all.item())
+    e2e_t = max_over_ranks(torch, sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist, "cuda")
+    e2e_value = world * nq * args.steps / e2e_t
 
     if rank != 0:
         dist.destroy_process_group()

@@ -281,7 +281,7 @@ typedef struct hn_tune_result {
     int32_t reserved;
     int64_t sizes[HN_TUNE_MAX];
     float ms_stream[HN_TUNE_MAX];
-    float ms_dense[HN_TUNE_MAX];   /* -1 when the index has no BF16 prefix */
+    float ms_dense[HN_TUNE_MAX];   /* -1 when the index has no tensor-core (BF16 or FP8) prefix */
     float ms_units[4];             /* dense time at the largest size for 8, 16, 32, 64 units per SM */
 } hn_tune_result;
 

@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
+    ap.add_argument("--hard", action="store_true",
+                    help="stress variant of the workload: entry noise 0.3, query noise 0.2 (many survivors)")
     ap.add_argument("--beta-sweep", action="store_true",
                     help="soft ANN mode: queries/s, survivors and recall@1 for beta = alpha .. 0 (c2 data)")
     return ap.parse_args()
@@ -209,11 +211,24 @@ def default_prefix(workload: str) -> str:
     return "bf16" if workload == "c2" else "f32"
 
 
+HARD_NOISE = (0.3, 0.2)  # entry and query noise of the stress variant
+
+
+def load_workload(workload: str, hard: bool):
+    wl, c = hn_synth.config_workload(workload)
+    if hard:
+        c = dict(c, entry_noise=HARD_NOISE[0], query_noise=HARD_NOISE[1])
+        wl = hn_synth.make_workload(c["n"], c["nq"], c["n_centres"], c["seed"], *HARD_NOISE)
+    return wl, c
+
+
 def workload_config(workload: str, c: dict, prefix_name: str, world: int) -> dict:
     """The `config` of a bench line; the reference arm prints the same one."""
     k, alpha, nq = c["k"], c["alpha"], c["nq"]
+    hard = (f", hard variant (entry noise {c['entry_noise']}, query noise {c['query_noise']})"
+            if "entry_noise" in c else "")
     return {"workload": f"{workload}: N={c['n']} entries, Q={nq} queries per step, D=128, K={k}, "
-                        f"alpha={alpha}, {c['n_centres']} centres, {prefix_name} prefix",
+                        f"alpha={alpha}, {c['n_centres']} centres, {prefix_name} prefix{hard}",
             "n": c["n"], "queries_per_step": nq, "k": k, "alpha": alpha, "prefix": prefix_name,
             "parallelism": f"replicated index, {world} GPU(s), independent query batches",
             "l2": "flushed before every timed step (256 MiB write); index 2 GiB > L2"}
@@ -223,7 +238,7 @@ def run_reference(args, rank: int):
     if rank != 0:
         return 0
     workload = args.workload if args.workload in ("c0", "c1", "c2") else "c2"
-    wl, c = hn_synth.config_workload(workload)
+    wl, c = load_workload(workload, args.hard)
     per_step, total_q = [], 0
     import oracle
     db = oracle.normalize(wl.db_raw, c["k"], c["alpha"])
@@ -282,7 +297,7 @@ def main():
     if args.workload == "c3":
         return run_proposal(args, hn, torch, world, rank, dist, barrier)
 
-    wl, c = hn_synth.config_workload(args.workload)
+    wl, c = load_workload(args.workload, args.hard)
     k, alpha = c["k"], c["alpha"]
     prefix_name = args.prefix or default_prefix(args.workload)
     prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8}[prefix_name]
@@ -385,10 +400,17 @@ def main():
     roof["kernel"] = "prefix scan (Phase 1 and Phase 2 launches)"
     roof["algorithmic"] = f"2*Q*N*K = {flops:.3e} flop per launch (Q={nq}, N={c['n']}, K={k_alg})"
     roof["avg_launch_ms"] = scan_ms_avg
+    if st["scan"] == hn.SCAN_DENSE:
+        # the epilogue's own floor: one FP32 max per score (Phase 2) on 148 SMs x 128 lanes at the
+        # maximum clock; Phase 1 reduces packed FP16 pairs, half an instruction per score
+        smax = (clocks.summary().get("sm_max_mhz") or 2032.0) * 1e6
+        roof["epilogue_alu_floor_ms"] = {"phase1": 1e3 * 0.5 * nq * c["n"] / (148 * 128 * smax),
+                                         "phase2": 1e3 * 1.0 * nq * c["n"] / (148 * 128 * smax)}
 
     line = {
         "metric": "exact 1-NN queries/s", "value": value, "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "ms_per_step_median": statistics.median(ms), "ms_per_step_best": min(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prefix_name,
         "data": "synthetic",
         "config": workload_config(args.workload, c, prefix_name, world),

@@ -368,6 +368,17 @@ hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64
 hn_status hn_bruteforce_static(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx,
                                double *out_sim, void *stream);
 
+/*
+ * Self-test of failure detection (the paper has no counterpart).  Launches one
+ * warp that waits on a device barrier nothing arrives on, through the same bounded
+ * wait every mbarrier wait of the dense scan uses.  The wait gives up after
+ * limit_ns nanoseconds of GPU global time (1e3 <= limit_ns <= 1e10, else
+ * HN_ERR_INVALID_ARG), the kernel returns normally, and the call reports
+ * HN_ERR_TIMEOUT -- the expected outcome.  HN_OK would mean the wait did not fire.
+ * The CUDA context stays usable.  Synchronises `stream`.
+ */
+hn_status hn_selftest_wait_timeout(uint64_t limit_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

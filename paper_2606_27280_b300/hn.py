@@ -117,6 +117,7 @@ SIGNATURES = {
     "hn_proposal_destroy": ([_vp], _i32),
     "hn_mlp_loss_grad": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
     "hn_bruteforce_static": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hn_selftest_wait_timeout": ([ctypes.c_uint64, _vp], _i32),
 }
 STATIC_MAX_QUERIES = 65536
 
@@ -386,3 +387,9 @@ def search_multi(batches, use_graph: bool = True, stream=None) -> dict:
     _check(_lib.hn_search_multi(arr, len(batches), ctypes.byref(opts), ctypes.byref(st), _stream(stream)),
            "hn_search_multi")
     return {name: getattr(st, name) for name, _ in st._fields_ if name != "reserved"}
+
+
+def selftest_wait_timeout(limit_ns: int, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the hn_status (HN_ERR_TIMEOUT = 6 is the
+    expected outcome: the device-side wait gave up and the kernel returned)."""
+    return int(_lib.hn_selftest_wait_timeout(int(limit_ns), _stream(stream)))

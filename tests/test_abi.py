@@ -118,3 +118,9 @@ def test_python_wrappers_reject_cpu_tensors(hn):
     import torch
     with pytest.raises(TypeError):
         hn.normalize(torch.zeros(4, 128), 8, 0.1)
+
+
+def test_selftest_rejects_bad_limit_on_host(hn):
+    # argument checks happen before any device work
+    assert hn._lib.hn_selftest_wait_timeout(10, None) == hn.ERR_INVALID_ARG
+    assert hn._lib.hn_selftest_wait_timeout(20_000_000_000, None) == hn.ERR_INVALID_ARG

@@ -35,7 +35,9 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
               int cap, unsigned long long *__restrict__ cand) {
     constexpr int KC = KT < kKC ? KT : kKC;
     __shared__ float sq[KT][kSQ];
-    __shared__ float se[KC][kSE];
+    // staged entries: thread tid's entry sits at position sp so that the entries lane + 64 jj
+    // and lane + 64 jj + 32 are adjacent (one 8-byte load gives a packed pair)
+    __shared__ __align__(16) float se[KC][kSE];
     __shared__ float sb[FMT == FMT_FP8 ? kSE : 1];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kSQ;
@@ -54,12 +56,18 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
     }
     const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_cta;
     const int64_t t_end = min64(n_tiles, t_begin + tiles_per_cta);
+    const int sp = (tid >> 6) * 64 + (tid & 31) * 2 + ((tid >> 5) & 1);
     for (int64_t t = t_begin; t < t_end; ++t) {
-        float acc[8][8];
+        // acc2[i][jj] = scores of query 8w+i with entries lane + 64 jj (.x) and lane + 64 jj + 32 (.y):
+        // packed FMA (fma.rn.f32x2), each half the same FMA chain as a scalar fmaf.  Measured on
+        // B300, the packed form runs no more FMAs per second than the scalar one; it pays here
+        // because it halves the instructions issued per FMA (8-byte pair loads, one issue per two)
+        // (c1, FP32 prefix: Phase 1 15.3 -> 12.1 ms, Phase 2 16.3 -> 12.9 ms).
+        float2 acc2[8][4];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = make_float2(0.f, 0.f);
         const int64_t e = t * kSE + tid;  // entry staged by this thread
         const uint8_t *tile8 = FMT == FMT_FP8
                                    ? static_cast<const uint8_t *>(e16) + (e >> 7) * kF8TileBytes(KT) : nullptr;
@@ -78,8 +86,8 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
-                    se[2 * u][tid] = f.x * esc;
-                    se[2 * u + 1][tid] = f.y * esc;
+                    se[2 * u][sp] = f.x * esc;
+                    se[2 * u + 1][sp] = f.y * esc;
                 }
             } else if (FMT == FMT_BF16) {
 #pragma unroll
@@ -90,34 +98,45 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const float2 f = __bfloat1622float2(h[u]);
-                        se[c + 2 * u][tid] = f.x;
-                        se[c + 2 * u + 1][tid] = f.y;
+                        se[c + 2 * u][sp] = f.x;
+                        se[c + 2 * u + 1][sp] = f.y;
                     }
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < KC; c += 4) {
                     const float4 f = *reinterpret_cast<const float4 *>(e32 + e * KT + c0 + c);
-                    se[c][tid] = f.x;
-                    se[c + 1][tid] = f.y;
-                    se[c + 2][tid] = f.z;
-                    se[c + 3][tid] = f.w;
+                    se[c][sp] = f.x;
+                    se[c + 1][sp] = f.y;
+                    se[c + 2][sp] = f.z;
+                    se[c + 3][sp] = f.w;
                 }
             }
             __syncthreads();
 #pragma unroll
             for (int c = 0; c < KC; ++c) {
-                float a[8], b[8];
+                float2 a2[8], b2[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) a[i] = sq[c0 + c][w * 8 + i];
+                for (int i = 0; i < 8; ++i) {
+                    const float a = sq[c0 + c][w * 8 + i];
+                    a2[i] = make_float2(a, a);
+                }
 #pragma unroll
-                for (int j = 0; j < 8; ++j) b[j] = se[c][lane + 32 * j];
+                for (int jj = 0; jj < 4; ++jj) b2[jj] = *reinterpret_cast<const float2 *>(&se[c][jj * 64 + lane * 2]);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                    for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = __ffma2_rn(a2[i], b2[jj], acc2[i][jj]);
             }
         }
+        float acc[8][8];  // acc[i][j]: entry lane + 32 j
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                acc[i][2 * jj] = acc2[i][jj].x;
+                acc[i][2 * jj + 1] = acc2[i][jj].y;
+            }
         const int64_t ebase = t * kSE + lane;
         const bool tail = (t + 1) * kSE > n;
         if (FMT == FMT_FP8 && PHASE == 2) {

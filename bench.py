@@ -590,6 +590,15 @@ def run_serving(args, hn, torch, world, rank, dist, barrier):
         batches.append((ix, torch.empty_like(qd), torch.empty(int(nq), dtype=torch.int64, device="cuda"),
                         torch.empty(int(nq), dtype=torch.float64, device="cuda")))
     total_q = int(sizes.sum())
+    # the autotuner picks, per index, the dense/stream crossover and the dense work granularity
+    # for the batch sizes it will see: a ladder up to its group's concatenated size
+    tuned = []
+    for g, (ix, di, k, a) in enumerate(indexes):
+        group_q = int(sizes[pick == g].sum())
+        ladder = sorted({min(s_, ix.n) for s_ in (128, 512, 2048, max(group_q, 1))})
+        r = ix.autotune(ladder)
+        tuned.append({"n": ix.n, "k": k, "alpha": a, "group_queries": group_q, "dense_min_q": r["dense_min_q"],
+                      "units_per_cta": r["units_per_cta"]})
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     # queries reach a serving system already HN-normalised (HN is the descriptor
     # network's last layer): normalise once, then time the multi-batch search
@@ -617,7 +626,7 @@ def run_serving(args, hn, torch, world, rank, dist, barrier):
                            "queries_per_step": total_q, "n_indexes": len(indexes)},
                 "graph_replayed": st["graph_replayed"], "groups": st["n_groups"],
                 "batch_latency_ms": {"p50": st["batch_ms_p50"], "p99": st["batch_ms_p99"], "max": st["batch_ms_max"]},
-                "search_multi_ms": st["ms_total"], "survivors": st["survivors"],
+                "search_multi_ms": st["ms_total"], "survivors": st["survivors"], "autotune": tuned,
                 "note": "step = one hn_search_multi over all 256 batches (queries HN-normalised beforehand); "
                         "batch latency is measured from the start of the multi-search graph",
                 "clocks": clocks.summary(), "index_build_s": build_s}

@@ -11,8 +11,8 @@ namespace hn {
 
 // ------------------------------------------------------------------ stream scan
 // CTA = 64 queries x a contiguous range of 256-entry tiles.  Thread (w, lane)
-// owns queries 8w..8w+7 and tile entries lane + 32j (j < 8), so every thread
-// holds an 8x8 block of prefix scores in registers.  Each score is the FMA
+// owns queries 8w..8w+7 and the tile entries 64 jj + 2 lane + {0, 1} (jj < 4),
+// so every thread holds an 8x8 block of prefix scores in registers.  Each score is the FMA
 // chain acc = fma(q_c, x_c, acc), c = 0..KT-1 from acc = 0 (zero padding adds
 // exact zeros), whose error is bounded by gamma_KT * sum |q_c x_c|.
 //   PHASE 1: per-query best (score, lowest index) -> atomicMax on key1[q].
@@ -35,10 +35,10 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
               int cap, unsigned long long *__restrict__ cand) {
     constexpr int KC = KT < kKC ? KT : kKC;
     __shared__ float sq[KT][kSQ];
-    // staged entries: thread tid's entry sits at position sp so that the entries lane + 64 jj
-    // and lane + 64 jj + 32 are adjacent (one 8-byte load gives a packed pair)
+    // staged entries of the tile, in entry order: thread tid stages entry tid (conflict-free
+    // stores), and lane reads its pairs 64 jj + 2 lane + {0, 1} with one 8-byte load each
     __shared__ __align__(16) float se[KC][kSE];
-    __shared__ float sb[FMT == FMT_FP8 ? kSE : 1];
+    __shared__ __align__(16) float sb[FMT == FMT_FP8 ? kSE : 2];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kSQ;
     for (int i = tid; i < kSQ * KT; i += 256) {
@@ -56,9 +56,9 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
     }
     const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_cta;
     const int64_t t_end = min64(n_tiles, t_begin + tiles_per_cta);
-    const int sp = (tid >> 6) * 64 + (tid & 31) * 2 + ((tid >> 5) & 1);
+    const int sp = tid;
     for (int64_t t = t_begin; t < t_end; ++t) {
-        // acc2[i][jj] = scores of query 8w+i with entries lane + 64 jj (.x) and lane + 64 jj + 32 (.y):
+        // acc2[i][jj] = scores of query 8w+i with entries 64 jj + 2 lane (.x) and 64 jj + 2 lane + 1 (.y):
         // packed FMA (fma.rn.f32x2), each half the same FMA chain as a scalar fmaf.  Measured on
         // B300, the packed form runs no more FMAs per second than the scalar one; it pays here
         // because it halves the instructions issued per FMA (8-byte pair loads, one issue per two)
@@ -129,7 +129,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                     for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = __ffma2_rn(a2[i], b2[jj], acc2[i][jj]);
             }
         }
-        float acc[8][8];  // acc[i][j]: entry lane + 32 j
+        float acc[8][8];  // acc[i][j]: entry 64 (j / 2) + 2 lane + j % 2, increasing in j
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -137,12 +137,16 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                 acc[i][2 * jj] = acc2[i][jj].x;
                 acc[i][2 * jj + 1] = acc2[i][jj].y;
             }
-        const int64_t ebase = t * kSE + lane;
+        const int64_t ebase = t * kSE + 2 * lane;
         const bool tail = (t + 1) * kSE > n;
         if (FMT == FMT_FP8 && PHASE == 2) {
             float b[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) b[j] = sb[lane + 32 * j];
+            for (int jj = 0; jj < 4; ++jj) {
+                const float2 bb = *reinterpret_cast<const float2 *>(&sb[64 * jj + 2 * lane]);
+                b[2 * jj] = bb.x;
+                b[2 * jj + 1] = bb.y;
+            }
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -157,7 +161,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                 if (m > best[i] || tail) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const int64_t ei = ebase + 32 * j;
+                        const int64_t ei = ebase + 64 * (j >> 1) + (j & 1);
                         if (ei < n && acc[i][j] > best[i]) { best[i] = acc[i][j]; bidx[i] = (uint32_t)ei; }
                     }
                 }
@@ -166,7 +170,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                     const int64_t qg = q0 + w * 8 + i;
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const int64_t ei = ebase + 32 * j;
+                        const int64_t ei = ebase + 64 * (j >> 1) + (j & 1);
                         if (ei < n && acc[i][j] >= thr[i]) {
                             const int slot = atomicAdd(count + qg, 1);
                             if (slot < cap) bucket[qg * cap + slot] = (int32_t)ei;

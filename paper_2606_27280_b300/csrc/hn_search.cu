@@ -34,11 +34,17 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
               unsigned long long *__restrict__ key1, int32_t *__restrict__ bucket, int32_t *__restrict__ count,
               int cap, unsigned long long *__restrict__ cand) {
     constexpr int KC = KT < kKC ? KT : kKC;
+    // staging buffers: two for KT <= 32 (one barrier per staged slice; a buffer is refilled only
+    // after the barrier that follows the next slice's staging, which every thread reaches after
+    // its last read of it), one for the wider prefixes (48 KB static shared-memory limit)
+    constexpr int NB = KT <= 32 ? 2 : 1;
     __shared__ float sq[KT][kSQ];
     // staged entries of the tile, in entry order: thread tid stages entry tid (conflict-free
     // stores), and lane reads its pairs 64 jj + 2 lane + {0, 1} with one 8-byte load each
-    __shared__ __align__(16) float se[KC][kSE];
-    __shared__ __align__(16) float sb[FMT == FMT_FP8 ? kSE : 2];
+    __shared__ __align__(16) float se[NB][KC][kSE];
+    // FP8 Phase 2: error terms of the tile, by tile parity (written after a barrier that follows
+    // every thread's last read of the same parity two tiles back)
+    __shared__ __align__(16) float sb[FMT == FMT_FP8 ? 2 : 1][FMT == FMT_FP8 ? kSE : 2];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kSQ;
     for (int i = tid; i < kSQ * KT; i += 256) {
@@ -57,6 +63,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
     const int64_t t_begin = (int64_t)blockIdx.y * tiles_per_cta;
     const int64_t t_end = min64(n_tiles, t_begin + tiles_per_cta);
     const int sp = tid;
+    int buf = 0;
     for (int64_t t = t_begin; t < t_end; ++t) {
         // acc2[i][jj] = scores of query 8w+i with entries 64 jj + 2 lane (.x) and 64 jj + 2 lane + 1 (.y):
         // packed FMA (fma.rn.f32x2), each half the same FMA chain as a scalar fmaf.  Measured on
@@ -71,23 +78,25 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
         const int64_t e = t * kSE + tid;  // entry staged by this thread
         const uint8_t *tile8 = FMT == FMT_FP8
                                    ? static_cast<const uint8_t *>(e16) + (e >> 7) * kF8TileBytes(KT) : nullptr;
-        float esc = 1.f;
+        float esc = 1.f, bterm = 0.f;
         if (FMT == FMT_FP8) {
             const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(KT));
             esc = sc2[e & 127] * kF8QScale;  // exact: powers of two
-            if (PHASE == 2) sb[tid] = sc2[kF8Tile + (e & 127)];
+            if (PHASE == 2) bterm = sc2[kF8Tile + (e & 127)];
         }
 #pragma unroll 1
         for (int c0 = 0; c0 < KT; c0 += KC) {
-            __syncthreads();
+            if (NB == 1) __syncthreads();  // every thread has finished reading the single buffer
+            if (FMT == FMT_FP8 && PHASE == 2 && c0 == 0) sb[t & 1][tid] = bterm;
+            float (*const sx)[kSE] = se[buf];
             if (FMT == FMT_FP8) {
                 const uint4 raw = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, c0, KT));
                 const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
-                    se[2 * u][sp] = f.x * esc;
-                    se[2 * u + 1][sp] = f.y * esc;
+                    sx[2 * u][sp] = f.x * esc;
+                    sx[2 * u + 1][sp] = f.y * esc;
                 }
             } else if (FMT == FMT_BF16) {
 #pragma unroll
@@ -98,18 +107,18 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const float2 f = __bfloat1622float2(h[u]);
-                        se[c + 2 * u][sp] = f.x;
-                        se[c + 2 * u + 1][sp] = f.y;
+                        sx[c + 2 * u][sp] = f.x;
+                        sx[c + 2 * u + 1][sp] = f.y;
                     }
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < KC; c += 4) {
                     const float4 f = *reinterpret_cast<const float4 *>(e32 + e * KT + c0 + c);
-                    se[c][sp] = f.x;
-                    se[c + 1][sp] = f.y;
-                    se[c + 2][sp] = f.z;
-                    se[c + 3][sp] = f.w;
+                    sx[c][sp] = f.x;
+                    sx[c + 1][sp] = f.y;
+                    sx[c + 2][sp] = f.z;
+                    sx[c + 3][sp] = f.w;
                 }
             }
             __syncthreads();
@@ -122,12 +131,13 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                     a2[i] = make_float2(a, a);
                 }
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) b2[jj] = *reinterpret_cast<const float2 *>(&se[c][jj * 64 + lane * 2]);
+                for (int jj = 0; jj < 4; ++jj) b2[jj] = *reinterpret_cast<const float2 *>(&sx[c][jj * 64 + lane * 2]);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = __ffma2_rn(a2[i], b2[jj], acc2[i][jj]);
             }
+            if (NB == 2) buf ^= 1;
         }
         float acc[8][8];  // acc[i][j]: entry 64 (j / 2) + 2 lane + j % 2, increasing in j
 #pragma unroll
@@ -143,7 +153,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
             float b[8];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-                const float2 bb = *reinterpret_cast<const float2 *>(&sb[64 * jj + 2 * lane]);
+                const float2 bb = *reinterpret_cast<const float2 *>(&sb[t & 1][64 * jj + 2 * lane]);
                 b[2 * jj] = bb.x;
                 b[2 * jj + 1] = bb.y;
             }

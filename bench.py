@@ -1,12 +1,13 @@
 """Benchmark: exact HN 1-NN queries/s on one B300 (or N, one process each).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c0|c1|c2|c3|c4] [--prefix f32|bf16|fp8] [--scan auto|stream|dense]
+                    [--workload c0|c1|c2|c3|c4] [--prefix f32|bf16|fp8|i8] [--scan auto|stream|dense]
 
 Workload (default c2): N = 4,000,000 database entries, a batch of 65,536
 queries, D = 128, K = 16, alpha = 1/8, clustered synthetic descriptors
 (800,000 centres, entry noise 0.15, query noise 0.10), BF16 major prefix
-(--prefix fp8: the FP8-e4m3 form of the same workload).  c0 and c1 are the
+(--prefix fp8: the FP8-e4m3 form of the same workload; --prefix i8: the int8
+fixed-point form, scanned with dp4a on the CUDA cores).  c0 and c1 are the
 smaller configurations (FP32 prefix by default); c3 compares the search
 seeded by the learned block proposal with the plain search on c2's data;
 c4 is uneven batched serving over 16 indexes.
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS) + ["c4"])
-    ap.add_argument("--prefix", default=None, choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--prefix", default=None, choices=["f32", "bf16", "fp8", "i8"])
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
@@ -300,7 +301,7 @@ def main():
     wl, c = load_workload(args.workload, args.hard)
     k, alpha = c["k"], c["alpha"]
     prefix_name = args.prefix or default_prefix(args.workload)
-    prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8}[prefix_name]
+    prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8, "i8": hn.PREFIX_I8}[prefix_name]
     scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE}[args.scan]
     stream = torch.cuda.current_stream()
 
@@ -388,6 +389,14 @@ def main():
             peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio)"
         roof = {"bound": "tensor", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak,
                 "unit": "TFLOP/s", "peak_source": src}
+    elif prefix_name == "i8":
+        # CUDA-core dp4a (4 int8 products and their sum per instruction): a throughput probe
+        # measured 64 dp4a issued per clock per SM on B300 (half the FP32 FMA rate), so
+        # 148 SMs x 64 x 8 integer ops x max SM clock
+        smax = (clocks.summary().get("sm_max_mhz") or 2032.0)
+        peak = 148 * 64 * 8 * smax * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak, "unit": "TOP/s",
+                "peak_source": "derived: 148 SMs x 64 dp4a per clock (measured issue rate) x 8 int ops x max SM clock"}
     else:
         # CUDA-core FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
         smax = (clocks.summary().get("sm_max_mhz") or 2032.0)
@@ -398,7 +407,8 @@ def main():
     roof["traffic"] = measured_traffic(args.workload, prefix_name) if st["scan"] == hn.SCAN_DENSE else None
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     roof["kernel"] = "prefix scan (Phase 1 and Phase 2 launches)"
-    roof["algorithmic"] = f"2*Q*N*K = {flops:.3e} flop per launch (Q={nq}, N={c['n']}, K={k_alg})"
+    roof["algorithmic"] = (f"2*Q*N*K = {flops:.3e} {'int ops' if prefix_name == 'i8' else 'flop'} per launch "
+                           f"(Q={nq}, N={c['n']}, K={k_alg})")
     roof["avg_launch_ms"] = scan_ms_avg
     if st["scan"] == hn.SCAN_DENSE:
         # the epilogue's own floor: one FP32 max per score (Phase 2) on 148 SMs x 128 lanes at the
@@ -472,7 +482,7 @@ def run_beta_sweep(args, hn, torch, world, rank):
     wl, c = hn_synth.config_workload(args.workload)
     k, alpha = c["k"], c["alpha"]
     prefix_name = args.prefix or "bf16"
-    prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8}[prefix_name]
+    prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8, "i8": hn.PREFIX_I8}[prefix_name]
     stream = torch.cuda.current_stream()
     db = hn.normalize(torch.from_numpy(wl.db_raw).cuda(), k, alpha)
     ix = hn.Index(db, k, alpha, prefix=prefix)

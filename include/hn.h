@@ -52,10 +52,18 @@ typedef enum hn_status {
 typedef enum hn_prefix {
     HN_PREFIX_F32 = 0,  /* binary32 prefix, scanned with FP32 FMA */
     HN_PREFIX_BF16 = 1, /* bfloat16 prefix, scanned on the tensor cores (FP32 accumulation) */
-    HN_PREFIX_FP8_E4M3 = 2 /* FP8 e4m3 prefix with a per-entry binary32 scale (a power of two, so
+    HN_PREFIX_FP8_E4M3 = 2, /* FP8 e4m3 prefix with a per-entry binary32 scale (a power of two, so
                               that dequantisation is exact) and a per-entry rounding-error term;
                               scanned on the tensor cores (FP32 accumulation) or dequantised on the
                               CUDA cores.  K <= 64. */
+    HN_PREFIX_I8 = 3       /* 8-bit fixed-point prefix (§7, "Power-of-two alpha"; the remark after
+                              Theorem 2 on quantised descriptors): x^ = RN(x / s) in [-127, 127]
+                              with ONE power-of-two scale s for the whole index, and queries coded
+                              the same way with a power-of-two scale per query.  The CUDA-core
+                              scan forms the prefix dot product in integers (dp4a), so it is
+                              exact; the only error terms are the two quantisation residuals.
+                              Stream scan only (HN_SCAN_DENSE returns HN_ERR_UNSUPPORTED).
+                              K <= 64. */
 } hn_prefix;
 
 /* Which prefix-scan kernel runs (Phase 1 and Phase 2 of Algorithm 1). */

@@ -75,6 +75,7 @@ static void free_index(Index *ix) {
     cudaFree(ix->pre16);
     cudaFree(ix->pre16h);
     cudaFree(ix->pre8);
+    cudaFree(ix->prei8);
     cudaFree(ix->mx);
     cudaFree(ix->dev_max);
     cudaFree(ix->block_ids);
@@ -162,7 +163,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     if (!x || !aligned16(x)) return fail(HN_ERR_INVALID_ARG, "null or unaligned x");
     hn_index_opts o{};
     if (opts) o = *opts;
-    if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16 && o.prefix != HN_PREFIX_FP8_E4M3)
+    if (o.prefix != HN_PREFIX_F32 && o.prefix != HN_PREFIX_BF16 && o.prefix != HN_PREFIX_FP8_E4M3 &&
+        o.prefix != HN_PREFIX_I8)
         return fail(HN_ERR_INVALID_ARG, "bad prefix type");
     for (int i = 0; i < 4; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
@@ -200,6 +202,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         TRY(dalloc(&ix.pre32, (size_t)n_pad * ix.k_pad4));
     } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
         TRY(dalloc(&ix.pre8, (size_t)(n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16)));
+    } else if (ix.prefix == HN_PREFIX_I8) {
+        TRY(dalloc(&ix.prei8, (size_t)n_pad * ix.k_pad16));
     } else {
         TRY(dalloc(&ix.pre16, (size_t)n_pad * ix.k_pad16));
         TRY(dalloc(&ix.pre16h, (size_t)n_pad * ix.k_pad16));
@@ -220,7 +224,8 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
 #undef TRY
     ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
                (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) +
-               (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) + n * 4;
+               (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) +
+               (ix.prei8 ? n_pad * ix.k_pad16 : 0) + n * 4;
     if (hs[ST_NOT_NORMALIZED]) {
         const int row = hs[ST_BAD_ROW];
         hn_index_destroy(h);

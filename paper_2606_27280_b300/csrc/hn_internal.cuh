@@ -70,6 +70,8 @@ struct Workspace {
     __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles (FP8 index:
                                        //   the e4m3 hi/lo pairs of Phase 2, 2 * k_pad16 bytes a query)
     __half *qpre16h = nullptr;         // same in FP16 (dense Phase 1; FP8 index: e4m3 hi, lo = 0)
+                                       // (int8 index: qpre16 holds k_pad16 int8 codes a query and
+                                       //  qpre16h, read as float[q_cap], 1 / (t_q s), see hn_prep.cu)
     float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
     float *qnorm = nullptr;            // [q_cap] |q| rounded up
     int32_t *status = nullptr;         // [8] device status words
@@ -94,9 +96,11 @@ struct Index {
     __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
     __half *pre16h = nullptr;        // FP16 copy of the same prefix (dense Phase 1 candidate search)
     uint8_t *pre8 = nullptr;         // HN_PREFIX_FP8_E4M3: [n_tiles * 2] tiles of kF8TileBytes(k_pad16)
+    int8_t *prei8 = nullptr;         // HN_PREFIX_I8: [n_tiles * 256][k_pad16] int8 codes, row-major
     float qt = 0.f;                  // FP8: |q~_major| bound the per-entry error terms assume
     float *mx = nullptr;             // [n] |x_minor| rounded up
-    float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|
+    float *dev_max = nullptr;        // [8] maxima (rounded up): |x_minor|, |x_major|, residual, |prefix|, |x|,
+                                     //     max |x_major component| (int8 index: sets the code scale)
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
     uint64_t serial = 0;             // unique per built index (a freed index's address may be reused)
     int32_t dense_min_q = 1024;      // smallest batch the AUTO scan sends to the dense kernel (autotuned)

@@ -103,6 +103,34 @@ __device__ inline float f8_decode(uint8_t b) {
     return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3)));
 }
 
+// ------------------------------------------------------------------ int8 fixed point
+// Code scale of the int8 prefix: the smallest power of two s (>= 2^-100) with
+// amax / s <= 127, from frexp, so every code RN(v / s) lies in [-127, 127] and
+// the dequantised value s * code is exact.  amax = 0 -> 1.
+__device__ inline float i8_scale(float amax) {
+    if (!(amax > 0.f)) return 1.f;
+    int ex;
+    frexp((double)amax / 127.0, &ex);
+    return (float)ldexp(1.0, ex < -100 ? -100 : ex);
+}
+// the code of v at scale s (v / s is exact: s is a power of two)
+__device__ inline uint32_t i8_code(float v, float s) {
+    return (uint32_t)(uint8_t)(int8_t)__float2int_rn(v / s);
+}
+
+// max |x_d| over the prefix columns d < k of all n entries -> dev_max[5]: the
+// int8 index takes its one code scale from it (non-negative floats order like
+// their bit patterns, so atomicMax on the bits is a float max)
+__global__ void __launch_bounds__(256) k_prefix_amax(const float *__restrict__ x, int64_t n, int k,
+                                                     float *dev_max) {
+    float m = 0.f;
+    const int64_t total = n * kD;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        if ((int)(i % kD) < k) m = fmaxf(m, fabsf(x[i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(dev_max) + 5, __float_as_int(m));
+}
+
 // ------------------------------------------------------------------ index build
 // One warp per entry (grid-stride).  Lane l owns dimensions 4l..4l+3.  Writes
 // the FP32 master row, the prefix in the index precision, |x_minor| rounded up,
@@ -112,12 +140,13 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
                                               int prefix, int k_pad4, int k_pad16, int64_t n_pad,
                                               float *__restrict__ rows, float *__restrict__ pre32,
                                               __nv_bfloat16 *__restrict__ pre16, __half *__restrict__ pre16h,
-                                              uint8_t *__restrict__ pre8, float qt,
+                                              uint8_t *__restrict__ pre8, int8_t *__restrict__ prei8, float qt,
                                               float *__restrict__ mx, float *dev_max, int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float m_min = 0.f, m_maj = 0.f, m_res = 0.f, m_pre = 0.f, m_full = 0.f;
+    const float s8 = prefix == HN_PREFIX_I8 ? i8_scale(dev_max[5]) : 1.f;  // k_prefix_amax ran before
     for (int64_t e = warp; e < n_pad; e += nwarps) {
         const int c0 = lane * 4;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -149,6 +178,17 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             }
             p4 = make_float4(dq[0], dq[1], dq[2], dq[3]);
         }
+        uint32_t i8w = 0;  // this lane's 4 int8 codes
+        if (prefix == HN_PREFIX_I8) {
+            float dq[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t b = i8_code(pv[j], s8);
+                i8w |= b << (8 * j);
+                dq[j] = (float)(int8_t)b * s8;  // exact
+            }
+            p4 = make_float4(dq[0], dq[1], dq[2], dq[3]);
+        }
         const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
         double res2 = 0, pre2 = 0;
 #pragma unroll
@@ -171,6 +211,8 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             hk.y = *reinterpret_cast<uint32_t *>(&hhi);
             *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16h) + pre16_offset(e, c0, k_pad16)) = hk;
         }
+        if (prefix == HN_PREFIX_I8 && c0 < k_pad16)
+            *reinterpret_cast<uint32_t *>(prei8 + e * k_pad16 + c0) = i8w;
         uint8_t *tile8 = nullptr;
         if (prefix == HN_PREFIX_FP8_E4M3) {
             tile8 = pre8 + (e >> 7) * kF8TileBytes(k_pad16);
@@ -221,8 +263,14 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
     const int64_t n_pad = ix.n_tiles * kTileE;
     int64_t blocks = (n_pad * 32 + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
+    if (ix.prefix == HN_PREFIX_I8) {
+        k_prefix_amax<<<148 * 8, 256, 0, st>>>(x, ix.n, ix.k, ix.dev_max);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_pack<<<(unsigned)blocks, 256, 0, st>>>(x, ix.n, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16, n_pad,
-                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.pre8, ix.qt, ix.mx, ix.dev_max,
+                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.pre8, ix.prei8, ix.qt, ix.mx,
+                                             ix.dev_max,
                                              ix.ws.status);
     return cudaGetLastError();
 }
@@ -311,6 +359,26 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         lo2 = warp_sum(lo2);
         qt2 = warp_sum(qt2);
     }
+    // int8 index: codes q^ = RN(q / t_q) with the query's own power-of-two scale t_q, written as
+    // k_pad16 bytes a query into qpre16, and 1 / (t_q s) (a power of two) into qpre16h read as
+    // float: the stream scan turns tau_q into an integer threshold with it
+    if (prefix == HN_PREFIX_I8) {
+        const float tq = i8_scale(warp_max(fmaxf(fmaxf(fabsf(pv[0]), fabsf(pv[1])), fmaxf(fabsf(pv[2]), fabsf(pv[3])))));
+        uint32_t w8 = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const uint32_t b = i8_code(pv[t], tq);
+            w8 |= b << (8 * t);
+            const double qq = (double)(int8_t)b * tq;  // exact
+            const double r = (double)pv[t] - qq;
+            rq2 += r * r;
+            qt2 += qq * qq;
+        }
+        if (c0 < k_pad16) *reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(qpre16) + j * k_pad16 + c0) = w8;
+        if (lane == 0) reinterpret_cast<float *>(qpre16h)[j] = (float)(1.0 / ((double)tq * (double)i8_scale(dev_max[5])));
+        rq2 = warp_sum(rq2);
+        qt2 = warp_sum(qt2);
+    }
     if (prefix == HN_PREFIX_BF16 && c0 < k_pad16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(p4.x, p4.y), hi = __floats2bfloat162_rn(p4.z, p4.w);
         uint2 pk;
@@ -351,6 +419,12 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         const double excess = fmax(0.0, fmax(qtil, qmaj) - (double)qt) * xres;
         const double u_round = 0x1p-23 * (fmax(qa, qmaj) * xhat * (1.0 + 0x1p-10) + (double)qt * xres);
         scan = acc + rq * xmaj + excess + u_round;
+    } else if (prefix == HN_PREFIX_I8) {
+        // With q~ = t_q q^ and x~_i = s x^_i (both exact):
+        //   q.x_i = q~.x~_i + (q - q~).x_i + q~.(x_i - x~_i) <= q~.x~_i + r(q) max|x_major| + |q~| max r_i.
+        // The scan forms q~.x~_i = t_q s (q^ . x^_i) in integers and tests it against tau_q
+        // exactly (an integer threshold), so no rounding term enters.
+        scan = (double)sqrt_up(rq2) * xmaj + (double)sqrt_up(qt2) * xres;
     } else {
         const double g = (k_pad16 + 2) * 0x1p-20;
         scan = qmaj * xres + qres * xhat + g * qhat * xhat;

@@ -20,19 +20,34 @@ namespace hn {
 // FMT selects the stored prefix: 0 FP32, 1 BF16 (UMMA order), 2 FP8 e4m3 tiles,
 // dequantised exactly (x~ = s_i x^) while staging; in Phase 2 the FP8 score is
 // RN(acc + b_i) with the entry's error term b_i (see the FP8 slack in hn_prep.cu).
+// 3 int8 rows: D = q^ . x^ by dp4a, exact.  The accumulator starts at 0x4B400000,
+// the bits of 1.5 * 2^23, so while |D| < 2^22 its bits read as the float
+// 1.5 * 2^23 + D exactly: the float epilogue below then orders by D unchanged, and
+// Phase 2 compares against 1.5 * 2^23 + ceil(tau_q / (t_q s)), which keeps exactly
+// the entries with t_q s D >= tau_q.
 // The same kernel with KT = 128 over the full rows is the brute-force baseline.
 constexpr int kSQ = 64;     // queries per CTA
 constexpr int kSE = 256;    // entries per tile
 constexpr int kKC = 16;     // prefix columns staged per step
 
-enum { FMT_F32 = 0, FMT_BF16 = 1, FMT_FP8 = 2 };
+enum { FMT_F32 = 0, FMT_BF16 = 1, FMT_FP8 = 2, FMT_I8 = 3 };
+constexpr int kI8Bias = 0x4B400000;  // bits of 1.5 * 2^23
+
+// Phase-2 threshold of an int8 scan: D >= ceil(tau * inv) <=> t_q s D >= tau, with inv =
+// 1 / (t_q s) a power of two (the product is exact in binary64); clamped to |.| < 2^22,
+// beyond which every D (|D| <= 64 * 127^2) lies on one side anyway
+__device__ inline float i8_threshold(float tau, float inv) {
+    if (!(tau > -INFINITY)) return -INFINITY;
+    const double v = fmin(fmax(ceil((double)tau * (double)inv), -4194303.0), 4194303.0);
+    return (float)(12582912.0 + v);
+}
 
 template <int KT, int FMT, int PHASE>
 __global__ void __launch_bounds__(256, 2)
 k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64_t n, int64_t n_tiles,
               int64_t tiles_per_cta, const float *__restrict__ qpre, int64_t nq, const float *__restrict__ tau,
               unsigned long long *__restrict__ key1, int32_t *__restrict__ bucket, int32_t *__restrict__ count,
-              int cap, unsigned long long *__restrict__ cand) {
+              int cap, unsigned long long *__restrict__ cand, const float *__restrict__ qinv) {
     constexpr int KC = KT < kKC ? KT : kKC;
     // staging buffers: two for KT <= 32 (one barrier per staged slice; a buffer is refilled only
     // after the barrier that follows the next slice's staging, which every thread reaches after
@@ -47,16 +62,27 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
     __shared__ __align__(16) float sb[FMT == FMT_FP8 ? 2 : 1][FMT == FMT_FP8 ? kSE : 2];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kSQ;
-    for (int i = tid; i < kSQ * KT; i += 256) {
-        const int qq = i / KT, c = i % KT;
-        sq[c][qq] = (q0 + qq < nq) ? qpre[(q0 + qq) * KT + c] : 0.f;
+    if (FMT == FMT_I8) {
+        // int8 codes: KT / 4 words a query, word-column-major in sq's first rows
+        constexpr int KW = KT / 4;
+        const uint32_t *qw = reinterpret_cast<const uint32_t *>(qpre);
+        uint32_t(*sqw)[kSQ] = reinterpret_cast<uint32_t(*)[kSQ]>(&sq[0][0]);
+        for (int i = tid; i < kSQ * KW; i += 256) {
+            const int qq = i / KW, c = i % KW;
+            sqw[c][qq] = (q0 + qq < nq) ? qw[(q0 + qq) * KW + c] : 0u;
+        }
+    } else {
+        for (int i = tid; i < kSQ * KT; i += 256) {
+            const int qq = i / KT, c = i % KT;
+            sq[c][qq] = (q0 + qq < nq) ? qpre[(q0 + qq) * KT + c] : 0.f;
+        }
     }
     float thr[8], best[8];
     uint32_t bidx[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t qg = q0 + w * 8 + i;
-        thr[i] = (PHASE == 2 && qg < nq) ? tau[qg] : INFINITY;
+        thr[i] = (PHASE == 2 && qg < nq) ? (FMT == FMT_I8 ? i8_threshold(tau[qg], qinv[qg]) : tau[qg]) : INFINITY;
         best[i] = -INFINITY;
         bidx[i] = 0xFFFFFFFFu;
     }
@@ -71,10 +97,14 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
         // because it halves the instructions issued per FMA (8-byte pair loads, one issue per two)
         // (c1, FP32 prefix: Phase 1 15.3 -> 12.1 ms, Phase 2 16.3 -> 12.9 ms).
         float2 acc2[8][4];
+        int acci[8][8];  // int8 scan: kI8Bias + D, entry 64 (j / 2) + 2 lane + j % 2
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acci[i][j] = kI8Bias;
+        }
         const int64_t e = t * kSE + tid;  // entry staged by this thread
         const uint8_t *tile8 = FMT == FMT_FP8
                                    ? static_cast<const uint8_t *>(e16) + (e >> 7) * kF8TileBytes(KT) : nullptr;
@@ -89,7 +119,15 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
             if (NB == 1) __syncthreads();  // every thread has finished reading the single buffer
             if (FMT == FMT_FP8 && PHASE == 2 && c0 == 0) sb[t & 1][tid] = bterm;
             float (*const sx)[kSE] = se[buf];
-            if (FMT == FMT_FP8) {
+            uint32_t(*const sxw)[kSE] = reinterpret_cast<uint32_t(*)[kSE]>(&sx[0][0]);
+            if (FMT == FMT_I8) {
+                // 16 codes = 4 words of this thread's entry, one word-column each
+                const uint4 raw = *reinterpret_cast<const uint4 *>(static_cast<const int8_t *>(e16) + e * KT + c0);
+                sxw[0][sp] = raw.x;
+                sxw[1][sp] = raw.y;
+                sxw[2][sp] = raw.z;
+                sxw[3][sp] = raw.w;
+            } else if (FMT == FMT_FP8) {
                 const uint4 raw = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, c0, KT));
                 const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
 #pragma unroll
@@ -122,6 +160,25 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
                 }
             }
             __syncthreads();
+            if (FMT == FMT_I8) {
+                const uint32_t(*sqw)[kSQ] = reinterpret_cast<const uint32_t(*)[kSQ]>(&sq[0][0]);
+#pragma unroll
+                for (int cw = 0; cw < KC / 4; ++cw) {
+                    int qa[8];
+                    uint2 xb[4];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) qa[i] = (int)sqw[c0 / 4 + cw][w * 8 + i];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) xb[jj] = *reinterpret_cast<const uint2 *>(&sxw[cw][jj * 64 + lane * 2]);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            acci[i][2 * jj] = __dp4a(qa[i], (int)xb[jj].x, acci[i][2 * jj]);
+                            acci[i][2 * jj + 1] = __dp4a(qa[i], (int)xb[jj].y, acci[i][2 * jj + 1]);
+                        }
+                }
+            } else {
 #pragma unroll
             for (int c = 0; c < KC; ++c) {
                 float2 a2[8], b2[4];
@@ -137,6 +194,7 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = __ffma2_rn(a2[i], b2[jj], acc2[i][jj]);
             }
+            }
             if (NB == 2) buf ^= 1;
         }
         float acc[8][8];  // acc[i][j]: entry 64 (j / 2) + 2 lane + j % 2, increasing in j
@@ -144,8 +202,8 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
         for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-                acc[i][2 * jj] = acc2[i][jj].x;
-                acc[i][2 * jj + 1] = acc2[i][jj].y;
+                acc[i][2 * jj] = FMT == FMT_I8 ? __int_as_float(acci[i][2 * jj]) : acc2[i][jj].x;
+                acc[i][2 * jj + 1] = FMT == FMT_I8 ? __int_as_float(acci[i][2 * jj + 1]) : acc2[i][jj].y;
             }
         const int64_t ebase = t * kSE + 2 * lane;
         const bool tail = (t + 1) * kSE > n;
@@ -229,7 +287,7 @@ int64_t stream_cand_slots(const Index &ix, int64_t nq) {
 template <int KT, int FMT>
 static cudaError_t stream_scan_kt(const float *e32, const void *e16, int64_t n, int64_t n_tiles,
                                   const float *qpre, int64_t nq, int phase, const Workspace &ws, cudaStream_t st,
-                                  unsigned long long *cand = nullptr) {
+                                  unsigned long long *cand = nullptr, const float *qinv = nullptr) {
     const int64_t qt = (nq + kSQ - 1) / kSQ;
     int64_t splits = 0, tpc = 0;
     stream_split(n_tiles, nq, &splits, &tpc);
@@ -237,10 +295,10 @@ static cudaError_t stream_scan_kt(const float *e32, const void *e16, int64_t n, 
     dim3 grid((unsigned)qt, (unsigned)splits);
     if (phase == 1)
         k_stream_scan<KT, FMT, 1><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
-                                                         ws.bucket, ws.count, ws.bucket_cap, cand);
+                                                         ws.bucket, ws.count, ws.bucket_cap, cand, qinv);
     else
         k_stream_scan<KT, FMT, 2><<<grid, 256, 0, st>>>(e32, e16, n, n_tiles, tpc, qpre, nq, ws.tau, ws.key1,
-                                                         ws.bucket, ws.count, ws.bucket_cap, nullptr);
+                                                         ws.bucket, ws.count, ws.bucket_cap, nullptr, qinv);
     return cudaGetLastError();
 }
 
@@ -251,6 +309,15 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
             case 16: return stream_scan_kt<16, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
             case 32: return stream_scan_kt<32, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
             case 64: return stream_scan_kt<64, FMT_BF16>(nullptr, ix.pre16, ix.n, ix.n_tiles, ws.qpre32, nq, phase, ws, st, cand);
+        }
+    } else if (ix.prefix == HN_PREFIX_I8) {
+        // int8 query codes (qpre16, k_pad16 bytes a query) against the int8 rows
+        const float *qc = reinterpret_cast<const float *>(ws.qpre16);
+        const float *qi = reinterpret_cast<const float *>(ws.qpre16h);
+        switch (ix.k_pad16) {
+            case 16: return stream_scan_kt<16, FMT_I8>(nullptr, ix.prei8, ix.n, ix.n_tiles, qc, nq, phase, ws, st, cand, qi);
+            case 32: return stream_scan_kt<32, FMT_I8>(nullptr, ix.prei8, ix.n, ix.n_tiles, qc, nq, phase, ws, st, cand, qi);
+            case 64: return stream_scan_kt<64, FMT_I8>(nullptr, ix.prei8, ix.n, ix.n_tiles, qc, nq, phase, ws, st, cand, qi);
         }
     } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
         // exact FP32 query prefix (k_pad16 wide) against the dequantised FP8 prefix

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 
 OK, ERR_INVALID_ARG, ERR_NOT_NORMALIZED, ERR_ZERO_NORM, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, \
     ERR_UNSUPPORTED = range(9)
-PREFIX_F32, PREFIX_BF16, PREFIX_FP8 = 0, 1, 2
+PREFIX_F32, PREFIX_BF16, PREFIX_FP8, PREFIX_I8 = 0, 1, 2, 3
 SCAN_AUTO, SCAN_STREAM, SCAN_DENSE = 0, 1, 2
 D = 128
 

@@ -90,6 +90,12 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
     const int64_t t_end = min64(n_tiles, t_begin + tiles_per_cta);
     const int sp = tid;
     int buf = 0;
+    // int8: the codes of the next staged slice, loaded one slice ahead so that the load's
+    // latency overlaps the current slice's dp4a work (4 registers)
+    const int8_t *codes = static_cast<const int8_t *>(e16);
+    uint4 i8next = make_uint4(0u, 0u, 0u, 0u);
+    if (FMT == FMT_I8 && t_begin < t_end)
+        i8next = *reinterpret_cast<const uint4 *>(codes + (t_begin * kSE + tid) * KT);
     for (int64_t t = t_begin; t < t_end; ++t) {
         // acc2[i][jj] = scores of query 8w+i with entries 64 jj + 2 lane (.x) and 64 jj + 2 lane + 1 (.y):
         // packed FMA (fma.rn.f32x2), each half the same FMA chain as a scalar fmaf.  Measured on
@@ -122,7 +128,10 @@ k_stream_scan(const float *__restrict__ e32, const void *__restrict__ e16, int64
             uint32_t(*const sxw)[kSE] = reinterpret_cast<uint32_t(*)[kSE]>(&sx[0][0]);
             if (FMT == FMT_I8) {
                 // 16 codes = 4 words of this thread's entry, one word-column each
-                const uint4 raw = *reinterpret_cast<const uint4 *>(static_cast<const int8_t *>(e16) + e * KT + c0);
+                const uint4 raw = i8next;
+                const int64_t tn = c0 + KC < KT ? t : t + 1;  // the slice after this one
+                const int cn = c0 + KC < KT ? c0 + KC : 0;
+                if (tn < t_end) i8next = *reinterpret_cast<const uint4 *>(codes + (tn * kSE + tid) * KT + cn);
                 sxw[0][sp] = raw.x;
                 sxw[1][sp] = raw.y;
                 sxw[2][sp] = raw.z;

@@ -291,7 +291,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 const int nt = t1 - tt < C::kTPS ? t1 - tt : C::kTPS;
                 for (int j = 0; j < nt; ++j, ++g, e0 += kDE) {
                     const uint32_t buf = g & 1u;
-                    if (!(ok = mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag, kWaitLimitNs))) break;
+                    // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag,
+                                                           kWaitLimitNs));
+                    if (!ok) break;
                     tc_fence_after();
                     // this tile's MMAs are done with the stage; the last tile of a short stage
                     // also arrives for the tiles the stage did not hold

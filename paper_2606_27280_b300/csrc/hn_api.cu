@@ -43,6 +43,9 @@ static void free_ws(Workspace &ws) {
     cudaFree(ws.cand);
     ws.cand = nullptr;
     ws.cand_cap = 0;
+    cudaFree(ws.gbits);
+    ws.gbits = nullptr;
+    ws.gbits_cap = 0;
     cudaFree(ws.tau);
     cudaFree(ws.qpre32);
     cudaFree(ws.qpre16);
@@ -346,6 +349,17 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn) {
         }
         ws.cand_slots = (int32_t)slots;
     }
+    if (scan == HN_SCAN_DENSE) {
+        const int64_t need = dense_gbits_words(ix, nq);
+        if (need > ws.gbits_cap) {
+            cudaFree(ws.gbits);
+            ws.gbits = nullptr;
+            ws.gbits_cap = 0;
+            HN_CUDA(dalloc(&ws.gbits, need));
+            ws.gbits_cap = need;
+            ++ws.gen;
+        }
+    }
     return HN_OK;
 }
 
@@ -436,6 +450,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
         if (st != HN_OK) return st;
         kernels += o.seed ? 4 + 5 * (int32_t)((nq + 8191) / 8192) : 5;
+        if (scan == HN_SCAN_DENSE) kernels += (int32_t)dense_phase2_launches(ix, nq) - 1;  // scan + extraction per pass
         HN_CUDA(cudaStreamSynchronize(s));
         int32_t want = 0;
         st = check_search(ix, nq, &want);

@@ -32,7 +32,11 @@
 //   warps 3-18 epilogue (4 per SM sub-partition): TMEM -> registers (thread =
 //            query row, 64 accumulator columns per warp), one max tree, then
 //              Phase 1: running best score and its 64-entry segment per (query, chunk, segment);
-//              Phase 2: entries with s~ >= tau_q appended to q's survivor slots.
+//              Phase 2: one bit per 32-entry group whose maximum reaches tau_q, stored as
+//              a coalesced word per 16 tiles; k_dense_extract then scores the flagged
+//              groups and appends their survivors.  Extracting survivors in the epilogue
+//              itself put a rare but slow path on the accumulator hand-off, which every
+//              tile waits for (c2, BF16: 27.1 ms against 18.5 + 4.9 ms for the two steps).
 // A work unit is (query tile, contiguous chunk of entry tiles); units are
 // numbered chunk-major so that the CTAs running together read the same entry
 // tiles, which then come from L2.
@@ -40,6 +44,10 @@
 // shared abort flag, the others leave their loops, copies and MMAs in flight
 // are drained (again with a limit), TMEM is released and the status word
 // ST_TIMEOUT tells the host.
+#include <algorithm>
+
+#include <cuda_fp8.h>
+
 #include "hn_internal.cuh"
 #include "hn_sm100.cuh"
 
@@ -60,12 +68,10 @@ struct DenseParams {
     int64_t n_qt, tiles_per_chunk, n_units;
     const float *tau;
     unsigned long long *cand;     // [nq][2 * chunks] Phase-1 (best score, segment id) per (query, chunk, entry half)
-    int32_t *bucket, *count;
-    int32_t cap;
+    uint32_t *gbits;              // Phase 2: [chunk][half][word][n_qt * 256] passing-group bits, 16 tiles a word
+    int64_t words;                // words per (chunk, half): ceil(tiles_per_chunk / 16)
     int32_t *status;
 };
-
-constexpr int kLcap = 32;  // Phase-2 survivors staged per epilogue thread before a flush
 constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
 constexpr int kDE = 128;   // entries per B tile (MMA N)
 
@@ -80,11 +86,11 @@ struct DenseCfg {
     static constexpr int kTPS = kB >= 16384 ? 1 : 16384 / kB;       // entry tiles per stage
     static constexpr uint32_t kStageBytes = kTPS * kB;
     static constexpr uint32_t kA = kDQ * KP * 2;                    // bytes of one query unit (FP8: hi + lo)
-    static constexpr uint32_t kSurvBytes = PHASE == 2 ? kLcap * kEpiWarps * 32 * 4 : 0;  // [kLcap][512] ids
-    // ring: 160 KB (Phase 1) / 128 KB (Phase 2), capped by what the 227 KB of shared
-    // memory leaves after the two query units, the survivor staging and the barriers
+    static constexpr uint32_t kSurvBytes = 0;
+    // ring: 160 KB, capped by what the 227 KB of shared memory leaves after the two
+    // query units and the barriers
     static constexpr uint32_t kRoom = 225 * 1024 - 2 * kA - kSurvBytes;
-    static constexpr uint32_t kWant = PHASE == 1 ? 160 * 1024 : 128 * 1024;
+    static constexpr uint32_t kWant = 160 * 1024;
     static constexpr uint32_t kRing = kWant < kRoom ? kWant : kRoom;
     static constexpr int kStages = kRing / kStageBytes < 2 ? 2 : kRing / kStageBytes;
     static constexpr uint32_t kSurvOff = kStages * kStageBytes + 2 * kA;
@@ -259,10 +265,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
         const int sub = seg >> 1;                // query A tile of those columns
         const int half = seg & 1;                // entry half of the B tile: entries 64*half ..
         const int row = sub * kTileQ + quarter * 32 + lane;
-        const int et = ew * 32 + lane;           // epilogue thread 0..511
         const bool releaser = ew == 0 && lane == 0;  // hands B stages back to the producer
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        uint32_t *sbuf = reinterpret_cast<uint32_t *>(smem + C::kSurvOff);  // [kLcap][512]
         uint32_t stage = 0, sphase = 0;
         uint32_t g = 0;  // tile counter of this CTA: buffer g & 1, its use number g >> 1
         bool ok = true;
@@ -276,14 +280,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
             float best = -INFINITY;
             int32_t bseg = -1;
-            int lc = 0;
-            // Phase 2: move this thread's staged survivors to its query's slots
-            auto flush = [&]() {
-                const int slot = atomicAdd(p.count + q, lc);
-                for (int j = 0; j < lc; ++j)
-                    if (slot + j < p.cap) p.bucket[q * p.cap + slot + j] = (int32_t)sbuf[j * 512 + et];
-                lc = 0;
-            };
+            uint32_t gword = 0;  // Phase 2: passing-group bits of the current 16 tiles
+            uint32_t *gb = PHASE == 2 ? p.gbits + (ch * 2 + half) * p.words * (p.n_qt * kDQ) + q : nullptr;
             const int32_t n32 = (int32_t)p.n;
             const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
             int32_t e0 = t0 * kDE + half * 64;    // first entry of this warp's 64 columns
@@ -356,28 +354,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                             __syncwarp();
                             if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
                         }
-                        float gm[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) gm[k] = max16(v + 16 * k);
-                        const float m = fmaxf(fmaxf(gm[0], gm[1]), fmaxf(gm[2], gm[3]));
-                        if (m >= thr) {
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (gm[k] >= thr) {
-                                    uint32_t mask = 0;
-#pragma unroll
-                                    for (int i = 0; i < 16; ++i) mask |= (v[16 * k + i] >= thr ? 1u : 0u) << i;
-                                    const int32_t ek = e0 + 16 * k;
-                                    if (ek + 16 > n32) mask &= ek >= n32 ? 0u : ((1u << (uint32_t)(n32 - ek)) - 1u);
-                                    if (lc + __popc(mask) > kLcap) flush();
-                                    while (mask) {
-                                        const int i = __ffs(mask) - 1;
-                                        mask &= mask - 1;
-                                        sbuf[lc * 512 + et] = (uint32_t)(ek + i);
-                                        ++lc;
-                                    }
-                                }
-                            }
+                        // bit 2 (tile mod 16) + k: the maximum of the 32 scores 32k .. 32k + 31 reaches
+                        // tau_q.  The bits go out as one coalesced word per 16 tiles; k_dense_extract
+                        // finds the survivors of those groups.  Nothing here waits on memory: the
+                        // accumulator hand-off has no slack for a rare, slow path in any warp.
+                        const int32_t ti = t - t0;
+                        const float g0 = fmaxf(max16(v), max16(v + 16)), g1 = fmaxf(max16(v + 32), max16(v + 48));
+                        gword |= ((g0 >= thr ? 1u : 0u) | (g1 >= thr ? 2u : 0u)) << (2 * (ti & 15));
+                        if ((ti & 15) == 15 || t == t1 - 1) {
+                            gb[(int64_t)(ti >> 4) * (p.n_qt * kDQ)] = gword;
+                            gword = 0;
                         }
                     }
                 }
@@ -388,7 +374,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             if (PHASE == 1 && qvalid)
                 p.cand[q * (2 * (p.n_units / p.n_qt)) + 2 * ch + half] =
                     bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
-            if (PHASE == 2 && lc > 0) flush();
         }
     }
 
@@ -397,6 +382,114 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------------ Phase-2 survivors
+// Second step of the dense Phase 2.  Every 32-entry group whose maximum reached tau_q in
+// the tensor-core scan (one bit of gbits) is scored again on the CUDA cores with the
+// stream scan's arithmetic: an FP32 FMA chain over the stored prefix in column order
+// (BF16 index: the BF16 values against the BF16-rounded query; FP8 index: s_i x^ against
+// the exact query, then + b_i).  The query slack E_q bounds that arithmetic as well as
+// the tensor cores', so keeping the entries with score >= tau_q keeps every possible
+// answer.  A block takes 256 queries and one entry chunk (many warps in flight hide the
+// gathers); a warp scores one group at a time, one entry a lane, and takes the group's
+// survivor slots with one atomicAdd on the query's count.
+struct ExtractParams {
+    const void *pre;          // BF16 prefix (UMMA order) or FP8 tiles
+    const float *qpre32;      // [nq][kp] query prefix in the scan precision
+    const uint32_t *gbits;    // as written by k_dense_scan
+    int64_t n, n_tiles, nq, q_pad, tiles_per_chunk, chunks, words;
+    const float *tau;
+    int32_t *bucket, *count;  // count: slots already used (soft mode: the kept best); may pass cap
+    int32_t cap;
+};
+
+template <int KP, bool F8>
+__device__ __forceinline__ float group_entry_score(const ExtractParams &x, int64_t e, const float *qp) {
+    float s = 0.f;
+    if (F8) {
+        const uint8_t *tile8 = static_cast<const uint8_t *>(x.pre) + (e >> 7) * kF8TileBytes(KP);
+        const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(KP));
+        const float esc = sc2[e & 127] * kF8QScale;  // s_i: exact
+#pragma unroll
+        for (int c0 = 0; c0 < KP; c0 += 16) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, c0, KP));
+            const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
+                s = fmaf(qp[c0 + 2 * u], f.x * esc, s);
+                s = fmaf(qp[c0 + 2 * u + 1], f.y * esc, s);
+            }
+        }
+        s += sc2[kF8Tile + (e & 127)];  // b_i
+    } else {
+#pragma unroll
+        for (int c = 0; c < KP; c += 8) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(static_cast<const char *>(x.pre) + pre16_offset(e, c, KP));
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float2 f = __bfloat1622float2(h[u]);
+                s = fmaf(qp[c + 2 * u], f.x, s);
+                s = fmaf(qp[c + 2 * u + 1], f.y, s);
+            }
+        }
+    }
+    return s;
+}
+
+template <int KP, bool F8>
+__global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // this thread's query
+    const bool qv = q < x.nq;
+    const float tau = qv ? x.tau[q] : INFINITY;
+    {
+        const int64_t c = blockIdx.y;  // this block's entry chunk
+        const int64_t t0 = c * x.tiles_per_chunk;
+        const int64_t nt = min64(x.n_tiles - t0, x.tiles_per_chunk);
+        const int64_t nw = (nt + 15) / 16;
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t *gw = x.gbits + (c * 2 + h) * x.words * x.q_pad;
+            for (int64_t w0 = 0; w0 < nw; w0 += 8) {
+                // 8 independent coalesced loads in flight; most words are zero
+                uint32_t wv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nw) ? gw[(w0 + i) * x.q_pad + q] : 0u;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                const uint32_t word = wv[i];
+                const int64_t w = w0 + i;
+                unsigned pend = __ballot_sync(0xffffffffu, word != 0u);
+                while (pend) {
+                    const int o = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    uint32_t wo = __shfl_sync(0xffffffffu, word, o);
+                    const float to = __shfl_sync(0xffffffffu, tau, o);
+                    const int64_t qo = q - lane + o;
+                    const float *qp = x.qpre32 + qo * KP;
+                    while (wo) {
+                        const int b = __ffs(wo) - 1;
+                        wo &= wo - 1;
+                        const int64_t e = (t0 + w * 16 + (b >> 1)) * kDE + h * 64 + (b & 1) * 32 + lane;
+                        const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
+                        const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                        if (hb) {
+                            int base = 0;
+                            if (lane == o) base = atomicAdd(x.count + qo, __popc(hb));
+                            base = __shfl_sync(0xffffffffu, base, o);
+                            if (hit) {
+                                const int slot = base + __popc(hb & ((1u << lane) - 1u));
+                                if (slot < x.cap) x.bucket[qo * x.cap + slot] = (int32_t)e;
+                            }
+                        }
+                    }
+                }
+                }
+            }
+        }
     }
 }
 
@@ -477,6 +570,48 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
     return cudaGetLastError();
 }
 
+// Passes of the dense Phase 2 over query tiles so that the group bitmap of a pass fits
+// `cap` words (0 if even one query tile does not fit).
+static int64_t phase2_tiles_per_pass(int64_t n_tiles, int64_t n_qt, int G, int upc, int64_t cap);
+
+// Words of the Phase-2 group bitmap for a pass over n_qt query tiles.
+static int64_t gbits_words(int64_t n_tiles, int64_t n_qt, int G, int upc) {
+    int64_t tpc = 0, chunks = 0;
+    dense_chunking(n_tiles, n_qt, G, upc, &tpc, &chunks);
+    return chunks * 2 * ((tpc + 15) / 16) * n_qt * kDQ;
+}
+
+// Bitmap words the workspace holds for nq queries: the whole batch up to kGbitsMaxWords
+// (4 GiB; larger batches run Phase 2 in passes over query tiles), but at least one tile's.
+int64_t dense_gbits_words(const Index &ix, int64_t nq) {
+    constexpr int64_t kGbitsMaxWords = (int64_t)1 << 30;
+    const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
+    const int64_t all = gbits_words(n_tiles, (nq + kDQ - 1) / kDQ, num_sms(), ix.units_per_cta);
+    const int64_t one = gbits_words(n_tiles, 1, num_sms(), ix.units_per_cta);
+    return std::max(std::min(all, kGbitsMaxWords), one);
+}
+
+static int64_t phase2_tiles_per_pass(int64_t n_tiles, int64_t n_qt, int G, int upc, int64_t cap) {
+    int64_t per = n_qt;
+    while (per > 1 && gbits_words(n_tiles, per, G, upc) > cap) per = (per + 1) / 2;
+    return gbits_words(n_tiles, per, G, upc) > cap ? 0 : per;
+}
+
+// Kernel launches of one dense Phase 2 (a scan and an extraction per pass).
+int64_t dense_phase2_launches(const Index &ix, int64_t nq) {
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
+    const int64_t per =
+        phase2_tiles_per_pass(ix.n_tiles * (kTileE / kDE), n_qt, num_sms(), ix.units_per_cta, ix.ws.gbits_cap);
+    return per > 0 ? 2 * ((n_qt + per - 1) / per) : 0;
+}
+
+template <int KP, bool F8>
+static cudaError_t launch_extract(const ExtractParams &x, cudaStream_t st) {
+    if (x.chunks > 65535) return cudaErrorInvalidConfiguration;
+    k_dense_extract<KP, F8><<<dim3((unsigned)(x.q_pad / 256), (unsigned)x.chunks), 256, 0, st>>>(x);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
     if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
     const Workspace &ws = ix.ws;
@@ -488,25 +623,73 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
     p.n = ix.n;
     p.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
-    p.nq = nq;
-    p.n_qt = (nq + kDQ - 1) / kDQ;
-    const int G = num_sms();
-    int64_t chunks = 0;
-    dense_chunking(p.n_tiles, p.n_qt, G, ix.units_per_cta, &p.tiles_per_chunk, &chunks);
-    p.n_units = p.n_qt * chunks;
-    p.tau = ws.tau;
-    p.cand = ws.cand;
-    p.bucket = ws.bucket;
-    p.count = ws.count;
-    p.cap = ws.bucket_cap;
     p.status = ws.status;
-    const int grid = (int)min64(G, p.n_units);
-    switch (ix.k_pad16) {
-        case 16: return f8 ? launch_kp<16, true>(p, phase, grid, st) : launch_kp<16, false>(p, phase, grid, st);
-        case 32: return f8 ? launch_kp<32, true>(p, phase, grid, st) : launch_kp<32, false>(p, phase, grid, st);
-        case 64: return f8 ? launch_kp<64, true>(p, phase, grid, st) : launch_kp<64, false>(p, phase, grid, st);
+    const int G = num_sms();
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
+    const int kp = ix.k_pad16;
+    if (phase == 1) {
+        int64_t chunks = 0;
+        p.nq = nq;
+        p.n_qt = n_qt;
+        dense_chunking(p.n_tiles, p.n_qt, G, ix.units_per_cta, &p.tiles_per_chunk, &chunks);
+        p.n_units = p.n_qt * chunks;
+        p.tau = ws.tau;
+        p.cand = ws.cand;
+        const int grid = (int)min64(G, p.n_units);
+        switch (kp) {
+            case 16: return f8 ? launch_kp<16, true>(p, 1, grid, st) : launch_kp<16, false>(p, 1, grid, st);
+            case 32: return f8 ? launch_kp<32, true>(p, 1, grid, st) : launch_kp<32, false>(p, 1, grid, st);
+            case 64: return f8 ? launch_kp<64, true>(p, 1, grid, st) : launch_kp<64, false>(p, 1, grid, st);
+        }
+        return cudaErrorNotSupported;
     }
-    return cudaErrorNotSupported;
+    // Phase 2: the tensor-core scan marks the passing 32-entry groups, k_dense_extract turns
+    // them into survivors; passes over query tiles keep the bitmap within the workspace
+    const int64_t per = phase2_tiles_per_pass(p.n_tiles, n_qt, G, ix.units_per_cta, ws.gbits_cap);
+    if (per == 0) return cudaErrorInvalidValue;  // prepare_search sizes the bitmap for one tile at least
+    for (int64_t qt0 = 0; qt0 < n_qt; qt0 += per) {
+        const int64_t nqt = min64(per, n_qt - qt0), q0 = qt0 * kDQ;
+        DenseParams pp = p;
+        int64_t chunks = 0;
+        pp.qpre = static_cast<const char *>(p.qpre) + q0 * kp * 2;  // 2 kp bytes a query (BF16, or e4m3 hi + lo)
+        pp.nq = min64(nq - q0, nqt * kDQ);
+        pp.n_qt = nqt;
+        dense_chunking(p.n_tiles, nqt, G, ix.units_per_cta, &pp.tiles_per_chunk, &chunks);
+        pp.n_units = nqt * chunks;
+        pp.tau = ws.tau + q0;
+        pp.gbits = ws.gbits;
+        pp.words = (pp.tiles_per_chunk + 15) / 16;
+        const int grid = (int)min64(G, pp.n_units);
+        ExtractParams x{};
+        x.pre = f8 ? (const void *)ix.pre8 : (const void *)ix.pre16;
+        x.qpre32 = ws.qpre32 + q0 * ix.k_pad4;
+        x.gbits = ws.gbits;
+        x.n = ix.n;
+        x.n_tiles = p.n_tiles;
+        x.nq = pp.nq;
+        x.q_pad = nqt * kDQ;
+        x.tiles_per_chunk = pp.tiles_per_chunk;
+        x.chunks = chunks;
+        x.words = pp.words;
+        x.tau = ws.tau + q0;
+        x.bucket = ws.bucket + q0 * ws.bucket_cap;
+        x.count = ws.count + q0;
+        x.cap = ws.bucket_cap;
+        cudaError_t e = cudaErrorNotSupported;
+        switch (kp) {
+            case 16: e = f8 ? launch_kp<16, true>(pp, 2, grid, st) : launch_kp<16, false>(pp, 2, grid, st); break;
+            case 32: e = f8 ? launch_kp<32, true>(pp, 2, grid, st) : launch_kp<32, false>(pp, 2, grid, st); break;
+            case 64: e = f8 ? launch_kp<64, true>(pp, 2, grid, st) : launch_kp<64, false>(pp, 2, grid, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        switch (kp) {
+            case 16: e = f8 ? launch_extract<16, true>(x, st) : launch_extract<16, false>(x, st); break;
+            case 32: e = f8 ? launch_extract<32, true>(x, st) : launch_extract<32, false>(x, st); break;
+            case 64: e = f8 ? launch_extract<64, true>(x, st) : launch_extract<64, false>(x, st); break;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace hn

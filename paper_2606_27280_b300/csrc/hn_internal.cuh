@@ -63,6 +63,8 @@ struct Workspace {
     int32_t *count = nullptr;          // [q_cap] survivor counts (may exceed bucket_cap)
     unsigned long long *key1 = nullptr;// [q_cap] Phase-1 best (score, index) key (stream scan)
     unsigned long long *cand = nullptr;// [q_cap][cand_slots] Phase-1 per-chunk bests (dense scan)
+    uint32_t *gbits = nullptr;         // dense Phase 2: bits of the 16-entry groups that reached tau_q
+    int64_t gbits_cap = 0;             // allocated words of gbits
     int64_t cand_cap = 0;              // allocated length of cand
     int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
@@ -196,5 +198,9 @@ cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);
 int32_t proposal_blocks(const hn_proposal *p);
 int32_t proposal_k(const hn_proposal *p);
 int64_t dense_cand_slots(const Index &ix, int64_t nq);
+// uint32 words of the dense Phase-2 group bitmap the workspace holds for nq queries
+int64_t dense_gbits_words(const Index &ix, int64_t nq);
+// kernel launches of one dense Phase 2 for nq queries (with the workspace as sized)
+int64_t dense_phase2_launches(const Index &ix, int64_t nq);
 
 }  // namespace hn

@@ -51,6 +51,22 @@ def test_struct_sizes_match_header(hn):
     assert ctypes.sizeof(hn.TuneResult) == 288
 
 
+def header_enums():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(HN_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_header_enums(hn):
+    e = header_enums()
+    pairs = {"HN_PREFIX_F32": hn.PREFIX_F32, "HN_PREFIX_BF16": hn.PREFIX_BF16, "HN_PREFIX_FP8_E4M3": hn.PREFIX_FP8,
+             "HN_PREFIX_I8": hn.PREFIX_I8, "HN_SCAN_AUTO": hn.SCAN_AUTO, "HN_SCAN_STREAM": hn.SCAN_STREAM,
+             "HN_SCAN_DENSE": hn.SCAN_DENSE}
+    for name, value in pairs.items():
+        assert e[name] == value, name
+    for code, name in hn._STATUS_NAMES.items():
+        assert e[name] == code, name
+
+
 def test_version(hn):
     assert hn.version() == (0, 1)
 
@@ -90,7 +106,7 @@ def test_index_build_host_checks(hn):
     assert h.value is None  # *out cleared on failure
     assert hn._lib.hn_index_build(ctypes.c_void_p(0x1000), 0, 128, 8, 0.1, None, ctypes.byref(h), None) == \
         hn.ERR_INVALID_ARG
-    bad = hn.IndexOpts(prefix=7)
+    bad = hn.IndexOpts(prefix=4)   # one past HN_PREFIX_I8
     assert hn._lib.hn_index_build(ctypes.c_void_p(0x1000), 10, 128, 8, 0.1, ctypes.byref(bad), ctypes.byref(h),
                                   None) == hn.ERR_INVALID_ARG
     res = hn.IndexOpts(prefix=0)

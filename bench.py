@@ -406,7 +406,8 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = measured_traffic(args.workload, prefix_name) if st["scan"] == hn.SCAN_DENSE else None
     roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
-    roof["kernel"] = "prefix scan (Phase 1 and Phase 2 launches)"
+    roof["kernel"] = ("prefix scan (Phase 1 and Phase 2 launches; a dense Phase 2 includes its survivor "
+                      "extraction kernel)")
     roof["algorithmic"] = (f"2*Q*N*K = {flops:.3e} {'int ops' if prefix_name == 'i8' else 'flop'} per launch "
                            f"(Q={nq}, N={c['n']}, K={k_alg})")
     roof["avg_launch_ms"] = scan_ms_avg

@@ -209,8 +209,11 @@ hn_status hn_index_get_info(const hn_index *index, hn_index_info *info);
  * survivors are scored in FP32, and the ones within the FP32 error band of
  * the best are scored again in binary64 to pick the exact winner.
  * The index's scratch storage is reused and grown on demand (device
- * allocation on first use and after an overflow).  Calls on one index must
- * not overlap.  Checks the query norm identities (HN_ERR_NOT_NORMALIZED).
+ * allocation on first use and after an overflow).  Besides the per-query
+ * survivor slots it holds, for the tensor-core scan, one bit per (query,
+ * 32-entry group): nq * n / 256 bytes (1 GB for 65,536 queries over 4M
+ * entries), at most 4 GiB (larger batches take Phase 2 in passes).  Calls on
+ * one index must not overlap.  Checks the query norm identities (HN_ERR_NOT_NORMALIZED).
  * Synchronises `stream` once at the end.  opts and stats may be NULL.
  */
 hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_search_opts *opts,

@@ -570,9 +570,10 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
     return cudaGetLastError();
 }
 
-// Passes of the dense Phase 2 over query tiles so that the group bitmap of a pass fits
-// `cap` words (0 if even one query tile does not fit).
-static int64_t phase2_tiles_per_pass(int64_t n_tiles, int64_t n_qt, int G, int upc, int64_t cap);
+// Query tiles of the dense Phase-2 pass that starts at tile qt0: as many as fit the group
+// bitmap's `cap` words (each pass is sized on its own: the chunking, and with it the word
+// rounding, depends on the pass's tile count); 0 if even one tile does not fit.
+static int64_t phase2_pass_tiles(int64_t n_tiles, int64_t n_qt, int64_t qt0, int G, int upc, int64_t cap);
 
 // Words of the Phase-2 group bitmap for a pass over n_qt query tiles.
 static int64_t gbits_words(int64_t n_tiles, int64_t n_qt, int G, int upc) {
@@ -591,18 +592,23 @@ int64_t dense_gbits_words(const Index &ix, int64_t nq) {
     return std::max(std::min(all, kGbitsMaxWords), one);
 }
 
-static int64_t phase2_tiles_per_pass(int64_t n_tiles, int64_t n_qt, int G, int upc, int64_t cap) {
-    int64_t per = n_qt;
-    while (per > 1 && gbits_words(n_tiles, per, G, upc) > cap) per = (per + 1) / 2;
-    return gbits_words(n_tiles, per, G, upc) > cap ? 0 : per;
+static int64_t phase2_pass_tiles(int64_t n_tiles, int64_t n_qt, int64_t qt0, int G, int upc, int64_t cap) {
+    int64_t nqt = n_qt - qt0;
+    while (nqt > 1 && gbits_words(n_tiles, nqt, G, upc) > cap) nqt = (nqt + 1) / 2;
+    return gbits_words(n_tiles, nqt, G, upc) > cap ? 0 : nqt;
 }
 
 // Kernel launches of one dense Phase 2 (a scan and an extraction per pass).
 int64_t dense_phase2_launches(const Index &ix, int64_t nq) {
-    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
-    const int64_t per =
-        phase2_tiles_per_pass(ix.n_tiles * (kTileE / kDE), n_qt, num_sms(), ix.units_per_cta, ix.ws.gbits_cap);
-    return per > 0 ? 2 * ((n_qt + per - 1) / per) : 0;
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ, n_tiles = ix.n_tiles * (kTileE / kDE);
+    int64_t launches = 0;
+    for (int64_t qt0 = 0; qt0 < n_qt;) {
+        const int64_t nqt = phase2_pass_tiles(n_tiles, n_qt, qt0, num_sms(), ix.units_per_cta, ix.ws.gbits_cap);
+        if (nqt == 0) break;
+        launches += 2;
+        qt0 += nqt;
+    }
+    return launches;
 }
 
 template <int KP, bool F8>
@@ -645,10 +651,11 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     }
     // Phase 2: the tensor-core scan marks the passing 32-entry groups, k_dense_extract turns
     // them into survivors; passes over query tiles keep the bitmap within the workspace
-    const int64_t per = phase2_tiles_per_pass(p.n_tiles, n_qt, G, ix.units_per_cta, ws.gbits_cap);
-    if (per == 0) return cudaErrorInvalidValue;  // prepare_search sizes the bitmap for one tile at least
-    for (int64_t qt0 = 0; qt0 < n_qt; qt0 += per) {
-        const int64_t nqt = min64(per, n_qt - qt0), q0 = qt0 * kDQ;
+    for (int64_t qt0 = 0; qt0 < n_qt;) {
+        const int64_t nqt = phase2_pass_tiles(p.n_tiles, n_qt, qt0, G, ix.units_per_cta, ws.gbits_cap);
+        if (nqt == 0) return cudaErrorInvalidValue;  // prepare_search sizes the bitmap for one tile at least
+        const int64_t q0 = qt0 * kDQ;
+        qt0 += nqt;
         DenseParams pp = p;
         int64_t chunks = 0;
         pp.qpre = static_cast<const char *>(p.qpre) + q0 * kp * 2;  // 2 kp bytes a query (BF16, or e4m3 hi + lo)

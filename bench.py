@@ -1,7 +1,8 @@
 """Benchmark: exact HN 1-NN queries/s on one B300 (or N, one process each).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c0|c1|c2|c3|c4] [--prefix f32|bf16|fp8|i8] [--scan auto|stream|dense]
+                    [--workload c0|c1|c2|c3|c4] [--prefix f32|bf16|fp8|i8]
+                    [--scan auto|stream|dense|dense2] [--clock-log PATH]
 
 Workload (default c2): N = 4,000,000 database entries, a batch of 65,536
 queries, D = 128, K = 16, alpha = 1/8, clustered synthetic descriptors
@@ -13,9 +14,12 @@ seeded by the learned block proposal with the plain search on c2's data;
 c4 is uneven batched serving over 16 indexes.
 
 A step is one pass of the hot path over one query batch, all through the C
-ABI: HN normalisation of the raw queries, query prefix packing, Phase-1
-prefix scan, threshold from the Phase-1 winner, Phase-2 prefix scan with the
-bound test, survivor rescore with binary64 near-ties, argmax.  The database
+ABI: HN normalisation of the raw queries, query prefix packing, the prefix
+scan, threshold from the best scanned candidates, the bound test, survivor
+rescore with binary64 near-ties, argmax.  The dense scan (BF16/FP8 prefix on
+the tensor cores) computes the prefix product once per step by default
+(--scan dense); --scan dense2 runs Algorithm 1's two passes (Phase 1, then
+Phase 2 against the threshold).  The database
 index (normalisation and SoA packing of the 4M entries) is built once before
 timing; its build time is reported separately.  L2 is flushed (256 MiB
 write) before every timed step.
@@ -58,7 +62,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(hn_synth.CONFIGS) + ["c4"])
     ap.add_argument("--prefix", default=None, choices=["f32", "bf16", "fp8", "i8"])
-    ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense"])
+    ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense", "dense2"])
+    ap.add_argument("--clock-log", default=None,
+                    help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
     ap.add_argument("--hard", action="store_true",
@@ -72,10 +78,10 @@ DRAM_PROFILE = os.path.join(ROOT, "profiles", "k_dense_scan_c2_dram.md")
 DENSE_SOURCE = os.path.join(ROOT, "paper_2606_27280_b300", "csrc", "hn_dense.cu")
 
 
-def measured_traffic(workload: str, prefix: str):
-    """DRAM bytes (read + write) per dense-scan launch from the committed ncu capture, averaged
-    over the Phase-1 and Phase-2 launches; None unless the capture covers this workload and
-    prefix and the kernel source is unchanged since (its sha256 is recorded beside the figures)."""
+def measured_traffic(workload: str, prefix: str, scan: int):
+    """DRAM bytes (read + write) per launch of the reported dense-scan kernel from the committed
+    ncu capture; None unless the capture covers this workload, prefix and scan form and the
+    kernel source is unchanged since (its sha256 is recorded beside the figures)."""
     try:
         with open(DRAM_PROFILE) as f:
             text = f.read()
@@ -90,7 +96,8 @@ def measured_traffic(workload: str, prefix: str):
             vals[key.strip()] = val.strip().strip("`")
     if vals.get("source sha256") != sha or workload != "c2":
         return None
-    v = vals.get(f"{prefix} bytes per launch")
+    form = "one-pass" if scan == 2 else "two-pass"
+    v = vals.get(f"{prefix} {form} bytes per launch")
     return float(v) if v else None
 
 
@@ -110,14 +117,18 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, path: str | None = None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        if path is None:
+            import tempfile
+            fd, path = tempfile.mkstemp(prefix=f"hn_clocks_gpu{gpu_index}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -302,7 +313,8 @@ def main():
     k, alpha = c["k"], c["alpha"]
     prefix_name = args.prefix or default_prefix(args.workload)
     prefix = {"f32": hn.PREFIX_F32, "bf16": hn.PREFIX_BF16, "fp8": hn.PREFIX_FP8, "i8": hn.PREFIX_I8}[prefix_name]
-    scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE}[args.scan]
+    scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE,
+            "dense2": hn.SCAN_DENSE_TWO_PASS}[args.scan]
     stream = torch.cuda.current_stream()
 
     # ---- index (built once, outside the timed region)
@@ -337,7 +349,7 @@ def main():
     phase = []
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local, args.clock_log) as clocks:
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
@@ -375,48 +387,64 @@ def main():
         dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (the prefix scan, one launch per phase)
+    # ---- roofline of the dominant kernel: the prefix scan (2*Q*N*K flop per pass over the batch)
     peaks, peak_src = load_peaks()
+    clk = clocks.summary()
     st = phase[-1]
-    scan_ms = [p["ms_phase1"] for p in phase] + [p["ms_phase2"] for p in phase]
-    scan_ms_avg = sum(scan_ms) / len(scan_ms)
-    k_alg = k
-    flops = 2.0 * nq * c["n"] * k_alg
-    if st["scan"] == hn.SCAN_DENSE:
-        peak = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
-        src = f"{peak_src} bf16 sustained (cuBLAS)"
+    flops = 2.0 * nq * c["n"] * k
+    ms_step = 1e3 * t_max / args.steps
+    med = {kk: statistics.median(p[kk] for p in phase) for kk in ("ms_phase1", "ms_threshold", "ms_phase2")}
+    smax = (clk.get("sm_max_mhz") or 2032.0)
+    if st["scan"] in (hn.SCAN_DENSE, hn.SCAN_DENSE_TWO_PASS):
+        # a kernel timed alone against the burst cuBLAS figure when the SM clock held its
+        # maximum through the timed steps, else against the sustained one
+        at_max = bool(clk.get("sm_mhz")) and clk["sm_mhz"] >= 0.97 * smax
+        key = "bf16_tflops" if at_max else "bf16_tflops_sustained"
+        peak = peaks.get(key, FALLBACK_PEAKS[key])
+        src = f"{peak_src} {'bf16 burst' if at_max else 'bf16 sustained'} (cuBLAS)" + \
+              (", SM clock at its maximum in the timed steps" if at_max else ", SM clock below its maximum")
         if prefix_name == "fp8":   # e4m3 operands: the bf16 figure x the nominal fp8/bf16 ratio 4.5/2.25
             peak, src = 2.0 * peak, src + " x 2 (nominal fp8 / bf16 dense ratio)"
-        roof = {"bound": "tensor", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "peak_source": src}
+        bound, unit = "tensor", "TFLOP/s"
+        if st["scan"] == hn.SCAN_DENSE:
+            kernel = f"k_dense_scan<{info['k_pad']},4,{int(prefix_name == 'fp8')}> (one-pass tensor-core prefix scan)"
+            launches = {"scan (one pass, tensor cores)": med["ms_phase1"]}
+            other = {"threshold": med["ms_threshold"], "survivor extraction from the group codes": med["ms_phase2"]}
+        else:
+            kernel = f"k_dense_scan<{info['k_pad']},1|2,{int(prefix_name == 'fp8')}> (two-pass: Phase 1, Phase 2)"
+            launches = {"phase 1 scan": med["ms_phase1"], "phase 2 scan + survivor extraction": med["ms_phase2"]}
+            other = {"threshold": med["ms_threshold"]}
     elif prefix_name == "i8":
-        # CUDA-core dp4a (4 int8 products and their sum per instruction): a throughput probe
-        # measured 64 dp4a issued per clock per SM on B300 (half the FP32 FMA rate), so
-        # 148 SMs x 64 x 8 integer ops x max SM clock
-        smax = (clocks.summary().get("sm_max_mhz") or 2032.0)
+        # CUDA-core dp4a: a throughput probe measured 64 dp4a issued per clock per SM on B300
         peak = 148 * 64 * 8 * smax * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak, "unit": "TOP/s",
-                "peak_source": "derived: 148 SMs x 64 dp4a per clock (measured issue rate) x 8 int ops x max SM clock"}
+        bound, unit = "alu", "TOP/s"
+        src = "derived: 148 SMs x 64 dp4a per clock (measured issue rate) x 8 int ops x max SM clock"
+        kernel = "k_stream_scan (int8, dp4a)"
+        launches = {"phase 1 scan": med["ms_phase1"], "phase 2 scan": med["ms_phase2"]}
+        other = {"threshold": med["ms_threshold"]}
     else:
         # CUDA-core FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock
-        smax = (clocks.summary().get("sm_max_mhz") or 2032.0)
         peak = 148 * 128 * 2 * smax * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (scan_ms_avg * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = measured_traffic(args.workload, prefix_name) if st["scan"] == hn.SCAN_DENSE else None
-    roof["traffic_unit"] = "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
-    roof["kernel"] = ("prefix scan (Phase 1 and Phase 2 launches; a dense Phase 2 includes its survivor "
-                      "extraction kernel)")
-    roof["algorithmic"] = (f"2*Q*N*K = {flops:.3e} {'int ops' if prefix_name == 'i8' else 'flop'} per launch "
-                           f"(Q={nq}, N={c['n']}, K={k_alg})")
-    roof["avg_launch_ms"] = scan_ms_avg
-    if st["scan"] == hn.SCAN_DENSE:
-        # the epilogue's own floor: one FP32 max per score (Phase 2) on 148 SMs x 128 lanes at the
-        # maximum clock; Phase 1 reduces packed FP16 pairs, half an instruction per score
-        smax = (clocks.summary().get("sm_max_mhz") or 2032.0) * 1e6
-        roof["epilogue_alu_floor_ms"] = {"phase1": 1e3 * 0.5 * nq * c["n"] / (148 * 128 * smax),
-                                         "phase2": 1e3 * 1.0 * nq * c["n"] / (148 * 128 * smax)}
+        bound, unit = "alu", "TFLOP/s"
+        src = "derived: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+        kernel = "k_stream_scan (FP32 FMA)"
+        launches = {"phase 1 scan": med["ms_phase1"], "phase 2 scan": med["ms_phase2"]}
+        other = {"threshold": med["ms_threshold"]}
+    per_launch = {name: {"ms": ms_, "achieved": flops / (ms_ * 1e-3) / 1e12,
+                         "frac": flops / (ms_ * 1e-3) / 1e12 / peak} for name, ms_ in launches.items()}
+    first = next(iter(per_launch.values()))
+    roof = {"bound": bound, "achieved": first["achieved"], "peak": peak, "unit": unit, "frac": first["frac"],
+            "traffic": None, "peak_source": src, "kernel": kernel,
+            "algorithmic": f"2*Q*N*K = {flops:.3e} {'int ops' if prefix_name == 'i8' else 'flop'} per scan launch "
+                           f"(Q={nq}, N={c['n']}, K={k})",
+            "avg_launch_ms": first["ms"], "per_launch": per_launch, "other_launches_ms": other,
+            "step_frac": flops / (ms_step * 1e-3) / 1e12 / peak,
+            "step_frac_note": "one 2*Q*N*K prefix product per step / whole step time / peak"}
+    roof["traffic"] = measured_traffic(args.workload, prefix_name, st["scan"]) if bound == "tensor" else None
+    roof["traffic_unit"] = "bytes per launch of the kernel above (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    if bound == "tensor":
+        # the epilogue's own floor: one FP32 max per score on 148 SMs x 128 lanes at the maximum clock
+        roof["epilogue_alu_floor_ms"] = 1e3 * nq * c["n"] / (148 * 128 * smax * 1e6)
 
     line = {
         "metric": "exact 1-NN queries/s", "value": value, "unit": "queries/s", "n_gpus": world,
@@ -429,10 +457,11 @@ def main():
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * 128 * 4,
                 "d2h_bytes_per_step": nq * (8 + 8)},
         "gpu_launches": args.steps * (st["kernels"] + 1),
-        "clocks": clocks.summary(),
+        "clocks": clk,
         "phases_ms": {kk: statistics.median(p[kk] for p in phase) for kk in
                       ("ms_prep", "ms_phase1", "ms_threshold", "ms_phase2", "ms_rescore", "ms_total")},
-        "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan")},
+        "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan",
+                                               "passes", "kernels")},
         "survivor_frac": st["survivors"] / (nq * c["n"]),
         "index_build_s": build_s, "index_bytes": info["device_bytes"],
     }
@@ -623,7 +652,7 @@ def run_serving(args, hn, torch, world, rank, dist, barrier):
         step()
     torch.cuda.synchronize()
     barrier()
-    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clocks:
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0")), args.clock_log) as clocks:
         ms, outs = _timed_steps(torch, stream, args.steps, step, flush)
     st = outs[-1]
     if rank == 0:

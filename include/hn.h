@@ -68,9 +68,18 @@ typedef enum hn_prefix {
 
 /* Which prefix-scan kernel runs (Phase 1 and Phase 2 of Algorithm 1). */
 typedef enum hn_scan {
-    HN_SCAN_AUTO = 0,   /* pick by query count and prefix type */
-    HN_SCAN_STREAM = 1, /* CUDA-core FMA scan streaming the prefix (any prefix type) */
-    HN_SCAN_DENSE = 2   /* tcgen05 tensor-core scan (HN_PREFIX_BF16 and HN_PREFIX_FP8_E4M3) */
+    HN_SCAN_AUTO = 0,   /* pick by query count and prefix type (HN_SCAN_DENSE from the autotuned
+                           batch size on a BF16 or FP8 index, else HN_SCAN_STREAM) */
+    HN_SCAN_STREAM = 1, /* CUDA-core FMA scan streaming the prefix (any prefix type), two passes */
+    HN_SCAN_DENSE = 2,  /* tcgen05 tensor-core scan (HN_PREFIX_BF16 and HN_PREFIX_FP8_E4M3), ONE pass
+                           over the prefix product: it keeps an 8-bit code of the largest score of
+                           every (query, 32-entry group) and the best group per (query, entry chunk);
+                           the threshold comes from those candidates, and the survivors from the
+                           groups whose code reaches the threshold's code.  Same result as the two
+                           passes of Algorithm 1; the scratch holds nq * n / 32 bytes of codes */
+    HN_SCAN_DENSE_TWO_PASS = 3 /* tcgen05 tensor-core scan in Algorithm 1's two passes: Phase 1 for
+                           the threshold candidates, Phase 2 against the threshold (one bit per
+                           (query, 32-entry group), nq * n / 256 bytes) */
 } hn_scan;
 
 typedef struct hn_index_opts {
@@ -98,6 +107,17 @@ typedef struct hn_search_opts {
                              the best fully scored threshold candidate always stays a candidate (as
                              Algorithm 1 keeps its Phase-1 winner).  1-NN only (hn_search_batch) */
     float beta;           /* with soft = 1: 0 <= beta <= alpha (else HN_ERR_INVALID_ARG) */
+    int64_t scratch_limit; /* > 0: bytes the dense scan's group map (codes or bits) may take; a larger
+                              batch runs in passes over 256-query tiles (at least one tile a pass,
+                              whatever the limit).  0: up to 16 GiB of codes (one-pass) or 4 GiB of
+                              bits (two-pass) */
+    uint64_t wait_limit_ns; /* device-side wait limit of the dense scan's main loop in nanoseconds of
+                              GPU global time; 0 = 2 s, else 1e3 .. 1e10 (HN_ERR_INVALID_ARG
+                              otherwise).  A wait that runs out ends the kernel early (its copies and
+                              MMAs still drain with the 2 s limit) and the call returns
+                              HN_ERR_TIMEOUT.  Limits of a few microseconds make the waits of a
+                              normally loaded scan run out: used to exercise that path */
+    int32_t reserved[4];  /* must be zero */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */
@@ -110,12 +130,16 @@ typedef struct hn_search_stats {
     int32_t reruns;         /* Phase-2 re-runs after survivor-slot overflow */
     int32_t scan;           /* hn_scan that ran */
     int32_t kernels;        /* kernel launches made by this call (all runs) */
-    int32_t reserved;
+    int32_t passes;         /* dense scan: passes over query tiles of the last run (its group map
+                               held that many parts of the batch; see scratch_limit); 0 otherwise */
     /* device time of each step of the last run, milliseconds (with opts->timing) */
     float ms_prep;          /* query prefix packing and slack computation */
-    float ms_phase1;        /* Phase-1 prefix scan, or the proposal's inference when seeded */
+    float ms_phase1;        /* Phase-1 prefix scan, or the proposal's inference when seeded;
+                               HN_SCAN_DENSE: its one tensor-core scan (first pass) */
     float ms_threshold;     /* full score of the Phase-1 (or proposed) candidates -> threshold */
-    float ms_phase2;        /* Phase-2 prefix scan with the bound test */
+    float ms_phase2;        /* Phase-2 prefix scan with the bound test; HN_SCAN_DENSE: the
+                               extraction of the survivors from the group codes (plus any
+                               further passes over query tiles) */
     float ms_rescore;       /* survivor rescore, binary64 near-ties, argmax */
     float ms_total;         /* whole search */
 } hn_search_stats;
@@ -343,6 +367,27 @@ hn_status hn_proposal_destroy(hn_proposal *proposal);
  */
 hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
                            const int32_t *y, int32_t batch, float *loss, float *grads, void *stream);
+
+/*
+ * Verification entry point of the scan arithmetic of the reduced-precision
+ * prefixes (ext. 1; the paper scans FP32 prefixes and has no counterpart).  For
+ * nq HN-normalised queries q (nq x 128 float32, device) and an index with a BF16
+ * or FP8 prefix, writes
+ *   out_scores[j * n + i]  the prefix score of query j and entry i exactly as the
+ *                          search computes it: path 0 the tensor-core scan (the
+ *                          FP32 accumulator of q^ . x^; FP8: RN(acc s_i/256 + b_i)),
+ *                          path 1 the CUDA-core FMA chain of the survivor extraction
+ *                          and of the stream scan;
+ *   out_slack[j]           E_q, what the search adds to a prefix score in its bound
+ *                          test: the scan's rounding error, |q_minor| max|x_minor|
+ *                          and 1e-12 for the binary64 rounding, rounded up.
+ * The search is exact because  <q_j, x_i> <= out_scores[j*n+i] + out_slack[j]
+ * for every pair (Eq. 2 and Eq. 3 with rounding terms).  out_scores: nq * n
+ * float32, out_slack: nq float32 (device, caller-owned).  Requires
+ * 1 <= nq, nq * n <= 2^28 and path 0 or 1.  Synchronises `stream`.
+ */
+hn_status hn_prefix_scores(hn_index *index, const float *q, int64_t nq, int32_t path, float *out_scores,
+                           float *out_slack, void *stream);
 
 /*
  * Brute-force baseline (the denominator of the paper's speed-ups, §6.2): the

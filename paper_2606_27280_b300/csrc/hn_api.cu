@@ -225,6 +225,12 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     TRY(cudaMemcpyAsync(ix.host_max, ix.dev_max, sizeof(ix.host_max), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
 #undef TRY
+    {
+        // one-pass dense scan: group scores lie within about |q^| max|x^| (+ the FP8 error
+        // term); the code maps [-B, B] onto 1..255 (any scale is exact, B sets the step)
+        const double b = 1.05 * (std::sqrt(1.0 - alpha) * ix.host_max[3] + (double)ix.qt * ix.host_max[2]);
+        ix.code_inv = b > 0 ? (float)(127.0 / b) : 1.f;
+    }
     ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
                (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) +
                (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) +
@@ -306,15 +312,23 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         HN_CUDA(proposal_topk(sp, q, nq, topk, blocks, s));
         HN_CUDA(mark(2));
         HN_CUDA(launch_seed_blocks(ix, q, nq, blocks, topk, minor_scale < 1.f, s));
+    } else if (scan == HN_SCAN_DENSE) {
+        // one pass: the prefix product once, then the threshold and the survivors from the
+        // group codes (ev[2], ev[3], ev[4] mark the scan, threshold and extraction)
+        HN_CUDA(launch_dense_onepass(ix, q, nq, nn, minor_scale < 1.f, s, timing ? &ws.ev[2] : nullptr));
     } else {
-        HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 1, s)
-                                      : launch_stream_scan(ix, nq, 1, s, nn > 1 ? ws.cand : nullptr));
+        HN_CUDA(scan == HN_SCAN_DENSE_TWO_PASS ? launch_dense_scan(ix, nq, 1, s)
+                                               : launch_stream_scan(ix, nq, 1, s, nn > 1 ? ws.cand : nullptr));
         HN_CUDA(mark(2));
-        HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE, nn, minor_scale < 1.f, s));
+        HN_CUDA(launch_seed_threshold(ix, q, nq, scan == HN_SCAN_DENSE_TWO_PASS, nn, minor_scale < 1.f, s));
     }
-    HN_CUDA(mark(3));
-    HN_CUDA(scan == HN_SCAN_DENSE ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
-    HN_CUDA(mark(4));
+    if (seed || scan != HN_SCAN_DENSE) {
+        // seeded: the proposal replaces Phase 1, and a dense Phase 2 takes the two-pass form's
+        // bit scan against the known threshold
+        HN_CUDA(mark(3));
+        HN_CUDA(scan != HN_SCAN_STREAM ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
+        HN_CUDA(mark(4));
+    }
     HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s)
                    : launch_rescore(ix, q, nq, out_idx, out_sim, s));
     HN_CUDA(mark(5));
@@ -327,17 +341,18 @@ namespace hn {
 
 int pick_scan(const Index &ix, int64_t nq, int requested) {
     if (requested != HN_SCAN_AUTO) return requested;
-    return (dense_scan_supported(ix) && nq >= ix.dense_min_q) ? HN_SCAN_DENSE : HN_SCAN_STREAM;
+    return (dense_scan_supported(ix) && nq >= ix.dense_min_q) ? HN_SCAN_DENSE : HN_SCAN_STREAM;  // one-pass dense
 }
 
 // Size the index's scratch for nq queries and `cap` survivor slots (may allocate).
-hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn) {
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn, bool seeded, int64_t scratch_limit) {
     Workspace &ws = ix.ws;
     hn_status st = ensure_ws(ix, nq, cap);
     if (st != HN_OK) return st;
-    if (scan == HN_SCAN_DENSE || nn > 1) {
+    const bool dense = scan == HN_SCAN_DENSE || scan == HN_SCAN_DENSE_TWO_PASS;
+    if (dense || nn > 1) {
         // candidate keys: dense segments, or one entry per stream-scan entry range (top-k)
-        const int64_t slots = scan == HN_SCAN_DENSE ? dense_cand_slots(ix, nq) : stream_cand_slots(ix, nq);
+        const int64_t slots = dense ? dense_cand_slots(ix, nq) : stream_cand_slots(ix, nq);
         const int64_t need = ((nq + kQPad - 1) / kQPad * kQPad) * slots;
         if (need > ws.cand_cap) {
             cudaFree(ws.cand);
@@ -349,8 +364,12 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn) {
         }
         ws.cand_slots = (int32_t)slots;
     }
-    if (scan == HN_SCAN_DENSE) {
-        const int64_t need = dense_gbits_words(ix, nq);
+    if (dense) {
+        // the one-pass form's code map, or the two-pass form's bitmap (seeded searches take the
+        // latter), within the search's scratch limit; ws.gbits_limit keeps that limit for the launch
+        const bool onepass = scan == HN_SCAN_DENSE && !seeded;
+        const int64_t need = dense_gbits_words(ix, nq, onepass, scratch_limit);
+        ws.gbits_limit = scratch_limit > 0 ? need : 0;
         if (need > ws.gbits_cap) {
             cudaFree(ws.gbits);
             ws.gbits = nullptr;
@@ -424,9 +443,15 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         if (nn > 1) return fail(HN_ERR_UNSUPPORTED, "the proposal seeds the 1-NN search only");
     }
     const int scan = pick_scan(ix, nq, o.scan);
-    if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE) return fail(HN_ERR_INVALID_ARG, "bad scan kind");
-    if (scan == HN_SCAN_DENSE && !dense_scan_supported(ix))
+    if (scan != HN_SCAN_STREAM && scan != HN_SCAN_DENSE && scan != HN_SCAN_DENSE_TWO_PASS)
+        return fail(HN_ERR_INVALID_ARG, "bad scan kind");
+    if (scan != HN_SCAN_STREAM && !dense_scan_supported(ix))
         return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 or FP8 prefix index");
+    if (o.scratch_limit < 0) return fail(HN_ERR_INVALID_ARG, "scratch_limit < 0");
+    if (o.wait_limit_ns != 0 && (o.wait_limit_ns < 1000 || o.wait_limit_ns > 10000000000ull))
+        return fail(HN_ERR_INVALID_ARG, "need wait_limit_ns = 0 or 1e3 <= wait_limit_ns <= 1e10");
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->n_queries = nq;
@@ -445,12 +470,28 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
     }
     int32_t reruns = 0, kernels = 0;
     for (;;) {
-        hn_status st = prepare_search(ix, nq, scan, cap, nn);
+        hn_status st = prepare_search(ix, nq, scan, cap, nn, o.seed != nullptr, o.scratch_limit);
         if (st != HN_OK) return st;
+        ws.wait_ns = o.wait_limit_ns;
         st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
-        if (st != HN_OK) return st;
-        kernels += o.seed ? 4 + 5 * (int32_t)((nq + 8191) / 8192) : 5;
-        if (scan == HN_SCAN_DENSE) kernels += (int32_t)dense_phase2_launches(ix, nq) - 1;  // scan + extraction per pass
+        ws.wait_ns = 0;
+        if (st != HN_OK) {
+            ws.gbits_limit = 0;
+            return st;
+        }
+        // query prep and rescore, plus Phase 1 and the threshold (or the seed's kernels), plus
+        // the Phase-2 launches; the one-pass dense form counts its scan, threshold and extraction
+        int32_t passes = 0;
+        if (scan == HN_SCAN_DENSE && !o.seed) {
+            const int32_t l = (int32_t)dense_phase2_launches(ix, nq, true);
+            kernels += 2 + l;
+            passes = l / 3;
+        } else {
+            const int32_t l = scan == HN_SCAN_STREAM ? 1 : (int32_t)dense_phase2_launches(ix, nq, false);
+            kernels += (o.seed ? 3 + 5 * (int32_t)((nq + 8191) / 8192) : 4) + l;
+            passes = scan == HN_SCAN_STREAM ? 0 : l / 2;
+        }
+        ws.gbits_limit = 0;  // the scratch limit holds for this search only
         HN_CUDA(cudaStreamSynchronize(s));
         int32_t want = 0;
         st = check_search(ix, nq, &want);
@@ -462,6 +503,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
                 stats->fp64_rescored = hc[CT_FP64];
                 stats->reruns = reruns;
                 stats->kernels = kernels;
+                stats->passes = passes;
                 if (timing) {
                     float *ms[5] = {&stats->ms_prep, &stats->ms_phase1, &stats->ms_threshold, &stats->ms_phase2,
                                     &stats->ms_rescore};
@@ -489,6 +531,29 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
 hn_status hn_search_topk(hn_index *index, const float *q, int64_t nq, int32_t k, const hn_search_opts *opts,
                          int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream) {
     return search_impl(index, q, nq, k, opts, out_idx, out_sim, stats, stream);
+}
+
+hn_status hn_prefix_scores(hn_index *index, const float *q, int64_t nq, int32_t path, float *out_scores,
+                           float *out_slack, void *stream) {
+    if (!index) return fail(HN_ERR_INVALID_ARG, "index is NULL");
+    Index &ix = index->ix;
+    if (!dense_scan_supported(ix)) return fail(HN_ERR_UNSUPPORTED, "needs a BF16 or FP8 prefix index");
+    if (path != 0 && path != 1) return fail(HN_ERR_INVALID_ARG, "path must be 0 or 1");
+    if (nq < 1 || nq > ((int64_t)1 << 28) / ix.n) return fail(HN_ERR_INVALID_ARG, "need 1 <= nq and nq * n <= 2^28");
+    if (!q || !out_scores || !out_slack || !aligned16(q)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    hn_status st = ensure_ws(ix, nq, std::max<int32_t>(ix.ws.bucket_cap, 1));
+    if (st != HN_OK) return st;
+    Workspace &ws = ix.ws;
+    HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
+    HN_CUDA(launch_query_prep(ix, q, nq, 1.f, s));
+    HN_CUDA(launch_prefix_scores(ix, nq, path, out_scores, s));
+    HN_CUDA(cudaMemcpyAsync(out_slack, ws.qeps, sizeof(float) * nq, cudaMemcpyDeviceToDevice, s));
+    HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    HN_CUDA(cudaStreamSynchronize(s));
+    if (ws.h_status[ST_NOT_NORMALIZED]) return fail(HN_ERR_NOT_NORMALIZED, "a query violates the HN norm identities");
+    if (ws.h_status[ST_TIMEOUT]) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
+    return HN_OK;
 }
 
 hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,

@@ -1,6 +1,16 @@
 // Dense prefix scan on the 5th-generation tensor cores (tcgen05), Phase 1 and
 // Phase 2 of Algorithm 1 (§3.3) for a BF16 major prefix.
 //
+// Two forms.  The two-pass form runs Algorithm 1's phases as two scans (PHASE 1,
+// then PHASE 2 against the threshold).  The one-pass form (PHASE 4) computes the
+// prefix product once: its epilogue keeps, per (query, 32-entry group), an 8-bit
+// code of the group's largest score (hn_internal.cuh) and, per (query, chunk, entry
+// half), the best group as a threshold candidate.  The threshold kernel then scores
+// the candidates in full and k_dense_extract_codes takes the survivors from the
+// groups whose code reaches code(tau_q).  The codes cost one byte per 32 scores of
+// HBM traffic (written once, read once), against a second tensor-core pass over all
+// Q x N scores.  PHASE 3 writes every FP32 score to memory (verification only).
+//
 // A work unit pairs 256 queries (two 128-row A tiles, K-major) with a stream
 // of 128-entry B tiles (K-major); per B tile two tcgen05.mma per 16 prefix
 // columns compute the 256 x 128 block of prefix scores s~ = q^ . x^ into tensor
@@ -58,7 +68,7 @@ constexpr int kIssuers = 2;                      // MMA-issuing threads, one per
 constexpr int kEpiWarps = 16;                    // 4 per SM sub-partition, 64 accumulator columns each
 constexpr int kEpiWarp0 = 1 + kIssuers;          // warp 0 producer, warps 1..kIssuers MMA, then epilogue
 constexpr int kDenseThreads = (kEpiWarp0 + kEpiWarps) * 32;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // default main-loop wait limit, and every drain's
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
 struct DenseParams {
@@ -67,9 +77,14 @@ struct DenseParams {
     int64_t n, n_tiles, nq;
     int64_t n_qt, tiles_per_chunk, n_units;
     const float *tau;
-    unsigned long long *cand;     // [nq][2 * chunks] Phase-1 (best score, segment id) per (query, chunk, entry half)
-    uint32_t *gbits;              // Phase 2: [chunk][half][word][n_qt * 256] passing-group bits, 16 tiles a word
-    int64_t words;                // words per (chunk, half): ceil(tiles_per_chunk / 16)
+    unsigned long long *cand;     // [nq][2 * chunks] PHASE 1: (best score, 64-entry segment id), PHASE 4:
+                                  //   (best group score, 32-entry group id) per (query, chunk, entry half)
+    uint32_t *gbits;              // [chunk][half][word][n_qt * 256] group map: PHASE 2 passing-group bits,
+                                  //   16 tiles a word; PHASE 4 group codes, 2 tiles (4 codes) a word
+    int64_t words;                // words per (chunk, half): ceil(tiles_per_chunk / 16), PHASE 4: / 2
+    float code_inv, code_base;    // PHASE 4: the group code (hn_internal.cuh)
+    float *dump;                  // PHASE 3: [nq][n] every FP32 score (Phase-2 arithmetic)
+    uint64_t wait_ns;             // limit of every main-loop wait (the drains keep kWaitLimitNs)
     int32_t *status;
 };
 constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
                 const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
                 const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
-                if (!(ok = mbar_wait(smem_u32(&a_empty[abuf]), aphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                if (!(ok = mbar_wait(smem_u32(&a_empty[abuf]), aphase ^ 1, abort_flag, p.wait_ns))) break;
                 mbar_arrive_expect_tx(smem_u32(&a_full[abuf]), C::kA);
                 bulk_g2s(smem_u32(sA + abuf * C::kA), static_cast<const char *>(p.qpre) + qt * C::kA, C::kA,
                          smem_u32(&a_full[abuf]));
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                 if (++abuf == 2) { abuf = 0; aphase ^= 1; }
                 for (int64_t tt = t0; tt < t1; tt += C::kTPS) {
                     const uint32_t bytes = (uint32_t)min64(C::kTPS, t1 - tt) * C::kB;
-                    if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, kWaitLimitNs))) break;
+                    if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, p.wait_ns))) break;
                     mbar_arrive_expect_tx(smem_u32(&b_full[stage]), bytes);
                     bulk_g2s(smem_u32(sB + stage * C::kStageBytes), static_cast<const char *>(p.pre) + tt * C::kB,
                              bytes, smem_u32(&b_full[stage]));
@@ -203,8 +218,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
         // accumulator buffer i (256 columns: A tile `sub` in columns 128*sub ..).
         if (lane == 0) {
             const uint32_t me = (uint32_t)(warp - 1);
-            // Phase 1: FP16 operands, FP16 accumulator; Phase 2: BF16 operands, FP32 accumulator
-            // FP8: e4m3 operands, FP16 (Phase 1) or FP32 (Phase 2) accumulator
+            // Phase 1: FP16 operands, FP16 accumulator; PHASE 2-4: BF16 operands, FP32 accumulator
+            // FP8: e4m3 operands, FP16 (Phase 1) or FP32 (PHASE 2-4) accumulator
             constexpr uint32_t idesc = F8 ? (PHASE == 1 ? idesc_e4m3_f16(kTileQ, kDE) : idesc_e4m3_f32(kTileQ, kDE))
                                           : (PHASE == 1 ? idesc_f16_f16(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE));
             uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, uses = 0;
@@ -213,17 +228,17 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
                 const int64_t ch = u / p.n_qt;
                 const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
-                if (!(ok = mbar_wait(smem_u32(&a_full[abuf]), aphase, abort_flag, kWaitLimitNs))) break;
+                if (!(ok = mbar_wait(smem_u32(&a_full[abuf]), aphase, abort_flag, p.wait_ns))) break;
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA + abuf * C::kA);
                 for (int64_t tt = t0; ok && tt < t1; tt += C::kTPS) {
                     const int nt = (int)min64(C::kTPS, t1 - tt);
                     // wait for every fill of the ring, even one holding none of this issuer's
                     // tiles, so that the parity of the next wait on the slot cannot alias
-                    if (!(ok = mbar_wait(smem_u32(&b_full[stage]), sphase, abort_flag, kWaitLimitNs))) break;
+                    if (!(ok = mbar_wait(smem_u32(&b_full[stage]), sphase, abort_flag, p.wait_ns))) break;
                     for (int j = 0; j < nt; ++j, ++g) {
                         if ((uint32_t)(g & 1) != me) continue;
-                        if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, kWaitLimitNs))) break;
+                        if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, p.wait_ns))) break;
                         tc_fence_after();
                         const uint32_t b_addr = smem_u32(sB + stage * C::kStageBytes + j * C::kB);
 #pragma unroll
@@ -279,9 +294,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             const bool qvalid = q < p.nq;
             const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
             float best = -INFINITY;
-            int32_t bseg = -1;
-            uint32_t gword = 0;  // Phase 2: passing-group bits of the current 16 tiles
-            uint32_t *gb = PHASE == 2 ? p.gbits + (ch * 2 + half) * p.words * (p.n_qt * kDQ) + q : nullptr;
+            int32_t bseg = -1;   // PHASE 1: 64-entry segment of `best`; PHASE 4: its 32-entry group
+            uint32_t gword = 0;  // PHASE 2: passing-group bits of the current 16 tiles; PHASE 4: codes of 2 tiles
+            uint32_t *gb = (PHASE == 2 || PHASE == 4) ? p.gbits + (ch * 2 + half) * p.words * (p.n_qt * kDQ) + q
+                                                      : nullptr;
             const int32_t n32 = (int32_t)p.n;
             const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
             int32_t e0 = t0 * kDE + half * 64;    // first entry of this warp's 64 columns
@@ -291,7 +307,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                     const uint32_t buf = g & 1u;
                     // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
                     ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag,
-                                                           kWaitLimitNs));
+                                                           p.wait_ns));
                     if (!ok) break;
                     tc_fence_after();
                     // this tile's MMAs are done with the stage; the last tile of a short stage
@@ -335,6 +351,36 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                        if (PHASE == 4) {
+                            // one-pass form: the largest score of each 32-entry group.  FP8: the
+                            // group's largest raw accumulator A bounds its scores u_i = RN(acc_i s_i/256
+                            // + b_i) from above by max(RU(A smax + bmax), RU(A smin + bmax)) with the
+                            // group's scale range and largest error term (k_f8_group_bounds).
+                            float g0 = fmaxf(max16(v), max16(v + 16)), g1 = fmaxf(max16(v + 32), max16(v + 48));
+                            if (F8) {
+                                const float4 *gbd = reinterpret_cast<const float4 *>(
+                                                        smem + stage * C::kStageBytes + j * C::kB + f8_group_off(KP)) +
+                                                    half * 2;
+                                const float4 b0 = gbd[0], b1 = gbd[1];
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                                g0 = fmaxf(__fmaf_ru(g0, b0.x, b0.z), __fmaf_ru(g0, b0.y, b0.z));
+                                g1 = fmaxf(__fmaf_ru(g1, b1.x, b1.z), __fmaf_ru(g1, b1.y, b1.z));
+                            }
+                            // threshold candidate: the best group of this (chunk, entry half)
+                            const float m = fmaxf(g0, g1);
+                            if (m > best && (t < full_tiles || e0 < n32)) {
+                                best = m;
+                                bseg = (t * 2 + half) * 2 + (g1 > g0 ? 1 : 0);
+                            }
+                            // codes of the two groups; a word holds tiles 2w and 2w + 1 of the chunk
+                            const int32_t ti = t - t0;
+                            const uint32_t c01 = code_group(g0, p.code_inv, p.code_base) |
+                                                 (code_group(g1, p.code_inv, p.code_base) << 8);
+                            gword = (ti & 1) ? gword | (c01 << 16) : c01;
+                            if ((ti & 1) || t == t1 - 1) gb[(int64_t)(ti >> 1) * (p.n_qt * kDQ)] = gword;
+                            continue;
+                        }
                         if (F8) {
                             // u = fma(acc, s_i / 256, b_i): one rounding, packed pairs
                             const float4 *s4 = reinterpret_cast<const float4 *>(esc) + half * 16;
@@ -354,6 +400,15 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                             __syncwarp();
                             if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
                         }
+                        if (PHASE == 3) {
+                            // verification: every score of the Phase-2 arithmetic to memory
+                            if (qvalid) {
+                                float *d = p.dump + q * p.n;
+                                for (int i = 0; i < 64; ++i)
+                                    if (e0 + i < n32) d[e0 + i] = v[i];
+                            }
+                            continue;
+                        }
                         // bit 2 (tile mod 16) + k: the maximum of the 32 scores 32k .. 32k + 31 reaches
                         // tau_q.  The bits go out as one coalesced word per 16 tiles; k_dense_extract
                         // finds the survivors of those groups.  Nothing here waits on memory: the
@@ -371,7 +426,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             }
             if (!ok) break;
             // one writer per (query, chunk, entry half): no atomics, every slot written
-            if (PHASE == 1 && qvalid)
+            if ((PHASE == 1 || PHASE == 4) && qvalid)
                 p.cand[q * (2 * (p.n_units / p.n_qt)) + 2 * ch + half] =
                     bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
         }
@@ -403,6 +458,7 @@ struct ExtractParams {
     const float *tau;
     int32_t *bucket, *count;  // count: slots already used (soft mode: the kept best); may pass cap
     int32_t cap;
+    float code_inv, code_base;  // one-pass form: the group code of k_dense_scan<., 4, .>
 };
 
 template <int KP, bool F8>
@@ -493,6 +549,76 @@ __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
     }
 }
 
+// The same step for the one-pass form: the map holds an 8-bit code of every group's
+// largest score (4 codes a word: tiles 2w and 2w + 1 of the chunk, two groups each),
+// and a group is scored when its code reaches code(tau_q) (a non-decreasing code, so
+// every group whose largest score reaches tau_q is among them).  __vcmpgeu4 tests the
+// four codes of a word at once.
+template <int KP, bool F8>
+__global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // this thread's query
+    const bool qv = q < x.nq;
+    const float tau = qv ? x.tau[q] : INFINITY;
+    const uint32_t ct4 = code_threshold(tau, x.code_inv, x.code_base) * 0x01010101u;
+    const int64_t c = blockIdx.y;  // this block's entry chunk
+    const int64_t t0 = c * x.tiles_per_chunk;
+    const int64_t nt = min64(x.n_tiles - t0, x.tiles_per_chunk);
+    const int64_t nw = (nt + 1) / 2;
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t *gw = x.gbits + (c * 2 + h) * x.words * x.q_pad;
+        for (int64_t w0 = 0; w0 < nw; w0 += 8) {
+            uint32_t wv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nw) ? gw[(w0 + i) * x.q_pad + q] : 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t w = w0 + i;
+                // the top bit of every passing code's byte; the second tile of a chunk's last
+                // word exists only for an even tile count, and absent words pass nothing
+                uint32_t word = (qv && w < nw) ? (__vcmpgeu4(wv[i], ct4) & 0x80808080u) : 0u;
+                if (2 * w + 1 >= nt) word &= 0x00008080u;
+                unsigned pend = __ballot_sync(0xffffffffu, word != 0u);
+                while (pend) {
+                    const int o = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    uint32_t wo = __shfl_sync(0xffffffffu, word, o);
+                    const float to = __shfl_sync(0xffffffffu, tau, o);
+                    const int64_t qo = q - lane + o;
+                    const float *qp = x.qpre32 + qo * KP;
+                    while (wo) {
+                        const int b = (__ffs(wo) - 1) >> 3;  // code byte: tile 2w + b / 2, group b % 2
+                        wo &= wo - 1;
+                        const int64_t e = (t0 + w * 2 + (b >> 1)) * kDE + h * 64 + (b & 1) * 32 + lane;
+                        const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
+                        const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                        if (hb) {
+                            int base = 0;
+                            if (lane == o) base = atomicAdd(x.count + qo, __popc(hb));
+                            base = __shfl_sync(0xffffffffu, base, o);
+                            if (hit) {
+                                const int slot = base + __popc(hb & ((1u << lane) - 1u));
+                                if (slot < x.cap) x.bucket[qo * x.cap + slot] = (int32_t)e;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Verification: the CUDA-core score of every (query, entry) pair, computed by
+// group_entry_score -- the arithmetic of k_dense_extract and of the stream scan's
+// FMA chain over the same stored prefix.  One thread per pair.
+template <int KP, bool F8>
+__global__ void __launch_bounds__(256) k_fma_scores(const ExtractParams x, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= x.nq * x.n) return;
+    const int64_t q = i / x.n, e = i % x.n;
+    out[i] = group_entry_score<KP, F8>(x, e, x.qpre32 + q * KP);
+}
+
 static int g_num_sms = 0;
 
 static int num_sms() {
@@ -532,13 +658,18 @@ static int dense_smem() {
     return (int)C::kSmem < kMinDenseSmem ? kMinDenseSmem : (int)C::kSmem;
 }
 
+template <int KP, int PHASE, bool F8>
+static cudaError_t set_attr1() {
+    return cudaFuncSetAttribute(k_dense_scan<KP, PHASE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                dense_smem<KP, PHASE, F8>());
+}
+
 template <int KP, bool F8>
 static cudaError_t set_attr2() {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_scan<KP, 1, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         dense_smem<KP, 1, F8>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dense_scan<KP, 2, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 dense_smem<KP, 2, F8>());
+    cudaError_t e = set_attr1<KP, 1, F8>();
+    if (e == cudaSuccess) e = set_attr1<KP, 2, F8>();
+    if (e == cudaSuccess) e = set_attr1<KP, 3, F8>();
+    if (e == cudaSuccess) e = set_attr1<KP, 4, F8>();
     return e;
 }
 
@@ -563,11 +694,34 @@ template <int KP, bool F8>
 static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStream_t st) {
     cudaError_t e = dense_init();
     if (e != cudaSuccess) return e;
-    if (phase == 1)
-        k_dense_scan<KP, 1, F8><<<grid, kDenseThreads, dense_smem<KP, 1, F8>(), st>>>(p);
-    else
-        k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p);
+    switch (phase) {
+        case 1: k_dense_scan<KP, 1, F8><<<grid, kDenseThreads, dense_smem<KP, 1, F8>(), st>>>(p); break;
+        case 2: k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p); break;
+        case 3: k_dense_scan<KP, 3, F8><<<grid, kDenseThreads, dense_smem<KP, 3, F8>(), st>>>(p); break;
+        case 4: k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+template <int KP>
+static cudaError_t launch_kp_any(bool f8, const DenseParams &p, int phase, int grid, cudaStream_t st) {
+    return f8 ? launch_kp<KP, true>(p, phase, grid, st) : launch_kp<KP, false>(p, phase, grid, st);
+}
+
+static cudaError_t launch_dense_kernel(int kp, bool f8, const DenseParams &p, int phase, int grid, cudaStream_t st) {
+    switch (kp) {
+        case 16: return launch_kp_any<16>(f8, p, phase, grid, st);
+        case 32: return launch_kp_any<32>(f8, p, phase, grid, st);
+        case 64: return launch_kp_any<64>(f8, p, phase, grid, st);
+    }
+    return cudaErrorNotSupported;
+}
+
+// Words of the group map the current search may use: what the workspace holds, or
+// less when the search set a scratch limit (hn_search_opts.scratch_limit).
+static int64_t map_cap(const Workspace &ws) {
+    return ws.gbits_limit > 0 ? std::min(ws.gbits_limit, ws.gbits_cap) : ws.gbits_cap;
 }
 
 // Query tiles of the dense Phase-2 pass that starts at tile qt0: as many as fit the group
@@ -582,14 +736,33 @@ static int64_t gbits_words(int64_t n_tiles, int64_t n_qt, int G, int upc) {
     return chunks * 2 * ((tpc + 15) / 16) * n_qt * kDQ;
 }
 
-// Bitmap words the workspace holds for nq queries: the whole batch up to kGbitsMaxWords
-// (4 GiB; larger batches run Phase 2 in passes over query tiles), but at least one tile's.
-int64_t dense_gbits_words(const Index &ix, int64_t nq) {
-    constexpr int64_t kGbitsMaxWords = (int64_t)1 << 30;
+// One-pass form: the chunking is that of the whole batch (so every pass writes the same
+// candidate slots), and a query tile's codes take chunks * 2 * ceil(tpc / 2) * 256 words.
+static int64_t onepass_tile_words(const Index &ix, int64_t n_qt_all, int64_t *tpc, int64_t *chunks) {
+    dense_chunking(ix.n_tiles * (kTileE / kDE), n_qt_all, num_sms(), ix.units_per_cta, tpc, chunks);
+    return *chunks * 2 * ((*tpc + 1) / 2) * kDQ;
+}
+
+// Group-map words the workspace holds for nq queries: the whole batch up to 4 GiB (two-pass
+// bits) or 16 GiB (one-pass codes), larger batches taking the scan in passes over query
+// tiles; at most limit_bytes when that is > 0; always at least one query tile's.
+int64_t dense_gbits_words(const Index &ix, int64_t nq, bool onepass, int64_t limit_bytes) {
     const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
-    const int64_t all = gbits_words(n_tiles, (nq + kDQ - 1) / kDQ, num_sms(), ix.units_per_cta);
-    const int64_t one = gbits_words(n_tiles, 1, num_sms(), ix.units_per_cta);
-    return std::max(std::min(all, kGbitsMaxWords), one);
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
+    int64_t all, one, max_words;
+    if (onepass) {
+        int64_t tpc = 0, chunks = 0;
+        one = onepass_tile_words(ix, n_qt, &tpc, &chunks);
+        all = one * n_qt;
+        max_words = (int64_t)1 << 32;
+    } else {
+        all = gbits_words(n_tiles, n_qt, num_sms(), ix.units_per_cta);
+        one = gbits_words(n_tiles, 1, num_sms(), ix.units_per_cta);
+        max_words = (int64_t)1 << 30;
+    }
+    int64_t w = std::min(all, max_words);
+    if (limit_bytes > 0) w = std::min(w, limit_bytes / 4);
+    return std::max(w, one);
 }
 
 static int64_t phase2_pass_tiles(int64_t n_tiles, int64_t n_qt, int64_t qt0, int G, int upc, int64_t cap) {
@@ -598,12 +771,20 @@ static int64_t phase2_pass_tiles(int64_t n_tiles, int64_t n_qt, int64_t qt0, int
     return gbits_words(n_tiles, nqt, G, upc) > cap ? 0 : nqt;
 }
 
-// Kernel launches of one dense Phase 2 (a scan and an extraction per pass).
-int64_t dense_phase2_launches(const Index &ix, int64_t nq) {
+// Kernel launches of the dense scan steps after query preparation: two-pass, one per
+// Phase-1 scan plus a scan and an extraction per Phase-2 pass (the threshold kernel is
+// counted by the caller); one-pass, a scan, a threshold and an extraction per pass.
+int64_t dense_phase2_launches(const Index &ix, int64_t nq, bool onepass) {
     const int64_t n_qt = (nq + kDQ - 1) / kDQ, n_tiles = ix.n_tiles * (kTileE / kDE);
+    const int64_t cap = map_cap(ix.ws);
+    if (onepass) {
+        int64_t tpc = 0, chunks = 0;
+        const int64_t per = std::max<int64_t>(1, cap / onepass_tile_words(ix, n_qt, &tpc, &chunks));
+        return 3 * ((n_qt + per - 1) / per);
+    }
     int64_t launches = 0;
     for (int64_t qt0 = 0; qt0 < n_qt;) {
-        const int64_t nqt = phase2_pass_tiles(n_tiles, n_qt, qt0, num_sms(), ix.units_per_cta, ix.ws.gbits_cap);
+        const int64_t nqt = phase2_pass_tiles(n_tiles, n_qt, qt0, num_sms(), ix.units_per_cta, cap);
         if (nqt == 0) break;
         launches += 2;
         qt0 += nqt;
@@ -612,27 +793,70 @@ int64_t dense_phase2_launches(const Index &ix, int64_t nq) {
 }
 
 template <int KP, bool F8>
-static cudaError_t launch_extract(const ExtractParams &x, cudaStream_t st) {
+static cudaError_t launch_extract(const ExtractParams &x, bool codes, cudaStream_t st) {
     if (x.chunks > 65535) return cudaErrorInvalidConfiguration;
-    k_dense_extract<KP, F8><<<dim3((unsigned)(x.q_pad / 256), (unsigned)x.chunks), 256, 0, st>>>(x);
+    const dim3 grid((unsigned)(x.q_pad / 256), (unsigned)x.chunks);
+    if (codes)
+        k_dense_extract_codes<KP, F8><<<grid, 256, 0, st>>>(x);
+    else
+        k_dense_extract<KP, F8><<<grid, 256, 0, st>>>(x);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
-    if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
+static cudaError_t launch_extract_any(int kp, bool f8, const ExtractParams &x, bool codes, cudaStream_t st) {
+    switch (kp) {
+        case 16: return f8 ? launch_extract<16, true>(x, codes, st) : launch_extract<16, false>(x, codes, st);
+        case 32: return f8 ? launch_extract<32, true>(x, codes, st) : launch_extract<32, false>(x, codes, st);
+        case 64: return f8 ? launch_extract<64, true>(x, codes, st) : launch_extract<64, false>(x, codes, st);
+    }
+    return cudaErrorNotSupported;
+}
+
+// Fields shared by every dense launch of index ix (PHASE-specific fields left zero).
+static DenseParams dense_base(const Index &ix, int phase) {
     const Workspace &ws = ix.ws;
-    DenseParams p{};
     const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
-    // FP8: one tile array for both phases; the query operands differ (qpre16h: Phase-1 e4m3 of 16 q,
-    // qpre16: Phase-2 hi/lo e4m3 of 256 q)
+    DenseParams p{};
+    // FP8: one tile array for every phase; the query operands differ (qpre16h: Phase-1 e4m3 of
+    // 16 q, qpre16: the hi/lo e4m3 of 256 q of the other phases)
     p.pre = f8 ? (const void *)ix.pre8 : phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
     p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
     p.n = ix.n;
     p.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
     p.status = ws.status;
+    p.wait_ns = ws.wait_ns ? ws.wait_ns : kWaitLimitNs;
+    p.code_inv = ix.code_inv;
+    p.code_base = code_base();
+    return p;
+}
+
+static ExtractParams extract_base(const Index &ix, int64_t q0, int64_t nq_pass, int64_t nqt) {
+    const Workspace &ws = ix.ws;
+    ExtractParams x{};
+    x.pre = ix.prefix == HN_PREFIX_FP8_E4M3 ? (const void *)ix.pre8 : (const void *)ix.pre16;
+    x.qpre32 = ws.qpre32 + q0 * ix.k_pad4;
+    x.gbits = ws.gbits;
+    x.n = ix.n;
+    x.n_tiles = ix.n_tiles * (kTileE / kDE);
+    x.nq = nq_pass;
+    x.q_pad = nqt * kDQ;
+    x.tau = ws.tau + q0;
+    x.bucket = ws.bucket + q0 * ws.bucket_cap;
+    x.count = ws.count + q0;
+    x.cap = ws.bucket_cap;
+    x.code_inv = ix.code_inv;
+    x.code_base = code_base();
+    return x;
+}
+
+cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
+    if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
+    const Workspace &ws = ix.ws;
+    DenseParams p = dense_base(ix, phase);
     const int G = num_sms();
     const int64_t n_qt = (nq + kDQ - 1) / kDQ;
     const int kp = ix.k_pad16;
+    const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
     if (phase == 1) {
         int64_t chunks = 0;
         p.nq = nq;
@@ -641,18 +865,13 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
         p.n_units = p.n_qt * chunks;
         p.tau = ws.tau;
         p.cand = ws.cand;
-        const int grid = (int)min64(G, p.n_units);
-        switch (kp) {
-            case 16: return f8 ? launch_kp<16, true>(p, 1, grid, st) : launch_kp<16, false>(p, 1, grid, st);
-            case 32: return f8 ? launch_kp<32, true>(p, 1, grid, st) : launch_kp<32, false>(p, 1, grid, st);
-            case 64: return f8 ? launch_kp<64, true>(p, 1, grid, st) : launch_kp<64, false>(p, 1, grid, st);
-        }
-        return cudaErrorNotSupported;
+        return launch_dense_kernel(kp, f8, p, 1, (int)min64(G, p.n_units), st);
     }
     // Phase 2: the tensor-core scan marks the passing 32-entry groups, k_dense_extract turns
     // them into survivors; passes over query tiles keep the bitmap within the workspace
+    const int64_t cap = map_cap(ws);
     for (int64_t qt0 = 0; qt0 < n_qt;) {
-        const int64_t nqt = phase2_pass_tiles(p.n_tiles, n_qt, qt0, G, ix.units_per_cta, ws.gbits_cap);
+        const int64_t nqt = phase2_pass_tiles(p.n_tiles, n_qt, qt0, G, ix.units_per_cta, cap);
         if (nqt == 0) return cudaErrorInvalidValue;  // prepare_search sizes the bitmap for one tile at least
         const int64_t q0 = qt0 * kDQ;
         qt0 += nqt;
@@ -666,37 +885,91 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
         pp.tau = ws.tau + q0;
         pp.gbits = ws.gbits;
         pp.words = (pp.tiles_per_chunk + 15) / 16;
-        const int grid = (int)min64(G, pp.n_units);
-        ExtractParams x{};
-        x.pre = f8 ? (const void *)ix.pre8 : (const void *)ix.pre16;
-        x.qpre32 = ws.qpre32 + q0 * ix.k_pad4;
-        x.gbits = ws.gbits;
-        x.n = ix.n;
-        x.n_tiles = p.n_tiles;
-        x.nq = pp.nq;
-        x.q_pad = nqt * kDQ;
+        ExtractParams x = extract_base(ix, q0, pp.nq, nqt);
         x.tiles_per_chunk = pp.tiles_per_chunk;
         x.chunks = chunks;
         x.words = pp.words;
-        x.tau = ws.tau + q0;
-        x.bucket = ws.bucket + q0 * ws.bucket_cap;
-        x.count = ws.count + q0;
-        x.cap = ws.bucket_cap;
-        cudaError_t e = cudaErrorNotSupported;
-        switch (kp) {
-            case 16: e = f8 ? launch_kp<16, true>(pp, 2, grid, st) : launch_kp<16, false>(pp, 2, grid, st); break;
-            case 32: e = f8 ? launch_kp<32, true>(pp, 2, grid, st) : launch_kp<32, false>(pp, 2, grid, st); break;
-            case 64: e = f8 ? launch_kp<64, true>(pp, 2, grid, st) : launch_kp<64, false>(pp, 2, grid, st); break;
-        }
-        if (e != cudaSuccess) return e;
-        switch (kp) {
-            case 16: e = f8 ? launch_extract<16, true>(x, st) : launch_extract<16, false>(x, st); break;
-            case 32: e = f8 ? launch_extract<32, true>(x, st) : launch_extract<32, false>(x, st); break;
-            case 64: e = f8 ? launch_extract<64, true>(x, st) : launch_extract<64, false>(x, st); break;
-        }
+        cudaError_t e = launch_dense_kernel(kp, f8, pp, 2, (int)min64(G, pp.n_units), st);
+        if (e == cudaSuccess) e = launch_extract_any(kp, f8, x, false, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// One-pass dense search steps, per pass over query tiles: the PHASE-4 scan (group codes and
+// threshold candidates), the threshold from the candidates, and the code-map extraction.
+// With `ev` (3 events), the first pass records ev[0] after its scan, ev[1] after its
+// threshold and ev[2] after the last pass's extraction.
+cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, int kk, bool keep_best,
+                                 cudaStream_t st, cudaEvent_t *ev) {
+    if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
+    const Workspace &ws = ix.ws;
+    const int G = num_sms();
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
+    const int kp = ix.k_pad16;
+    const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
+    int64_t tpc = 0, chunks = 0;
+    const int64_t tile_words = onepass_tile_words(ix, n_qt, &tpc, &chunks);
+    const int64_t per = map_cap(ws) / tile_words;  // query tiles per pass
+    if (per < 1) return cudaErrorInvalidValue;      // prepare_search sizes the map for one tile at least
+    const int S = (int)(2 * chunks);                // candidate slots per query
+    if (S > ws.cand_slots) return cudaErrorInvalidValue;
+    DenseParams p = dense_base(ix, 4);
+    p.tiles_per_chunk = tpc;
+    p.words = (tpc + 1) / 2;
+    p.gbits = ws.gbits;
+    for (int64_t qt0 = 0; qt0 < n_qt;) {
+        const int64_t nqt = std::min(per, n_qt - qt0);
+        const int64_t q0 = qt0 * kDQ;
+        const bool first = qt0 == 0;
+        qt0 += nqt;
+        DenseParams pp = p;
+        pp.qpre = static_cast<const char *>(p.qpre) + q0 * kp * 2;
+        pp.nq = min64(nq - q0, nqt * kDQ);
+        pp.n_qt = nqt;
+        pp.n_units = nqt * chunks;
+        pp.cand = ws.cand + q0 * S;
+        cudaError_t e = launch_dense_kernel(kp, f8, pp, 4, (int)min64(G, pp.n_units), st);
+        if (e == cudaSuccess && ev && first) e = cudaEventRecord(ev[0], st);
+        if (e == cudaSuccess) e = launch_seed_threshold_at(ix, q, q0, pp.nq, S, 32, kk, keep_best, st);
+        if (e == cudaSuccess && ev && first) e = cudaEventRecord(ev[1], st);
+        ExtractParams x = extract_base(ix, q0, pp.nq, nqt);
+        x.tiles_per_chunk = tpc;
+        x.chunks = chunks;
+        x.words = pp.words;
+        if (e == cudaSuccess) e = launch_extract_any(kp, f8, x, true, st);
+        if (e != cudaSuccess) return e;
+    }
+    return ev ? cudaEventRecord(ev[2], st) : cudaSuccess;
+}
+
+// Verification: every prefix score of nq prepared queries (ws.qpre*) against the index,
+// [nq][n] FP32, from the tensor-core scan's Phase-2 arithmetic (path 0) or the CUDA-core
+// FMA chain of the survivor extraction (path 1).
+cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *out, cudaStream_t st) {
+    if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
+    const int kp = ix.k_pad16;
+    const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
+    if (path == 0) {
+        DenseParams p = dense_base(ix, 3);
+        int64_t chunks = 0;
+        p.nq = nq;
+        p.n_qt = (nq + kDQ - 1) / kDQ;
+        dense_chunking(p.n_tiles, p.n_qt, num_sms(), ix.units_per_cta, &p.tiles_per_chunk, &chunks);
+        p.n_units = p.n_qt * chunks;
+        p.dump = out;
+        return launch_dense_kernel(kp, f8, p, 3, (int)min64(num_sms(), p.n_units), st);
+    }
+    ExtractParams x = extract_base(ix, 0, nq, (nq + kDQ - 1) / kDQ);
+    const int64_t total = nq * ix.n;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    switch (kp) {
+        case 16: f8 ? k_fma_scores<16, true><<<blocks, 256, 0, st>>>(x, out) : k_fma_scores<16, false><<<blocks, 256, 0, st>>>(x, out); break;
+        case 32: f8 ? k_fma_scores<32, true><<<blocks, 256, 0, st>>>(x, out) : k_fma_scores<32, false><<<blocks, 256, 0, st>>>(x, out); break;
+        case 64: f8 ? k_fma_scores<64, true><<<blocks, 256, 0, st>>>(x, out) : k_fma_scores<64, false><<<blocks, 256, 0, st>>>(x, out); break;
+        default: return cudaErrorNotSupported;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace hn

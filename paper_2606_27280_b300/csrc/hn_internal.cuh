@@ -63,8 +63,12 @@ struct Workspace {
     int32_t *count = nullptr;          // [q_cap] survivor counts (may exceed bucket_cap)
     unsigned long long *key1 = nullptr;// [q_cap] Phase-1 best (score, index) key (stream scan)
     unsigned long long *cand = nullptr;// [q_cap][cand_slots] Phase-1 per-chunk bests (dense scan)
-    uint32_t *gbits = nullptr;         // dense Phase 2: bits of the 16-entry groups that reached tau_q
+    uint32_t *gbits = nullptr;         // dense scan group map: two-pass form, one bit per 32-entry group
+                                       //   that reached tau_q; one-pass form, one 8-bit code of the group's
+                                       //   largest score per 32-entry group
     int64_t gbits_cap = 0;             // allocated words of gbits
+    int64_t gbits_limit = 0;           // words the current search may use (<= gbits_cap; 0 = all)
+    uint64_t wait_ns = 0;              // main-loop wait limit of the dense scan for the current search (0 = 2 s)
     int64_t cand_cap = 0;              // allocated length of cand
     int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
@@ -107,6 +111,7 @@ struct Index {
     uint64_t serial = 0;             // unique per built index (a freed index's address may be reused)
     int32_t dense_min_q = 1024;      // smallest batch the AUTO scan sends to the dense kernel (autotuned)
     int32_t units_per_cta = 32;      // dense work-unit granularity (autotuned)
+    float code_inv = 1.f;            // one-pass dense scan: inv of the group code (127 / bound on |score|)
     int32_t n_blocks = 0;            // block partition for the learned proposal (0 = none)
     int32_t *block_ids = nullptr;    // [n] entry ids in block order
     int32_t *block_of = nullptr;     // [n] block of each entry
@@ -136,21 +141,51 @@ __host__ __device__ inline int64_t pre16_offset(int64_t e, int c, int k_pad16) {
 //   [128 x float  s_i / kF8QScale]      (scale of the Phase-2 tensor-core product)
 //   [128 x float  b_i = RU(qt * r_i)]   (r_i = |x_i,major - x~_i|: per-entry error term)
 //   [128 x half   s_i * 2^11]           (scale of the Phase-1 FP16 product)
+//   [4 x float4 (max_i s_i / kF8QScale, min_i s_i / kF8QScale, max_i b_i, 0)] over the
+//    real entries (i < n) of each 32-entry group: the one-pass scan bounds a group's
+//    largest score from its largest raw accumulator with them (zeros for a group
+//    holding padding rows only)
 constexpr int kF8Tile = 128;
 constexpr float kF8QScale = 256.f;   // Phase-2 query prefix scale (hi + lo e4m3 parts)
 constexpr float kF8QScale1 = 16.f;   // Phase-1 query prefix scale (FP16 accumulation stays finite)
 constexpr float kF8HScale = 2048.f;  // Phase-1 entry scale factor
-__host__ __device__ constexpr int64_t kF8TileBytes(int kp) { return (int64_t)kF8Tile * (kp + 10); }
+__host__ __device__ constexpr int64_t kF8TileBytes(int kp) { return (int64_t)kF8Tile * (kp + 10) + 64; }
 __host__ __device__ inline int64_t f8_scale_off(int kp) { return (int64_t)kF8Tile * kp; }
+__host__ __device__ inline int64_t f8_group_off(int kp) { return (int64_t)kF8Tile * (kp + 10); }
 // byte offset of (row r, byte column c) in a K-major UMMA tile whose rows hold `row_bytes` bytes
 __host__ __device__ inline int64_t umma8_offset(int64_t r, int c, int row_bytes) {
     return (r >> 3) * (int64_t)row_bytes * 8 + (int64_t)(c >> 4) * 128 + (r & 7) * 16 + (c & 15);
 }
 
+// ---------------------------------------------------------------- group-map codes
+// One-pass dense scan: the largest score g of every 32-entry group is kept as an
+// 8-bit code, and the survivor extraction, once tau_q is known, looks only at the
+// groups with code(g) >= code(tau_q).  Any non-decreasing code is exact for that
+// test (g >= tau  =>  code(g) >= code(tau)); this one is
+//   code(v) = clamp(RU(v * inv + base) - 2^23, 0, 255)
+// with inv = 127 / B and base = 2^23 + 128 (B bounds |g| for unit HN prefixes, so
+// scores map to 1..255 with a step of about B / 127).  The value RU(.) lies in
+// [2^23, 2^24) where binary32 steps by 1, so its bits minus those of 2^23 are the
+// integer code.  The scan side takes the cheaper clamp code_group: a score below
+// the range wraps round to 255 instead of 0, which can only flag more groups.
+constexpr uint32_t kCodeBits0 = 0x4B000000u;  // bits of 2^23
+__host__ __device__ inline float code_base() { return 8388608.f + 128.f; }
+__device__ __forceinline__ uint32_t code_group(float g, float inv, float base) {
+    const uint32_t b = __float_as_uint(__fmaf_ru(g, inv, base)) - kCodeBits0;
+    return b < 255u ? b : 255u;
+}
+__device__ __forceinline__ uint32_t code_threshold(float tau, float inv, float base) {
+    const float v = fminf(fmaxf(__fmaf_ru(tau, inv, base), 8388608.f), 8388608.f + 255.f);
+    return __float_as_uint(v) - kCodeBits0;
+}
+
 // search pipeline pieces (hn_api.cu), shared with the multi-batch path
 int pick_scan(const Index &ix, int64_t nq, int requested);
 // nn: neighbours per query (1: the 1-NN; 2..32: exact top-nn, outputs [nq][nn])
-hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn = 1);
+// seeded: the proposal gives the threshold (a dense Phase 2 then takes the two-pass bit scan);
+// scratch_limit: bytes of the dense group map this search may use (0 = the default cap)
+hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn = 1, bool seeded = false,
+                         int64_t scratch_limit = 0);
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                          int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn = 1,
                          float minor_scale = 1.f);
@@ -175,6 +210,15 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
 // keep_best (soft ANN mode): the best scored candidate is put into survivor slot 0
 cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, int kk, bool keep_best,
                                   cudaStream_t s);
+// The same for queries q0 .. q0 + nq - 1 of the batch, from S candidate keys per query naming
+// seg_entries-entry segments (cand laid out [query][S] from query 0 of the batch).
+cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0, int64_t nq, int S, int seg_entries,
+                                     int kk, bool keep_best, cudaStream_t s);
+// One-pass dense search steps (scan, threshold, extraction per pass; hn_dense.cu)
+cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, int kk, bool keep_best, cudaStream_t s,
+                                 cudaEvent_t *ev);
+// Verification: [nq][n] prefix scores of the prepared queries; path 0 tensor cores, 1 CUDA-core FMA chain
+cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *out, cudaStream_t s);
 // Exact top-kk of every query from its Phase-2 survivors (1 <= kk <= 32): out_idx/out_sim [nq][kk].
 cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
                                 double *out_sim, cudaStream_t s);
@@ -198,9 +242,10 @@ cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);
 int32_t proposal_blocks(const hn_proposal *p);
 int32_t proposal_k(const hn_proposal *p);
 int64_t dense_cand_slots(const Index &ix, int64_t nq);
-// uint32 words of the dense Phase-2 group bitmap the workspace holds for nq queries
-int64_t dense_gbits_words(const Index &ix, int64_t nq);
-// kernel launches of one dense Phase 2 for nq queries (with the workspace as sized)
-int64_t dense_phase2_launches(const Index &ix, int64_t nq);
+// uint32 words of the dense group map the workspace holds for nq queries (onepass: codes, else
+// the two-pass Phase-2 bits), at most limit_bytes when > 0, at least one query tile's
+int64_t dense_gbits_words(const Index &ix, int64_t nq, bool onepass, int64_t limit_bytes);
+// kernel launches of the dense steps after Phase 1 / the threshold (see hn_dense.cu)
+int64_t dense_phase2_launches(const Index &ix, int64_t nq, bool onepass);
 
 }  // namespace hn

@@ -86,8 +86,14 @@ __device__ inline float4 bf16_round4(float4 v) {
 
 // ------------------------------------------------------------------ FP8 e4m3
 // Per-entry scale of the FP8 prefix: the smallest power of two s with
-// amax / s <= 448 (the largest finite e4m3 value), so the largest component
-// uses the top binade of e4m3 and x~ = s * x^ is exact.  amax = 0 (padding) -> 1.
+// amax / s <= 448 (the largest finite e4m3 value), x~ = s * x^ exact.  The index
+// passes the entry's prefix norm (rounded up) as amax, which bounds every
+// component, so no code saturates; HN entries all have prefix norm sqrt(1 - alpha),
+// so they share one scale, and the one-pass dense scan can bound a group's largest
+// score from its largest raw accumulator without loss.  Relative to a scale from the
+// largest component this moves codes down by at most two binades, where e4m3 keeps
+// its relative precision (the per-entry error term b_i holds the actual residual).
+// amax = 0 (padding) -> 1.
 __device__ inline float f8_entry_scale(float amax) {
     if (!(amax > 0.f)) return 1.f;
     int ex;
@@ -168,7 +174,9 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
         float sc = 1.f;
         uint32_t f8 = 0;  // this lane's 4 e4m3 codes
         if (prefix == HN_PREFIX_FP8_E4M3) {
-            sc = f8_entry_scale(warp_max(fmaxf(fmaxf(fabsf(pv[0]), fabsf(pv[1])), fmaxf(fabsf(pv[2]), fabsf(pv[3])))));
+            const double pn2 = warp_sum((double)pv[0] * pv[0] + (double)pv[1] * pv[1] + (double)pv[2] * pv[2] +
+                                        (double)pv[3] * pv[3]);
+            sc = f8_entry_scale(sqrt_up(pn2));
             float dq[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -259,6 +267,29 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
     }
 }
 
+// Per 32-entry group of an FP8 tile: (max s_i, min s_i) / kF8QScale and max b_i over the
+// group's real entries (i < n).  A score u_i = RN(acc_i * s_i / 256 + b_i) of the group is
+// at most max(RU(A * smax + bmax), RU(A * smin + bmax)) with A = max_i acc_i: the product
+// with a positive scale is increasing in acc_i, and linear in the scale, so its largest
+// value over the group's scales is at an end of their range.  One thread per group.
+__global__ void __launch_bounds__(256) k_f8_group_bounds(uint8_t *__restrict__ pre8, int64_t n, int64_t n_groups,
+                                                         int kp) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_groups) return;
+    uint8_t *tile8 = pre8 + (g >> 2) * kF8TileBytes(kp);
+    const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(kp));
+    const int r0 = (int)(g & 3) * 32;
+    float smax = 0.f, smin = INFINITY, bmax = 0.f;
+    for (int r = 0; r < 32; ++r) {
+        if ((g >> 2) * kF8Tile + r0 + r >= n) break;
+        smax = fmaxf(smax, sc2[r0 + r]);
+        smin = fminf(smin, sc2[r0 + r]);
+        bmax = fmaxf(bmax, sc2[kF8Tile + r0 + r]);
+    }
+    if (smin == INFINITY) smin = 0.f;
+    reinterpret_cast<float4 *>(tile8 + f8_group_off(kp))[g & 3] = make_float4(smax, smin, bmax, 0.f);
+}
+
 cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
     const int64_t n_pad = ix.n_tiles * kTileE;
     int64_t blocks = (n_pad * 32 + 255) / 256;
@@ -272,6 +303,12 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
                                              ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.pre8, ix.prei8, ix.qt, ix.mx,
                                              ix.dev_max,
                                              ix.ws.status);
+    if (ix.prefix == HN_PREFIX_FP8_E4M3) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t n_groups = n_pad / 32;
+        k_f8_group_bounds<<<(unsigned)((n_groups + 255) / 256), 256, 0, st>>>(ix.pre8, ix.n, n_groups, ix.k_pad16);
+    }
     return cudaGetLastError();
 }
 

@@ -595,6 +595,18 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     return cudaGetLastError();
 }
 
+cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0, int64_t nq, int S, int seg_entries,
+                                     int kk, bool keep_best, cudaStream_t st) {
+    const Workspace &ws = ix.ws;
+    const int64_t blocks = (nq * 32 + 255) / 256;
+    const int cap = ws.bucket_cap;
+    k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q + q0 * kD, nq, ix.n, ws.cand + q0 * S, S, seg_entries,
+                                                       ix.pre16, ix.k_pad4, ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
+                                                       ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.count + q0,
+                                                       ws.bucket + q0 * cap, cap, keep_best ? 1 : 0);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ rescore
 // One warp per query.  For every survivor i: FP32 128-dim score (lane l owns
 // dims 4l..4l+3, then a butterfly sum), error <= eps_r = gamma_128 |q| max|x|

@@ -18,7 +18,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "li
 OK, ERR_INVALID_ARG, ERR_NOT_NORMALIZED, ERR_ZERO_NORM, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_OVERFLOW, \
     ERR_UNSUPPORTED = range(9)
 PREFIX_F32, PREFIX_BF16, PREFIX_FP8, PREFIX_I8 = 0, 1, 2, 3
-SCAN_AUTO, SCAN_STREAM, SCAN_DENSE = 0, 1, 2
+SCAN_AUTO, SCAN_STREAM, SCAN_DENSE, SCAN_DENSE_TWO_PASS = 0, 1, 2, 3
 D = 128
 
 _STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_INVALID_ARG", 2: "HN_ERR_NOT_NORMALIZED", 3: "HN_ERR_ZERO_NORM",
@@ -34,7 +34,8 @@ class IndexOpts(ctypes.Structure):
 class SearchOpts(ctypes.Structure):
     _fields_ = [("scan", ctypes.c_int32), ("bucket_cap", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("soft", ctypes.c_int32),
-                ("beta", ctypes.c_float)]
+                ("beta", ctypes.c_float), ("scratch_limit", ctypes.c_int64), ("wait_limit_ns", ctypes.c_uint64),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -52,7 +53,7 @@ class ProposalInfo(ctypes.Structure):
 class SearchStats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("n_entries", ctypes.c_int64), ("survivors", ctypes.c_int64),
                 ("max_survivors", ctypes.c_int64), ("fp64_rescored", ctypes.c_int64), ("reruns", ctypes.c_int32),
-                ("scan", ctypes.c_int32), ("kernels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("scan", ctypes.c_int32), ("kernels", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("ms_prep", ctypes.c_float), ("ms_phase1", ctypes.c_float), ("ms_threshold", ctypes.c_float),
                 ("ms_phase2", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float)]
 
@@ -106,6 +107,7 @@ SIGNATURES = {
     "hn_search_batch": ([_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_search_topk": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "hn_prefix_scores": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
     "hn_index_blocks": ([_vp, _vp, _vp, _vp, _vp], _i32),
     "hn_search_multi": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "hn_autotune": ([_vp, _vp, _i32, _vp, _vp], _i32),
@@ -246,11 +248,13 @@ class Index:
                timing: bool = False,
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
                proposal: "Proposal | None" = None, seed_topk: int = 0, beta: float | None = None,
-               stream=None) -> SearchResult:
+               scratch_limit: int = 0, wait_limit_ns: int = 0, stream=None) -> SearchResult:
         """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
         `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped.
         `beta` (0 <= beta <= alpha) selects the soft ANN mode: alpha in the skip test becomes
-        beta (beta = alpha is exact)."""
+        beta (beta = alpha is exact).  `scratch_limit` caps the bytes of the dense scan's group
+        map (larger batches run in passes); `wait_limit_ns` sets the dense scan's device-side
+        wait limit (0 = 2 s)."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         if out_idx is None:
@@ -259,7 +263,8 @@ class Index:
             out_sim = torch.empty(nq, dtype=torch.float64, device=q.device)
         opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), timing=int(bool(timing)),
                           seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None,
-                          soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0)
+                          soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0,
+                          scratch_limit=int(scratch_limit), wait_limit_ns=int(wait_limit_ns))
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),
                                     out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
@@ -280,6 +285,17 @@ class Index:
                                    out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
                                    _stream(stream)), "hn_search_topk")
         return SearchResult(out_idx, out_sim, st.as_dict() if st is not None else None)
+
+    def prefix_scores(self, q: torch.Tensor, path: int, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """(scores [nq, n] float32, slack [nq] float32): every prefix score as the search computes
+        it (path 0: tensor-core scan, 1: CUDA-core FMA chain) and the slack E_q of its bound test."""
+        q = _dev_f32(q, "q")
+        nq = q.shape[0]
+        scores = torch.empty((nq, self.n), dtype=torch.float32, device=q.device)
+        slack = torch.empty(nq, dtype=torch.float32, device=q.device)
+        _check(_lib.hn_prefix_scores(self._h, q.data_ptr(), nq, int(path), scores.data_ptr(), slack.data_ptr(),
+                                     _stream(stream)), "hn_prefix_scores")
+        return scores, slack
 
     def bruteforce(self, q: torch.Tensor, stream=None) -> SearchResult:
         """FP32 128-dim brute force (baseline; ranks by FP32 scores)."""

@@ -40,8 +40,9 @@ def test_library_exports_every_declared_symbol(hn):
 def test_struct_sizes_match_header(hn):
     # sizes implied by the field lists in include/hn.h (x86-64 ABI)
     assert ctypes.sizeof(hn.IndexOpts) == 32
-    assert ctypes.sizeof(hn.SearchOpts) == 32
+    assert ctypes.sizeof(hn.SearchOpts) == 64
     assert ctypes.sizeof(hn.SearchStats) == 80
+    assert hn.SearchStats.passes.offset == 52
     assert ctypes.sizeof(hn.IndexInfo) == 64
     assert ctypes.sizeof(hn.TrainOpts) == 40
     assert ctypes.sizeof(hn.ProposalInfo) == 40
@@ -60,7 +61,7 @@ def test_binding_constants_match_header_enums(hn):
     e = header_enums()
     pairs = {"HN_PREFIX_F32": hn.PREFIX_F32, "HN_PREFIX_BF16": hn.PREFIX_BF16, "HN_PREFIX_FP8_E4M3": hn.PREFIX_FP8,
              "HN_PREFIX_I8": hn.PREFIX_I8, "HN_SCAN_AUTO": hn.SCAN_AUTO, "HN_SCAN_STREAM": hn.SCAN_STREAM,
-             "HN_SCAN_DENSE": hn.SCAN_DENSE}
+             "HN_SCAN_DENSE": hn.SCAN_DENSE, "HN_SCAN_DENSE_TWO_PASS": hn.SCAN_DENSE_TWO_PASS}
     for name, value in pairs.items():
         assert e[name] == value, name
     for code, name in hn._STATUS_NAMES.items():
@@ -120,6 +121,7 @@ def test_search_host_checks(hn):
     assert hn._lib.hn_bruteforce(None, None, 4, None, None, None) == hn.ERR_INVALID_ARG
     assert hn._lib.hn_index_destroy(None) == hn.OK
     assert hn._lib.hn_index_get_info(None, None) == hn.ERR_INVALID_ARG
+    assert hn._lib.hn_prefix_scores(None, None, 4, 0, None, None, None) == hn.ERR_INVALID_ARG
 
 
 def test_multi_and_autotune_host_checks(hn):

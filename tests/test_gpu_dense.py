@@ -1,4 +1,6 @@
-"""GPU parity of the tcgen05 dense prefix scan (BF16 prefix) against the oracle."""
+"""GPU parity of the tcgen05 dense prefix scan (BF16 prefix) against the oracle, in both
+forms: one pass (group codes, HN_SCAN_DENSE) and Algorithm 1's two passes
+(HN_SCAN_DENSE_TWO_PASS)."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +11,8 @@ from tests._gpu_util import assert_parity, oracle_case, to_dev
 
 pytestmark = pytest.mark.gpu
 
-DENSE, STREAM = 2, 1
+DENSE, STREAM, DENSE2 = 2, 1, 3
+FORMS = pytest.mark.parametrize("form", [DENSE, DENSE2])
 
 
 @pytest.fixture(scope="module")
@@ -18,29 +21,32 @@ def hn(gpu):
     return mod
 
 
-def test_dense_one_tile(hn):
+@FORMS
+def test_dense_one_tile(hn, form):
     """One query tile, one entry tile: the smallest launch."""
     w, db, q, o_idx, o_sim = oracle_case(256, 128, 40, 21, 16, 1 / 8)
     with hn.Index(to_dev(db), 16, 1 / 8, prefix=1) as ix:
-        r = ix.search(to_dev(q), scan=DENSE, stats=True)
-        assert r.stats["scan"] == DENSE
+        r = ix.search(to_dev(q), scan=form, stats=True)
+        assert r.stats["scan"] == form
         assert_parity(r.idx, r.sim, o_idx, o_sim)
 
 
 @pytest.mark.parametrize("n,nq", [(1, 1), (2, 3), (255, 1), (257, 129), (1000, 200), (4097, 300), (20011, 1000)])
-def test_dense_ragged_sizes(hn, n, nq):
+@FORMS
+def test_dense_ragged_sizes(hn, n, nq, form):
     w, db, q, o_idx, o_sim = oracle_case(n, nq, max(1, n // 5), 22, 16, 1 / 8)
     with hn.Index(to_dev(db), 16, 1 / 8, prefix=1) as ix:
-        r = ix.search(to_dev(q), scan=DENSE)
+        r = ix.search(to_dev(q), scan=form)
         assert_parity(r.idx, r.sim, o_idx, o_sim)
 
 
 @pytest.mark.parametrize("k,alpha", [(8, 1 / 32), (16, 0.0), (16, 0.25), (24, 1 / 16), (32, 1 / 8), (64, 1 / 8),
                                      (3, 0.5)])
-def test_dense_k_alpha(hn, k, alpha):
+@FORMS
+def test_dense_k_alpha(hn, k, alpha, form):
     w, db, q, o_idx, o_sim = oracle_case(9001, 700, 1500, 23, k, alpha)
     with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
-        r = ix.search(to_dev(q), scan=DENSE)
+        r = ix.search(to_dev(q), scan=form)
         assert_parity(r.idx, r.sim, o_idx, o_sim)
 
 
@@ -53,7 +59,8 @@ def test_dense_config0(hn):
         assert r.stats["survivors"] >= c["nq"]
 
 
-def test_dense_ties_and_duplicates(hn):
+@FORMS
+def test_dense_ties_and_duplicates(hn, form):
     k, alpha = 16, 1 / 8
     w = hn_synth.make_workload(3000, 256, 300, seed=31)
     db = oracle.normalize(w.db_raw, k, alpha)
@@ -63,7 +70,7 @@ def test_dense_ties_and_duplicates(hn):
     q[0], q[130], q[255] = db[10], db[255], db[0]
     o_idx, o_sim = oracle.search(db, q)
     with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
-        r = ix.search(to_dev(q), scan=DENSE)
+        r = ix.search(to_dev(q), scan=form)
         assert_parity(r.idx, r.sim, o_idx, o_sim)
 
 
@@ -73,16 +80,39 @@ def test_dense_equals_stream_and_repeats(hn):
     with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
         qd = to_dev(q)
         ref = ix.search(qd, scan=STREAM)
-        outs = [ix.search(qd, scan=DENSE) for _ in range(3)]
+        outs = [ix.search(qd, scan=DENSE) for _ in range(3)] + [ix.search(qd, scan=DENSE2)]
         for r in outs:
             assert torch.equal(r.idx, ref.idx) and torch.equal(r.sim, ref.sim)
         assert_parity(outs[0].idx, outs[0].sim, o_idx, o_sim)
 
 
-def test_dense_overflow_rerun(hn):
+@FORMS
+def test_dense_overflow_rerun(hn, form):
     k, alpha = 8, 1 / 8
     w, db, q, o_idx, o_sim = oracle_case(20000, 500, 4000, 5, k, alpha, 0.3, 0.2)
     with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
-        r = ix.search(to_dev(q), scan=DENSE, bucket_cap=16, stats=True)
+        r = ix.search(to_dev(q), scan=form, bucket_cap=16, stats=True)
         assert r.stats["reruns"] >= 1
         assert_parity(r.idx, r.sim, o_idx, o_sim)
+
+
+@pytest.mark.parametrize("prefix", [1, 2])
+@pytest.mark.parametrize("limit", [1, 1 << 20])
+@FORMS
+def test_dense_passes_over_query_tiles(hn, prefix, limit, form):
+    """A scratch limit below the group map's size runs the dense scan in passes over
+    256-query tiles (11 tiles here, the last one holding 40 queries): limit 1 takes one
+    tile a pass, 1 MiB a few tiles a pass with a shorter last pass.  Same answers as
+    the oracle, and as one pass."""
+    k, alpha = 16, 1 / 8
+    w, db, q, o_idx, o_sim = oracle_case(20011, 2600, 4000, 25, k, alpha)
+    with hn.Index(to_dev(db), k, alpha, prefix=prefix) as ix:
+        qd = to_dev(q)
+        one = ix.search(qd, scan=form, stats=True)
+        assert one.stats["passes"] == 1
+        r = ix.search(qd, scan=form, stats=True, scratch_limit=limit)
+        assert r.stats["passes"] >= 3, r.stats
+        if limit == 1:
+            assert r.stats["passes"] == 11
+        assert_parity(r.idx, r.sim, o_idx, o_sim)
+        assert r.stats["survivors"] == one.stats["survivors"]

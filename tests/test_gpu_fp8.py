@@ -11,7 +11,7 @@ from tests._gpu_util import assert_parity, oracle_case, to_dev
 
 pytestmark = pytest.mark.gpu
 
-STREAM, DENSE = 1, 2
+STREAM, DENSE, DENSE2 = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +20,7 @@ def hn(gpu):
     return mod
 
 
-@pytest.mark.parametrize("scan", [STREAM, DENSE])
+@pytest.mark.parametrize("scan", [STREAM, DENSE, DENSE2])
 def test_fp8_config0(hn, scan):
     c = hn_synth.CONFIGS["c0"]
     w, db, q, o_idx, o_sim = oracle_case(c["n"], c["nq"], c["n_centres"], c["seed"], c["k"], c["alpha"])
@@ -31,7 +31,7 @@ def test_fp8_config0(hn, scan):
 
 
 @pytest.mark.parametrize("n,nq", [(1, 1), (2, 3), (127, 5), (129, 257), (4097, 300), (20011, 1000)])
-@pytest.mark.parametrize("scan", [STREAM, DENSE])
+@pytest.mark.parametrize("scan", [STREAM, DENSE, DENSE2])
 def test_fp8_ragged_sizes(hn, n, nq, scan):
     w, db, q, o_idx, o_sim = oracle_case(n, nq, max(1, n // 5), 41, 16, 1 / 8)
     with hn.Index(to_dev(db), 16, 1 / 8, prefix=hn.PREFIX_FP8) as ix:
@@ -41,7 +41,7 @@ def test_fp8_ragged_sizes(hn, n, nq, scan):
 
 @pytest.mark.parametrize("k,alpha", [(3, 0.5), (8, 1 / 32), (16, 0.0), (16, 0.25), (24, 1 / 16), (32, 1 / 8),
                                      (64, 1 / 8)])
-@pytest.mark.parametrize("scan", [STREAM, DENSE])
+@pytest.mark.parametrize("scan", [STREAM, DENSE, DENSE2])
 def test_fp8_k_alpha(hn, k, alpha, scan):
     w, db, q, o_idx, o_sim = oracle_case(9001, 700, 1500, 42, k, alpha)
     with hn.Index(to_dev(db), k, alpha, prefix=hn.PREFIX_FP8) as ix:
@@ -61,7 +61,7 @@ def test_fp8_ties_and_duplicates(hn):
     q[0], q[130], q[255] = db[10], db[127], db[0]
     o_idx, o_sim = oracle.search(db, q)
     with hn.Index(to_dev(db), k, alpha, prefix=hn.PREFIX_FP8) as ix:
-        for scan in (STREAM, DENSE):
+        for scan in (STREAM, DENSE, DENSE2):
             r = ix.search(to_dev(q), scan=scan)
             assert_parity(r.idx, r.sim, o_idx, o_sim)
 
@@ -78,7 +78,8 @@ def test_fp8_agrees_with_bf16_and_repeats(hn):
     with hn.Index(to_dev(db), k, alpha, prefix=hn.PREFIX_FP8) as ix:
         inf = ix.info()
         assert inf["prefix"] == hn.PREFIX_FP8 and 0 < inf["resid_norm_max"] < 0.12
-        runs = [ix.search(qd, scan=DENSE, stats=True) for _ in range(3)] + [ix.search(qd, scan=STREAM, stats=True)]
+        runs = [ix.search(qd, scan=DENSE, stats=True) for _ in range(3)] + [ix.search(qd, scan=STREAM, stats=True),
+                                                                            ix.search(qd, scan=DENSE2, stats=True)]
         for r in runs:
             assert torch.equal(r.idx, ref.idx) and torch.equal(r.sim, ref.sim)
         assert runs[0].stats["survivors"] >= ref.stats["survivors"]
@@ -89,7 +90,7 @@ def test_fp8_hard_data_and_overflow_rerun(hn):
     """Noisier data (far more survivors) with tiny survivor storage: re-runs, still exact."""
     k, alpha = 8, 1 / 8
     w, db, q, o_idx, o_sim = oracle_case(20000, 500, 4000, 5, k, alpha, 0.3, 0.2)
-    for scan in (STREAM, DENSE):   # a fresh index each: its survivor storage only grows
+    for scan in (STREAM, DENSE, DENSE2):   # a fresh index each: its survivor storage only grows
         with hn.Index(to_dev(db), k, alpha, prefix=hn.PREFIX_FP8) as ix:
             r = ix.search(to_dev(q), scan=scan, bucket_cap=2, stats=True)
             assert r.stats["max_survivors"] > 2 and r.stats["reruns"] >= 1, r.stats

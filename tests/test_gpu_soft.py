@@ -15,7 +15,7 @@ def hn(gpu):
     return mod
 
 
-@pytest.mark.parametrize("prefix,scan", [(0, 1), (1, 2), (2, 2)])
+@pytest.mark.parametrize("prefix,scan", [(0, 1), (1, 2), (2, 2), (1, 3), (2, 3)])
 def test_soft_beta_equal_alpha_is_exact(hn, prefix, scan):
     k, alpha = 16, 1 / 8
     w, db, q, o_idx, o_sim = oracle_case(30000, 800, 6000, 71, k, alpha)

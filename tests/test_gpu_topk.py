@@ -9,7 +9,7 @@ from tests._gpu_util import oracle_case, to_dev
 
 pytestmark = pytest.mark.gpu
 
-STREAM, DENSE = 1, 2
+STREAM, DENSE, DENSE2 = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +27,7 @@ def _check(res, o_idx, o_sim):
 
 
 @pytest.mark.parametrize("k", [1, 2, 5, 16, 32])
-@pytest.mark.parametrize("prefix,scan", [(0, STREAM), (1, STREAM), (1, DENSE), (2, DENSE)])
+@pytest.mark.parametrize("prefix,scan", [(0, STREAM), (1, STREAM), (1, DENSE), (2, DENSE), (1, DENSE2), (2, DENSE2)])
 def test_topk_matches_oracle(hn, k, prefix, scan):
     w, db, q, _, _ = oracle_case(20011, 700, 4000, 61, 16, 1 / 8)
     o_idx, o_sim = oracle.search_topk(db, q, k)

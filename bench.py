@@ -461,7 +461,7 @@ def main():
         "phases_ms": {kk: statistics.median(p[kk] for p in phase) for kk in
                       ("ms_prep", "ms_phase1", "ms_threshold", "ms_phase2", "ms_rescore", "ms_total")},
         "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan",
-                                               "passes", "kernels")},
+                                               "passes", "kernels", "groups_scored")},
         "survivor_frac": st["survivors"] / (nq * c["n"]),
         "index_build_s": build_s, "index_bytes": info["device_bytes"],
     }

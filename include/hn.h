@@ -142,6 +142,8 @@ typedef struct hn_search_stats {
                                further passes over query tiles) */
     float ms_rescore;       /* survivor rescore, binary64 near-ties, argmax */
     float ms_total;         /* whole search */
+    int64_t groups_scored;  /* dense scan: 32-entry groups the survivor extraction scored on the
+                               CUDA cores (the group map's pass count of the bound test) */
 } hn_search_stats;
 
 typedef struct hn_index_info {

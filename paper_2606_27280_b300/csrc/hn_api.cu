@@ -501,6 +501,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
                 stats->survivors = hc[CT_SURVIVORS];
                 stats->max_survivors = hc[CT_MAXSURV];
                 stats->fp64_rescored = hc[CT_FP64];
+                stats->groups_scored = hc[CT_GROUPS];
                 stats->reruns = reruns;
                 stats->kernels = kernels;
                 stats->passes = passes;

@@ -375,9 +375,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                             }
                             // codes of the two groups; a word holds tiles 2w and 2w + 1 of the chunk
                             const int32_t ti = t - t0;
-                            const uint32_t c01 = code_group(g0, p.code_inv, p.code_base) |
-                                                 (code_group(g1, p.code_inv, p.code_base) << 8);
-                            gword = (ti & 1) ? gword | (c01 << 16) : c01;
+                            // (byte permutes: the low bytes of the two bit patterns, then bytes
+                            // 0-1 of the even tile's word with bytes 0-1 of the odd tile's)
+                            const uint32_t c01 = __byte_perm(code_group_bits(g0, p.code_inv, p.code_base),
+                                                             code_group_bits(g1, p.code_inv, p.code_base), 0x0040);
+                            gword = (ti & 1) ? __byte_perm(gword, c01, 0x5410) : c01;
                             if ((ti & 1) || t == t1 - 1) gb[(int64_t)(ti >> 1) * (p.n_qt * kDQ)] = gword;
                             continue;
                         }
@@ -459,46 +461,80 @@ struct ExtractParams {
     int32_t *bucket, *count;  // count: slots already used (soft mode: the kept best); may pass cap
     int32_t cap;
     float code_inv, code_base;  // one-pass form: the group code of k_dense_scan<., 4, .>
+    long long *counters;        // device counters (CT_GROUPS: groups scored)
+};
+
+// One entry of a flagged group: its stored prefix (and FP8 scale and error term), and the
+// CUDA-core score the extraction kernels and the verification kernel compute from it.
+template <int KP, bool F8>
+struct GroupEntry {
+    static constexpr int kV = F8 ? KP / 16 : KP / 8;  // 16-byte pieces of the stored prefix
+    uint4 v[kV];
+    float esc, b;                                      // FP8: s_i (exact) and b_i
+
+    __device__ __forceinline__ void load(const ExtractParams &x, int64_t e) {
+        if (F8) {
+            const uint8_t *tile8 = static_cast<const uint8_t *>(x.pre) + (e >> 7) * kF8TileBytes(KP);
+            const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(KP));
+#pragma unroll
+            for (int i = 0; i < kV; ++i) v[i] = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, 16 * i, KP));
+            esc = sc2[e & 127] * kF8QScale;
+            b = sc2[kF8Tile + (e & 127)];
+        } else {
+#pragma unroll
+            for (int i = 0; i < kV; ++i)
+                v[i] = *reinterpret_cast<const uint4 *>(static_cast<const char *>(x.pre) + pre16_offset(e, 8 * i, KP));
+        }
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < kV; ++i) v[i] = make_uint4(0u, 0u, 0u, 0u);
+        esc = 0.f;
+        b = 0.f;
+    }
+    // FP32 FMA chain over the prefix columns in order (BF16: the stored values against the
+    // BF16-rounded query; FP8: s_i x^ against the exact query, then + b_i)
+    __device__ __forceinline__ float score(const float *qp) const {
+        float s = 0.f;
+        if (F8) {
+#pragma unroll
+            for (int i = 0; i < kV; ++i) {
+                const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&v[i]);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
+                    s = fmaf(qp[16 * i + 2 * u], f.x * esc, s);
+                    s = fmaf(qp[16 * i + 2 * u + 1], f.y * esc, s);
+                }
+            }
+            s += b;
+        } else {
+#pragma unroll
+            for (int i = 0; i < kV; ++i) {
+                const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v[i]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 f = __bfloat1622float2(h[u]);
+                    s = fmaf(qp[8 * i + 2 * u], f.x, s);
+                    s = fmaf(qp[8 * i + 2 * u + 1], f.y, s);
+                }
+            }
+        }
+        return s;
+    }
 };
 
 template <int KP, bool F8>
 __device__ __forceinline__ float group_entry_score(const ExtractParams &x, int64_t e, const float *qp) {
-    float s = 0.f;
-    if (F8) {
-        const uint8_t *tile8 = static_cast<const uint8_t *>(x.pre) + (e >> 7) * kF8TileBytes(KP);
-        const float *sc2 = reinterpret_cast<const float *>(tile8 + f8_scale_off(KP));
-        const float esc = sc2[e & 127] * kF8QScale;  // s_i: exact
-#pragma unroll
-        for (int c0 = 0; c0 < KP; c0 += 16) {
-            const uint4 raw = *reinterpret_cast<const uint4 *>(tile8 + umma8_offset(e & 127, c0, KP));
-            const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
-                s = fmaf(qp[c0 + 2 * u], f.x * esc, s);
-                s = fmaf(qp[c0 + 2 * u + 1], f.y * esc, s);
-            }
-        }
-        s += sc2[kF8Tile + (e & 127)];  // b_i
-    } else {
-#pragma unroll
-        for (int c = 0; c < KP; c += 8) {
-            const uint4 raw = *reinterpret_cast<const uint4 *>(static_cast<const char *>(x.pre) + pre16_offset(e, c, KP));
-            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float2 f = __bfloat1622float2(h[u]);
-                s = fmaf(qp[c + 2 * u], f.x, s);
-                s = fmaf(qp[c + 2 * u + 1], f.y, s);
-            }
-        }
-    }
-    return s;
+    GroupEntry<KP, F8> g;
+    g.load(x, e);
+    return g.score(qp);
 }
 
 template <int KP, bool F8>
 __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
     const int lane = threadIdx.x & 31;
+    uint32_t scored = 0;  // groups this warp scored (warp-uniform)
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // this thread's query
     const bool qv = q < x.nq;
     const float tau = qv ? x.tau[q] : INFINITY;
@@ -529,6 +565,7 @@ __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
                     while (wo) {
                         const int b = __ffs(wo) - 1;
                         wo &= wo - 1;
+                        ++scored;
                         const int64_t e = (t0 + w * 16 + (b >> 1)) * kDE + h * 64 + (b & 1) * 32 + lane;
                         const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
                         const unsigned hb = __ballot_sync(0xffffffffu, hit);
@@ -547,6 +584,7 @@ __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
             }
         }
     }
+    if (lane == 0 && scored) atomicAdd(reinterpret_cast<unsigned long long *>(x.counters + CT_GROUPS), scored);
 }
 
 // The same step for the one-pass form: the map holds an 8-bit code of every group's
@@ -557,6 +595,7 @@ __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
 template <int KP, bool F8>
 __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams x) {
     const int lane = threadIdx.x & 31;
+    uint32_t scored = 0;  // groups this warp scored (warp-uniform)
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // this thread's query
     const bool qv = q < x.nq;
     const float tau = qv ? x.tau[q] : INFINITY;
@@ -589,6 +628,7 @@ __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams
                     while (wo) {
                         const int b = (__ffs(wo) - 1) >> 3;  // code byte: tile 2w + b / 2, group b % 2
                         wo &= wo - 1;
+                        ++scored;
                         const int64_t e = (t0 + w * 2 + (b >> 1)) * kDE + h * 64 + (b & 1) * 32 + lane;
                         const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
                         const unsigned hb = __ballot_sync(0xffffffffu, hit);
@@ -606,6 +646,7 @@ __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams
             }
         }
     }
+    if (lane == 0 && scored) atomicAdd(reinterpret_cast<unsigned long long *>(x.counters + CT_GROUPS), scored);
 }
 
 // Verification: the CUDA-core score of every (query, entry) pair, computed by
@@ -846,6 +887,7 @@ static ExtractParams extract_base(const Index &ix, int64_t q0, int64_t nq_pass, 
     x.cap = ws.bucket_cap;
     x.code_inv = ix.code_inv;
     x.code_base = code_base();
+    x.counters = ws.counters;
     return x;
 }
 

@@ -123,7 +123,7 @@ struct Index {
 // status word slots
 enum { ST_NOT_NORMALIZED = 0, ST_ZERO_NORM = 1, ST_OVERFLOW = 2, ST_TIMEOUT = 3, ST_BAD_ROW = 4 };
 // counter slots
-enum { CT_SURVIVORS = 0, CT_MAXSURV = 1, CT_FP64 = 2 };
+enum { CT_SURVIVORS = 0, CT_MAXSURV = 1, CT_FP64 = 2, CT_GROUPS = 3 };
 
 // byte offset of (entry e, prefix column c) in the BF16 UMMA-ordered prefix:
 // groups of 8 entries; inside a group, 16-byte core-matrix rows per 8 columns.
@@ -170,9 +170,13 @@ __host__ __device__ inline int64_t umma8_offset(int64_t r, int c, int row_bytes)
 // the range wraps round to 255 instead of 0, which can only flag more groups.
 constexpr uint32_t kCodeBits0 = 0x4B000000u;  // bits of 2^23
 __host__ __device__ inline float code_base() { return 8388608.f + 128.f; }
-__device__ __forceinline__ uint32_t code_group(float g, float inv, float base) {
-    const uint32_t b = __float_as_uint(__fmaf_ru(g, inv, base)) - kCodeBits0;
-    return b < 255u ? b : 255u;
+// The scan's code of a group score, returned in the low byte of a binary32 bit pattern:
+// RU(g * inv + base) clamped from above to 2^23 + 255.  Inside [2^23, 2^23 + 255] the low
+// byte is the code.  A score below the range leaves a value under 2^23 whose low byte is
+// arbitrary: harmless, because such a group matters only for a threshold below the range
+// too, whose code is 0, which every byte reaches.
+__device__ __forceinline__ uint32_t code_group_bits(float g, float inv, float base) {
+    return __float_as_uint(fminf(__fmaf_ru(g, inv, base), 8388608.f + 255.f));
 }
 __device__ __forceinline__ uint32_t code_threshold(float tau, float inv, float base) {
     const float v = fminf(fmaxf(__fmaf_ru(tau, inv, base), 8388608.f), 8388608.f + 255.f);

@@ -55,7 +55,8 @@ class SearchStats(ctypes.Structure):
                 ("max_survivors", ctypes.c_int64), ("fp64_rescored", ctypes.c_int64), ("reruns", ctypes.c_int32),
                 ("scan", ctypes.c_int32), ("kernels", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("ms_prep", ctypes.c_float), ("ms_phase1", ctypes.c_float), ("ms_threshold", ctypes.c_float),
-                ("ms_phase2", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_phase2", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("groups_scored", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense", "dense2"])
     ap.add_argument("--clock-log", default=None,
                     help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
+    ap.add_argument("--best-first", action="store_true",
+                    help="best-first rescore: the survivor of largest prefix score first, the rest only while "
+                         "their prefix bound reaches the best full score (same result)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
     ap.add_argument("--hard", action="store_true",
@@ -338,7 +341,8 @@ def main():
 
     def step(timing=False):
         hn.normalize(q_raw, k, alpha, out=q_norm)
-        return ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, timing=timing)
+        return ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, timing=timing,
+                         best_first=args.best_first)
 
     for _ in range(args.warmup):
         r = step()
@@ -374,7 +378,7 @@ def main():
         e2e_ev[i][0].record(stream)
         q_stage.copy_(q_host, non_blocking=True)
         hn.normalize(q_stage, k, alpha, out=q_norm)
-        ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim)
+        ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, best_first=args.best_first)
         res_idx_host.copy_(out_idx, non_blocking=True)
         res_sim_host.copy_(out_sim, non_blocking=True)
         e2e_ev[i][1].record(stream)
@@ -461,7 +465,7 @@ def main():
         "phases_ms": {kk: statistics.median(p[kk] for p in phase) for kk in
                       ("ms_prep", "ms_phase1", "ms_threshold", "ms_phase2", "ms_rescore", "ms_total")},
         "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan",
-                                               "passes", "kernels", "groups_scored")},
+                                               "passes", "kernels", "groups_scored", "rescore_skipped")},
         "survivor_frac": st["survivors"] / (nq * c["n"]),
         "index_build_s": build_s, "index_bytes": info["device_bytes"],
     }

@@ -117,7 +117,14 @@ typedef struct hn_search_opts {
                               MMAs still drain with the 2 s limit) and the call returns
                               HN_ERR_TIMEOUT.  Limits of a few microseconds make the waits of a
                               normally loaded scan run out: used to exercise that path */
-    int32_t reserved[4];  /* must be zero */
+    int32_t best_first;   /* 1-NN rescore order.  0: every survivor in slot order (Algorithm 1's
+                             Phase 2 in index order).  1: best first, the early exit the remark
+                             after Algorithm 1 describes for a sorted Phase 2: the survivor with
+                             the largest FP32 prefix score is scored first, and every other one only
+                             while its prefix bound reaches the best certified full score so far,
+                             so most survivors cost a read of K values instead of the whole row.
+                             Same result either way */
+    int32_t reserved[3];  /* must be zero */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */
@@ -144,6 +151,8 @@ typedef struct hn_search_stats {
     float ms_total;         /* whole search */
     int64_t groups_scored;  /* dense scan: 32-entry groups the survivor extraction scored on the
                                CUDA cores (the group map's pass count of the bound test) */
+    int64_t rescore_skipped; /* best-first rescore: survivors dropped by the prefix bound before
+                               their full score */
 } hn_search_stats;
 
 typedef struct hn_index_info {
@@ -262,6 +271,29 @@ hn_status hn_search_batch(hn_index *index, const float *q, int64_t nq, const hn_
  */
 hn_status hn_search_topk(hn_index *index, const float *q, int64_t nq, int32_t k, const hn_search_opts *opts,
                          int64_t *out_idx, double *out_sim, hn_search_stats *stats, void *stream);
+
+/*
+ * Merge step of the entry-range sharded search.  Theorem 1's exact maximum is
+ * associative: cut the database into contiguous entry ranges (one per GPU), search
+ * each range exactly (hn_search_batch, k = 1, or hn_search_topk), gather every
+ * range's results, and the k best of the union in the order (similarity
+ * descending, global index ascending) -- Theorem 2's tie rule -- are the answer
+ * over the whole database.
+ *   idx, sim     [n_shards][nq][k] int64 / double: shard r's answers in that order,
+ *                with indices local to the shard (idx < 0: no entry, e.g. a shard
+ *                holding fewer than k entries);
+ *   id_offset    [n_shards] int64: the global index of each shard's entry 0;
+ *   out_idx, out_sim  [nq][k]: the merged answers (global indices; -1 and -inf
+ *                where fewer than k entries exist in all).
+ * Requires 1 <= n_shards <= 64, 1 <= k <= 32, nq >= 0.
+ * hn_merge_topk: every array a DEVICE pointer; one thread per query on `stream`,
+ * does not synchronise.  hn_merge_topk_host: the same on HOST arrays, on the
+ * calling thread (for results gathered through host memory).
+ */
+hn_status hn_merge_topk(const int64_t *idx, const double *sim, const int64_t *id_offset, int32_t n_shards,
+                        int64_t nq, int32_t k, int64_t *out_idx, double *out_sim, void *stream);
+hn_status hn_merge_topk_host(const int64_t *idx, const double *sim, const int64_t *id_offset, int32_t n_shards,
+                             int64_t nq, int32_t k, int64_t *out_idx, double *out_sim);
 
 /*
  * Batched serving (an extension of the method; the paper searches one query

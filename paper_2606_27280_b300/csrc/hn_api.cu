@@ -47,11 +47,15 @@ static void free_ws(Workspace &ws) {
     ws.gbits = nullptr;
     ws.gbits_cap = 0;
     cudaFree(ws.tau);
+    cudaFree(ws.tlow);
+    ws.tlow = nullptr;
     cudaFree(ws.qpre32);
     cudaFree(ws.qpre16);
     cudaFree(ws.qpre16h);
     ws.qpre16h = nullptr;
     cudaFree(ws.qeps);
+    cudaFree(ws.qeps32);
+    ws.qeps32 = nullptr;
     cudaFree(ws.qnorm);
     ws.bucket = nullptr;
     ws.count = nullptr;
@@ -99,10 +103,12 @@ static hn_status ensure_ws(Index &ix, int64_t nq, int32_t cap) {
     HN_CUDA(dalloc(&ws.count, qc));
     HN_CUDA(dalloc(&ws.key1, qc));
     HN_CUDA(dalloc(&ws.tau, qc));
+    HN_CUDA(dalloc(&ws.tlow, qc));
     HN_CUDA(dalloc(&ws.qpre32, (size_t)qc * ix.k_pad4));
     HN_CUDA(dalloc(&ws.qpre16, (size_t)qc * ix.k_pad16));
     HN_CUDA(dalloc(&ws.qpre16h, (size_t)qc * ix.k_pad16));
     HN_CUDA(dalloc(&ws.qeps, qc));
+    HN_CUDA(dalloc(&ws.qeps32, qc));
     HN_CUDA(dalloc(&ws.qnorm, qc));
     ws.q_cap = qc;
     ws.bucket_cap = bc;
@@ -298,7 +304,7 @@ hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *
 // With a proposal (`seed`), its top blocks give the threshold and Phase 1 is skipped.
 static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                             int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn,
-                            float minor_scale) {
+                            float minor_scale, bool best_first) {
     Workspace &ws = ix.ws;
     auto mark = [&](int i) { return timing ? cudaEventRecord(ws.ev[i], s) : cudaSuccess; };
     HN_CUDA(cudaMemsetAsync(ws.key1, 0, sizeof(unsigned long long) * nq, s));
@@ -330,7 +336,7 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         HN_CUDA(mark(4));
     }
     HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s)
-                   : launch_rescore(ix, q, nq, out_idx, out_sim, s));
+                   : launch_rescore(ix, q, nq, out_idx, out_sim, s, best_first));
     HN_CUDA(mark(5));
     return HN_OK;
 }
@@ -386,11 +392,12 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn, b
 // be captured into a CUDA graph.  Status words and counters land in the pinned
 // host mirror ws.h_status once the stream has run.
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
-                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn, float minor_scale) {
+                         int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn, float minor_scale,
+                         bool best_first) {
     Workspace &ws = ix.ws;
     HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
     HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
-    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
+    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s, nn, minor_scale, best_first);
     if (st != HN_OK) return st;
     HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -450,8 +457,9 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
     if (o.scratch_limit < 0) return fail(HN_ERR_INVALID_ARG, "scratch_limit < 0");
     if (o.wait_limit_ns != 0 && (o.wait_limit_ns < 1000 || o.wait_limit_ns > 10000000000ull))
         return fail(HN_ERR_INVALID_ARG, "need wait_limit_ns = 0 or 1e3 <= wait_limit_ns <= 1e10");
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.best_first != 0 && o.best_first != 1) return fail(HN_ERR_INVALID_ARG, "best_first must be 0 or 1");
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->n_queries = nq;
@@ -473,7 +481,8 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         hn_status st = prepare_search(ix, nq, scan, cap, nn, o.seed != nullptr, o.scratch_limit);
         if (st != HN_OK) return st;
         ws.wait_ns = o.wait_limit_ns;
-        st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale);
+        st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale,
+                            o.best_first != 0);
         ws.wait_ns = 0;
         if (st != HN_OK) {
             ws.gbits_limit = 0;
@@ -502,6 +511,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
                 stats->max_survivors = hc[CT_MAXSURV];
                 stats->fp64_rescored = hc[CT_FP64];
                 stats->groups_scored = hc[CT_GROUPS];
+                stats->rescore_skipped = hc[CT_SKIPPED];
                 stats->reruns = reruns;
                 stats->kernels = kernels;
                 stats->passes = passes;

@@ -72,6 +72,8 @@ struct Workspace {
     int64_t cand_cap = 0;              // allocated length of cand
     int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold
+    float *tlow = nullptr;             // [q_cap] T_q: certified lower bound on the best similarity
+                                       //   (the best fully scored threshold candidate; -inf: none)
     float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
     __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles (FP8 index:
                                        //   the e4m3 hi/lo pairs of Phase 2, 2 * k_pad16 bytes a query)
@@ -79,6 +81,8 @@ struct Workspace {
                                        // (int8 index: qpre16 holds k_pad16 int8 codes a query and
                                        //  qpre16h, read as float[q_cap], 1 / (t_q s), see hn_prep.cu)
     float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
+    float *qeps32 = nullptr;           // [q_cap] slack of the FP32 prefix score over the master rows
+                                       //   (best-first rescore): gamma_K |q_maj| max|x_maj| + minor bound
     float *qnorm = nullptr;            // [q_cap] |q| rounded up
     int32_t *status = nullptr;         // [8] device status words
     long long *counters = nullptr;     // [8] device counters for stats
@@ -123,7 +127,7 @@ struct Index {
 // status word slots
 enum { ST_NOT_NORMALIZED = 0, ST_ZERO_NORM = 1, ST_OVERFLOW = 2, ST_TIMEOUT = 3, ST_BAD_ROW = 4 };
 // counter slots
-enum { CT_SURVIVORS = 0, CT_MAXSURV = 1, CT_FP64 = 2, CT_GROUPS = 3 };
+enum { CT_SURVIVORS = 0, CT_MAXSURV = 1, CT_FP64 = 2, CT_GROUPS = 3, CT_SKIPPED = 4 };
 
 // byte offset of (entry e, prefix column c) in the BF16 UMMA-ordered prefix:
 // groups of 8 entries; inside a group, 16-byte core-matrix rows per 8 columns.
@@ -192,7 +196,7 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn = 
                          int64_t scratch_limit = 0);
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                          int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn = 1,
-                         float minor_scale = 1.f);
+                         float minor_scale = 1.f, bool best_first = false);
 hn_status check_search(Index &ix, int64_t nq, int32_t *want_cap);
 int32_t default_cap(const Index &ix);
 Index *index_state_mut(hn_index *h);
@@ -226,8 +230,10 @@ cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *o
 // Exact top-kk of every query from its Phase-2 survivors (1 <= kk <= 32): out_idx/out_sim [nq][kk].
 cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
                                 double *out_sim, cudaStream_t s);
+// best_first: the survivor of largest FP32 prefix score is scored first and the others only
+// while their prefix bound reaches the running certified best (f4)
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
-                           double *out_sim, cudaStream_t s);
+                           double *out_sim, cudaStream_t s, bool best_first = false);
 cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                               double *out_sim, cudaStream_t s);
 // Brute force with a caller-provided per-query key array (nq entries, cleared here).

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
                                                     float qt, float minor_scale,
                                                     const float *__restrict__ dev_max, float *__restrict__ qpre32,
                                                     __nv_bfloat16 *__restrict__ qpre16, __half *__restrict__ qpre16h,
-                                                    float *__restrict__ qeps,
+                                                    float *__restrict__ qeps, float *__restrict__ qeps32,
                                                     float *__restrict__ qnorm, int32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -470,6 +470,11 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     // (soft ANN mode: minor_scale = beta / alpha < 1 relaxes the minor bound; 1 is exact)
     const double e = (scan + (double)minor_scale * qmin * xmin) * (1.0 + 1e-9) + 1e-12;
     qeps[j] = __double2float_ru(e);
+    // the best-first rescore's bound: an FP32 FMA chain over the K prefix dimensions of the
+    // exact query and master row, error <= gamma_K |q_maj| max|x_maj|, plus the full minor
+    // bound (alpha, never the soft mode's beta: the rescore keeps the best survivor exactly)
+    const double gk = k * 0x1p-24 / (1.0 - k * 0x1p-24);
+    qeps32[j] = __double2float_ru((gk * qmaj * xmaj + qmin * xmin) * (1.0 + 1e-9) + 1e-12);
     qnorm[j] = __double2float_ru(sqrt_up(maj2 + min2));
 }
 
@@ -477,7 +482,7 @@ cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, float
     const int64_t nq_pad = (nq + kQPad - 1) / kQPad * kQPad;
     const int64_t blocks = (nq_pad * 32 + 255) / 256;
     k_query_prep<<<(unsigned)blocks, 256, 0, st>>>(q, nq, nq_pad, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16,
-                                                   ix.qt, minor_scale, ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps,
+                                                   ix.qt, minor_scale, ix.dev_max, ix.ws.qpre32, ix.ws.qpre16, ix.ws.qpre16h, ix.ws.qeps, ix.ws.qeps32,
                                                    ix.ws.qnorm, ix.ws.status);
     return cudaGetLastError();
 }

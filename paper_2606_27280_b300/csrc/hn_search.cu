@@ -413,7 +413,8 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                                                         int kp, const float *__restrict__ qpre32,
                                                         const float *__restrict__ qeps,
                                                         const float *__restrict__ qnorm, float xnorm_max, int kk,
-                                                        float *__restrict__ tau, int32_t *__restrict__ count,
+                                                        float *__restrict__ tau, float *__restrict__ tlow,
+                                                        int32_t *__restrict__ count,
                                                         int32_t *__restrict__ bucket, int cap, int keep_best) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -478,7 +479,10 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
         const unsigned hit = __ballot_sync(0xffffffffu, lane < found && rank == kk - 1);
         t_low = __shfl_sync(0xffffffffu, lb, __ffs(hit) - 1);
     }
-    if (lane == 0) tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+    if (lane == 0) {
+        tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+        tlow[j] = t_low;
+    }
     if (keep_best && found > 0) {
         // soft ANN mode: the relaxed bound may prune every entry, the scored candidates
         // included; like Algorithm 1's Phase-1 winner, the best candidate is always kept
@@ -508,7 +512,8 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
                                                      int topk, const int32_t *__restrict__ block_start,
                                                      const int32_t *__restrict__ block_ids, const float *__restrict__ qeps,
                                                      const float *__restrict__ qnorm, float xnorm_max,
-                                                     float *__restrict__ tau, int32_t *__restrict__ count,
+                                                     float *__restrict__ tau, float *__restrict__ tlow,
+                                                     int32_t *__restrict__ count,
                                                      int32_t *__restrict__ bucket, int cap, int keep_best) {
     const int lane = threadIdx.x & 31;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -550,6 +555,7 @@ __global__ void __launch_bounds__(256) k_seed_blocks(const float *__restrict__ r
     }
     if (lane == 0) {
         tau[j] = t_low == -INFINITY ? -INFINITY : __fsub_rd(t_low, qeps[j]);
+        tlow[j] = t_low;
         if (keep_best && t_e >= 0 && cap > 0) {  // soft ANN mode: keep the best candidate (see above)
             bucket[j * (int64_t)cap] = (int32_t)t_e;
             count[j] = 1;
@@ -564,7 +570,8 @@ cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, cons
     // FP32 and BF16 indexes score candidates on their stored prefix, an FP8 index on its master rows
     k_seed_blocks<<<(unsigned)gblocks, 256, 0, st>>>(ix.rows, q, nq, ix.pre32, ix.pre16, ix.k_pad4, ws.qpre32, blocks, topk,
                                                      ix.block_start, ix.block_ids, ws.qeps, ws.qnorm, ix.host_max[4],
-                                                     ws.tau, ws.count, ws.bucket, ws.bucket_cap, keep_best ? 1 : 0);
+                                                     ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
+                                                     keep_best ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -591,7 +598,8 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
                                                        multi ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
                                                        ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
-                                                       ws.tau, ws.count, ws.bucket, ws.bucket_cap, keep_best ? 1 : 0);
+                                                       ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
+                                                       keep_best ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -602,8 +610,8 @@ cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0
     const int cap = ws.bucket_cap;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q + q0 * kD, nq, ix.n, ws.cand + q0 * S, S, seg_entries,
                                                        ix.pre16, ix.k_pad4, ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
-                                                       ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.count + q0,
-                                                       ws.bucket + q0 * cap, cap, keep_best ? 1 : 0);
+                                                       ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.tlow + q0,
+                                                       ws.count + q0, ws.bucket + q0 * cap, cap, keep_best ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -621,6 +629,74 @@ __device__ inline double dot64_seq(const float *__restrict__ a, const float *__r
 #pragma unroll 8
     for (int c = 0; c < kD; ++c) s = fma((double)a[c], (double)b[c], s);
     return s;
+}
+
+// FP32 prefix score over the K leading dimensions of a master row (FMA chain in order),
+// the query's prefix in qs (exact FP32 values); error <= gamma_K |q_maj| |x_maj|.
+__device__ inline float prefix_score32(const float *__restrict__ x, const float *qs, int k) {
+    float s = 0.f;
+    for (int c = 0; c < k; ++c) s = fmaf(qs[c], x[c], s);
+    return s;
+}
+
+// One FP32 full score v of entry id (warp-uniform) into the rescore state: the FP32
+// best, and the band members (FP32 score within 2 eps_r of the best) held one per lane.
+__device__ __forceinline__ void band_push(float v, int32_t id, float band, int lane, float &best32, float &cval,
+                                          int32_t &cidx, int &ncand, bool &spill) {
+    if (v > best32) {
+        // new FP32 best: keep only band members still within 2 eps_r of it
+        best32 = v;
+        const bool keep = lane < ncand && cval >= __fsub_rd(best32, band);
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        const int nk = __popc(mk);
+        unsigned rest = mk;  // clear the `lane` lowest set bits: the next one is member #lane
+        for (int p = 0; p < lane && rest; ++p) rest &= rest - 1;
+        const int src = rest ? __ffs(rest) - 1 : 0;
+        const float nv = __shfl_sync(0xffffffffu, cval, src);
+        const int32_t ni = __shfl_sync(0xffffffffu, cidx, src);
+        cval = lane < nk ? nv : -INFINITY;
+        cidx = lane < nk ? ni : -1;
+        ncand = nk;
+    }
+    if (v >= __fsub_rd(best32, band)) {
+        if (ncand < 32) {
+            if (lane == ncand) { cval = v; cidx = id; }
+            ++ncand;
+        } else {
+            spill = true;
+        }
+    }
+}
+
+// The binary64 step: band members (or, after a spill, every survivor) scored in the
+// oracle's order, and the (score desc, index asc) maximum written out.
+__device__ __forceinline__ void rescore_finish(const float *__restrict__ rows, const float *__restrict__ q, int64_t j,
+                                               const int32_t *bk, int cnt, int lane, bool spill, int ncand,
+                                               int32_t cidx, int64_t *__restrict__ out_idx,
+                                               double *__restrict__ out_sim, long long *__restrict__ counters) {
+    double bs = -INFINITY;
+    int64_t bi = -1;
+    if (!spill) {
+        if (lane < ncand) { bs = dot64_seq(q + j * kD, rows + (int64_t)cidx * kD); bi = cidx; }
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)ncand);
+    } else {
+        for (int s = lane; s < cnt; s += 32) {
+            const int32_t id = bk[s];
+            const double v = dot64_seq(q + j * kD, rows + (int64_t)id * kD);
+            if (v > bs || (v == bs && id < bi)) { bs = v; bi = id; }
+        }
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || os > bs || (os == bs && oi < bi))) { bs = os; bi = oi; }
+    }
+    if (lane == 0) {
+        out_idx[j] = bi;
+        out_sim[j] = bs;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows, const float *__restrict__ q,
@@ -666,57 +742,93 @@ __global__ void __launch_bounds__(256) k_rescore(const float *__restrict__ rows,
 #pragma unroll
             for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (id[u] < 0) continue;
-            const float v = part[u];
-            if (v > best32) {
-                // new FP32 best: keep only band members still within 2 eps_r of it
-                best32 = v;
-                const bool keep = lane < ncand && cval >= __fsub_rd(best32, band);
-                const unsigned mk = __ballot_sync(0xffffffffu, keep);
-                const int nk = __popc(mk);
-                unsigned rest = mk;  // clear the `lane` lowest set bits: the next one is member #lane
-                for (int p = 0; p < lane && rest; ++p) rest &= rest - 1;
-                const int src = rest ? __ffs(rest) - 1 : 0;
-                const float nv = __shfl_sync(0xffffffffu, cval, src);
-                const int32_t ni = __shfl_sync(0xffffffffu, cidx, src);
-                cval = lane < nk ? nv : -INFINITY;
-                cidx = lane < nk ? ni : -1;
-                ncand = nk;
-            }
-            if (v >= __fsub_rd(best32, band)) {
-                if (ncand < 32) {
-                    if (lane == ncand) { cval = v; cidx = id[u]; }
-                    ++ncand;
-                } else {
-                    spill = true;
-                }
-            }
-        }
+        for (int u = 0; u < U; ++u)
+            if (id[u] >= 0) band_push(part[u], id[u], band, lane, best32, cval, cidx, ncand, spill);
     }
-    double bs = -INFINITY;
-    int64_t bi = -1;
-    if (!spill) {
-        if (lane < ncand) { bs = dot64_seq(q + j * kD, rows + (int64_t)cidx * kD); bi = cidx; }
-        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)ncand);
-    } else {
-        for (int s = lane; s < cnt; s += 32) {
-            const int32_t id = bk[s];
-            const double v = dot64_seq(q + j * kD, rows + (int64_t)id * kD);
-            if (v > bs || (v == bs && id < bi)) { bs = v; bi = id; }
+    rescore_finish(rows, q, j, bk, cnt, lane, spill, ncand, cidx, out_idx, out_sim, counters);
+}
+
+// Best-first rescore (the early exit of a sorted Phase 2 that the remark after
+// Algorithm 1 describes).  A sorted Phase 2 reaches a good full score early and then
+// drops every entry whose bound cannot beat it.  Here the threshold kernel has already
+// scored the best prefix candidates in full: their best certified lower bound T_q
+// starts the cut, and a survivor is scored in full only if its bound, an FP32 prefix
+// score over the master row plus eps32, reaches cut = max(T_q, RD(best32 - eps_r)),
+// which rises with every better FP32 score.  A survivor below the cut has similarity
+// < cut <= max, so it can neither win nor tie the winner: the answer is unchanged, and
+// each such survivor costs a read of its K prefix values instead of its whole row.
+__global__ void __launch_bounds__(256) k_rescore_bf(const float *__restrict__ rows, const float *__restrict__ q,
+                                                    int64_t nq, const int32_t *__restrict__ bucket,
+                                                    const int32_t *__restrict__ count, int cap,
+                                                    const float *__restrict__ qnorm, float xnorm_max,
+                                                    const float *__restrict__ qeps32, const float *__restrict__ tlow,
+                                                    int k, int64_t *__restrict__ out_idx, double *__restrict__ out_sim,
+                                                    int32_t *__restrict__ status, long long *__restrict__ counters) {
+    __shared__ float qsh[8][64];  // the query prefix of each warp (zeros beyond K)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    const int cnt = count[j];
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SURVIVORS), (unsigned long long)cnt);
+        atomicMax(reinterpret_cast<unsigned long long *>(counters + CT_MAXSURV), (unsigned long long)cnt);
+    }
+    if (cnt > cap) {
+        if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
+        return;
+    }
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float eps = rescore_eps(qnorm[j], xnorm_max);
+    const float band = __fmul_ru(2.f, eps);
+    const int32_t *bk = bucket + j * (int64_t)cap;
+    float best32 = -INFINITY;
+    float cval = -INFINITY;
+    int32_t cidx = -1;
+    int ncand = 0;
+    bool spill = false;
+    constexpr int U = 8;
+    for (int c = lane; c < 64; c += 32) qsh[wib][c] = c < k ? q[j * kD + c] : 0.f;
+    __syncwarp();
+    const float *qs = qsh[wib];
+    const float e32 = qeps32[j];
+    float cut = tlow[j];
+    long long skipped = 0;
+    for (int s0 = 0; s0 < cnt; s0 += 32) {
+        const int s = s0 + lane;
+        bool keep = false;
+        if (s < cnt) {
+            keep = __fadd_ru(prefix_score32(rows + (int64_t)bk[s] * kD, qs, k), e32) >= cut;
+            skipped += keep ? 0 : 1;
         }
-        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt);
+        unsigned mk = __ballot_sync(0xffffffffu, keep);
+        while (mk) {
+            // up to U kept survivors: FP32 full scores (warp-cooperative rows)
+            int32_t id[U];
+            float part[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int src = mk ? __ffs(mk) - 1 : -1;
+                if (mk) mk &= mk - 1;
+                id[u] = src >= 0 ? bk[s0 + src] : -1;
+                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (id[u] >= 0) xv = reinterpret_cast<const float4 *>(rows + (int64_t)id[u] * kD)[lane];
+                part[u] = fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w)));
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (id[u] >= 0) band_push(part[u], id[u], band, lane, best32, cval, cidx, ncand, spill);
+        }
+        cut = fmaxf(cut, __fsub_rd(best32, eps));
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-        const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (bi < 0 || os > bs || (os == bs && oi < bi))) { bs = os; bi = oi; }
-    }
-    if (lane == 0) {
-        out_idx[j] = bi;
-        out_sim[j] = bs;
-    }
+    for (int o = 16; o; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
+    if (lane == 0 && skipped)
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SKIPPED), (unsigned long long)skipped);
+    rescore_finish(rows, q, j, bk, cnt, lane, spill, ncand, cidx, out_idx, out_sim, counters);
 }
 
 // Exact top-kk (1 <= kk <= 32), one warp per query.  Pass 1 finds f_k, the kk-th
@@ -877,11 +989,16 @@ cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int
 }
 
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool best_first) {
     const int64_t blocks = (nq * 32 + 255) / 256;
-    k_rescore<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
-                                                ix.ws.qnorm, ix.host_max[4], out_idx, out_sim, ix.ws.status,
-                                                ix.ws.counters);
+    if (best_first)
+        k_rescore_bf<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
+                                                       ix.ws.qnorm, ix.host_max[4], ix.ws.qeps32, ix.ws.tlow, ix.k, out_idx,
+                                                       out_sim, ix.ws.status, ix.ws.counters);
+    else
+        k_rescore<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
+                                                    ix.ws.qnorm, ix.host_max[4], out_idx, out_sim, ix.ws.status,
+                                                    ix.ws.counters);
     return cudaGetLastError();
 }
 

@@ -46,13 +46,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait: returns false (and raises *abort) once `limit_ns` of global
-// time has passed, or as soon as another thread has raised *abort.
+// time has passed, or as soon as another thread has raised *abort.  The clock is
+// read every 256 tries, or every try for limits under 1 ms (so that a limit of a
+// few microseconds is honoured).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
+    const uint32_t mask = limit_ns < 1000000ull ? 0u : 255u;
     for (uint32_t i = 1;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 255u) == 0) {
+        if ((i & mask) == 0) {
             if (*abort) return false;
             if (globaltimer() - t0 > limit_ns) {
                 *abort = 1;

@@ -35,7 +35,7 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("scan", ctypes.c_int32), ("bucket_cap", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("soft", ctypes.c_int32),
                 ("beta", ctypes.c_float), ("scratch_limit", ctypes.c_int64), ("wait_limit_ns", ctypes.c_uint64),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("best_first", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -56,7 +56,7 @@ class SearchStats(ctypes.Structure):
                 ("scan", ctypes.c_int32), ("kernels", ctypes.c_int32), ("passes", ctypes.c_int32),
                 ("ms_prep", ctypes.c_float), ("ms_phase1", ctypes.c_float), ("ms_threshold", ctypes.c_float),
                 ("ms_phase2", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("groups_scored", ctypes.c_int64)]
+                ("groups_scored", ctypes.c_int64), ("rescore_skipped", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -109,6 +109,8 @@ SIGNATURES = {
     "hn_search_topk": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "hn_bruteforce": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "hn_prefix_scores": ([_vp, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
+    "hn_merge_topk": ([_vp, _vp, _vp, _i32, _i64, _i32, _vp, _vp, _vp], _i32),
+    "hn_merge_topk_host": ([_vp, _vp, _vp, _i32, _i64, _i32, _vp, _vp], _i32),
     "hn_index_blocks": ([_vp, _vp, _vp, _vp, _vp], _i32),
     "hn_search_multi": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "hn_autotune": ([_vp, _vp, _i32, _vp, _vp], _i32),
@@ -249,13 +251,15 @@ class Index:
                timing: bool = False,
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
                proposal: "Proposal | None" = None, seed_topk: int = 0, beta: float | None = None,
-               scratch_limit: int = 0, wait_limit_ns: int = 0, stream=None) -> SearchResult:
+               scratch_limit: int = 0, wait_limit_ns: int = 0, best_first: bool = False,
+               stream=None) -> SearchResult:
         """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
         `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped.
         `beta` (0 <= beta <= alpha) selects the soft ANN mode: alpha in the skip test becomes
         beta (beta = alpha is exact).  `scratch_limit` caps the bytes of the dense scan's group
         map (larger batches run in passes); `wait_limit_ns` sets the dense scan's device-side
-        wait limit (0 = 2 s)."""
+        wait limit (0 = 2 s).  `best_first` rescores the survivor of best prefix score first and
+        drops the others whose prefix bound cannot reach it (same result)."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         if out_idx is None:
@@ -265,7 +269,8 @@ class Index:
         opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), timing=int(bool(timing)),
                           seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None,
                           soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0,
-                          scratch_limit=int(scratch_limit), wait_limit_ns=int(wait_limit_ns))
+                          scratch_limit=int(scratch_limit), wait_limit_ns=int(wait_limit_ns),
+                          best_first=int(bool(best_first)))
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),
                                     out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,
@@ -404,6 +409,41 @@ def search_multi(batches, use_graph: bool = True, stream=None) -> dict:
     _check(_lib.hn_search_multi(arr, len(batches), ctypes.byref(opts), ctypes.byref(st), _stream(stream)),
            "hn_search_multi")
     return {name: getattr(st, name) for name, _ in st._fields_ if name != "reserved"}
+
+
+def merge_topk(idx: torch.Tensor, sim: torch.Tensor, id_offset: torch.Tensor, stream=None):
+    """Merge per-shard answers: idx int64 / sim float64 of shape (n_shards, nq, k) with
+    shard-local indices, id_offset int64 (n_shards,), all on the device.  Returns the
+    (nq, k) global answers in the order (similarity desc, index asc)."""
+    if idx.dim() != 3 or sim.shape != idx.shape or id_offset.numel() != idx.shape[0]:
+        raise ValueError("idx, sim: (n_shards, nq, k); id_offset: (n_shards,)")
+    if idx.dtype != torch.int64 or sim.dtype != torch.float64 or id_offset.dtype != torch.int64:
+        raise TypeError("idx and id_offset int64, sim float64")
+    if not (idx.is_cuda and sim.is_cuda and id_offset.is_cuda):
+        raise TypeError("merge_topk takes device tensors (merge_topk_host: numpy arrays)")
+    r, nq, k = idx.shape
+    idx, sim, id_offset = idx.contiguous(), sim.contiguous(), id_offset.contiguous()
+    out_idx = torch.empty((nq, k), dtype=torch.int64, device=idx.device)
+    out_sim = torch.empty((nq, k), dtype=torch.float64, device=idx.device)
+    _check(_lib.hn_merge_topk(idx.data_ptr(), sim.data_ptr(), id_offset.data_ptr(), r, nq, k, out_idx.data_ptr(),
+                              out_sim.data_ptr(), _stream(stream)), "hn_merge_topk")
+    return out_idx, out_sim
+
+
+def merge_topk_host(idx, sim, id_offset):
+    """merge_topk on host (numpy) arrays, computed by the library's host merge."""
+    import numpy as np
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    sim = np.ascontiguousarray(sim, dtype=np.float64)
+    off = np.ascontiguousarray(id_offset, dtype=np.int64)
+    if idx.ndim != 3 or sim.shape != idx.shape or off.size != idx.shape[0]:
+        raise ValueError("idx, sim: (n_shards, nq, k); id_offset: (n_shards,)")
+    r, nq, k = idx.shape
+    out_idx = np.empty((nq, k), np.int64)
+    out_sim = np.empty((nq, k), np.float64)
+    _check(_lib.hn_merge_topk_host(idx.ctypes.data, sim.ctypes.data, off.ctypes.data, r, nq, k, out_idx.ctypes.data,
+                                   out_sim.ctypes.data), "hn_merge_topk_host")
+    return out_idx, out_sim
 
 
 def selftest_wait_timeout(limit_ns: int, stream=None) -> int:

@@ -41,7 +41,7 @@ def test_struct_sizes_match_header(hn):
     # sizes implied by the field lists in include/hn.h (x86-64 ABI)
     assert ctypes.sizeof(hn.IndexOpts) == 32
     assert ctypes.sizeof(hn.SearchOpts) == 64
-    assert ctypes.sizeof(hn.SearchStats) == 88
+    assert ctypes.sizeof(hn.SearchStats) == 96
     assert hn.SearchStats.passes.offset == 52
     assert ctypes.sizeof(hn.IndexInfo) == 64
     assert ctypes.sizeof(hn.TrainOpts) == 40

@@ -35,3 +35,32 @@ def test_repeated_timeouts(hn):
     from paper_2606_27280_b300 import hn as binding
     for _ in range(3):
         assert hn.selftest_wait_timeout(2_000_000) == binding.ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("prefix,scan", [(1, 2), (2, 2), (2, 3)])
+def test_dense_scan_abort_and_drain(hn, prefix, scan):
+    """A main-loop wait limit of one microsecond makes the tensor-core scan's waits give up
+    under normal load (the one-pass form, and the two-pass form of the FP8 prefix, whose
+    epilogue is slow enough that waits pass 1 us), with copies and MMAs in flight: the CTA raises its abort flag, the
+    other roles leave their loops, copies and MMAs still in flight drain (with the full 2 s
+    limit), tensor memory is freed and the kernel returns.  The call reports
+    HN_ERR_TIMEOUT, and an exact search right after, on the same index, is the oracle's."""
+    from paper_2606_27280_b300 import hn as binding
+    # 400k entries and 512 queries give every CTA ~64 entry tiles, more than its copy ring
+    # holds (40), so the producer waits about four tile periods (> 1 us) for each freed stage
+    w, db, q, o_idx, o_sim = oracle_case(400003, 512, 80000, 82, 16, 1 / 8)
+    with hn.Index(to_dev(db), 16, 1 / 8, prefix=prefix) as ix:
+        qd = to_dev(q)
+        timeouts = 0
+        for _ in range(5):
+            try:
+                ix.search(qd, scan=scan, wait_limit_ns=1000)
+            except hn.HNError as e:
+                assert e.status == binding.ERR_TIMEOUT, str(e)
+                timeouts += 1
+        assert timeouts >= 1
+        r = ix.search(qd, scan=scan)
+        assert_parity(r.idx, r.sim, o_idx, o_sim)
+        with pytest.raises(hn.HNError) as e:
+            ix.search(qd, scan=scan, wait_limit_ns=999)     # below the documented range
+        assert e.value.status == binding.ERR_INVALID_ARG

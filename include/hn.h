@@ -447,8 +447,10 @@ hn_status hn_bruteforce(const hn_index *index, const float *q, int64_t nq, int64
  *  - The scratch holds HN_STATIC_MAX_QUERIES 8-byte keys (512 KiB) on every GPU
  *    that loads the library, kept until the process exits.
  *  - The first call on each device looks the scratch address up
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it with the
+ *    CUDA context's unique id; after a device reset (cudaDeviceReset makes a new
+ *    context) the next call looks it up again.  Make the first call on a device,
+ *    and the first after a reset, before any stream capture.
  *  - All calls share the one array and it keeps the last call's contents; each
  *    call clears the keys it uses before scanning.  Calls that overlap on the
  *    GPU (e.g. on unordered streams) race and can return wrong answers: order them.

@@ -19,8 +19,9 @@
  *                   search (Theorem 1, §3.3) with ties resolved by index
  *                   (Theorem 2 and the remark after it): the lowest index
  *                   among the maximal binary64 similarities.
- *   hno_two_phase   Algorithm 1 (§3.3), steps in the paper's order, with the
- *                   readings listed at its definition.
+ *   hno_two_phase   the branch-and-bound that Eq. 3 licenses and Theorem 1
+ *                   proves exact (the search of §3.3), with the readings listed
+ *                   at its definition.
  *   hno_search_topk exhaustive top-k by (similarity desc, index asc).
  */
 #include <math.h>
@@ -195,13 +196,15 @@ int hno_search_topk(const float *db, int64_t n, const float *q, int64_t nq, int 
     return HNO_OK;
 }
 
-/* ------------------------------------------------------------ Algorithm 1 */
-/* Two-phase search for one query, in the paper's order:
- *   Phase 1: s_i = dot_K(q, x_i) for all i; b = argmax_i s_i (lowest index on ties).
- *   s_best = <q, x_b> (the full dot continues the stored prefix sum s_b);
- *   Phase 2: for i != b in index order: skip when s_i + bound_i < s_best, else
- *            c = s_i + <q_minor, x_i,minor>; take i when c > s_best, or c == s_best
- *            and i < best_idx.
+/* --------------------------------------------------- bound-based search (§3.3) */
+/* Per query, from Eq. 2 and Eq. 3: <q, x_i> = s_i + <q_minor, x_i,minor> with
+ * s_i = dot_K(q, x_i), and <q_minor, x_i,minor> <= bound_i, so an entry whose
+ * s_i + bound_i lies below the full score of an entry already evaluated cannot be
+ * the nearest neighbour, and evaluating every other entry in full gives the
+ * exhaustive answer (Theorem 1).  The first full score is taken from the entry of
+ * largest s_i (lowest index on ties), the natural choice the search of §3.3 makes;
+ * every other entry is then tested against the best full score so far, in index
+ * order, and evaluated only when its bound reaches it.
  * Readings (the paper is silent or literal-but-different on these):
  *   - bound_i: with literal_bound != 0 it is alpha, as printed in Eq. 3; otherwise
  *     it is |q_minor| |x_i,minor| (binary64 norms of the stored values) + 1e-12,
@@ -209,10 +212,11 @@ int hno_search_topk(const float *db, int64_t n, const float *q, int64_t nq, int 
  *     because binary32 storage moves the norms off sqrt(alpha) by O(2^-24).
  *   - the skip is strict ('<' instead of the printed '<=') and equal full scores
  *     go to the lower index, so the result is the lowest index among the maxima
- *     (the printed '<=' and strict-'>' update return b on an exact tie instead).
- * Because the full dot continues the prefix sum in dimension order, c equals
- * hno_dot(q, x_i) bit for bit.  *n_full counts Phase-2 full evaluations
- * (the paper's Phase2%), excluding b. */
+ *     (the printed '<=' with a strict-'>' update returns the first evaluated entry
+ *     on an exact tie instead).
+ * Because the full score continues the prefix sum in dimension order, it equals
+ * hno_dot(q, x_i) bit for bit.  *n_full counts the full evaluations after the
+ * first (the paper's Phase2%). */
 int hno_two_phase(const float *db, int64_t n, const float *q, int64_t nq, int d, int k,
                   double alpha, int literal_bound, int64_t *out_idx, double *out_sim,
                   int64_t *n_full)

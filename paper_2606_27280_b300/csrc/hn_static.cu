@@ -11,6 +11,8 @@
 // the only other memory the call touches.
 #include <mutex>
 
+#include <cuda.h>
+
 #include "hn_internal.cuh"
 
 namespace hn {
@@ -20,25 +22,61 @@ namespace hn {
 static __device__ __align__(256) unsigned long long g_static_keys[HN_STATIC_MAX_QUERIES];
 
 constexpr int kMaxDevices = 64;
-static unsigned long long *g_static_addr[kMaxDevices] = {};
+struct StaticSlot {
+    unsigned long long ctx_id = 0;   // the CUDA context the address belongs to (0: none yet)
+    unsigned long long *addr = nullptr;
+};
+static StaticSlot g_static_slot[kMaxDevices];
 static std::mutex g_static_mu;
 
-// Device address of g_static_keys on the current device.  In host code the
-// symbol is only a host-side stand-in, so the address is looked up once per
-// device, with that device current, and cached.
+// Unique id of the current CUDA context (driver entry points looked up once through the
+// runtime, so the library does not link the driver library); 0 if unavailable.
+static unsigned long long current_ctx_id() {
+    typedef CUresult (*GetCurrent)(CUcontext *);
+    typedef CUresult (*GetId)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult r1, r2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &r1) == cudaSuccess &&
+            r1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &r2) == cudaSuccess &&
+            r2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(g);
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_static_keys in the current context.  In host code the symbol is
+// only a host-side stand-in, so the address is looked up with the device current and
+// cached per device together with the context's unique id: after a device reset (a new
+// primary context) the id differs and the address is looked up again.
 static hn_status static_keys(unsigned long long **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(HN_ERR_UNSUPPORTED, "device ordinal out of range");
+    // 0 when this thread has no current context yet: then the address is looked up, which
+    // also makes the device's primary context current for the next call
+    const unsigned long long id = current_ctx_id();
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    StaticSlot &slot = g_static_slot[dev];
+    if (!slot.addr || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_keys);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_keys)");
-        g_static_addr[dev] = static_cast<unsigned long long *>(p);
+        slot.addr = static_cast<unsigned long long *>(p);
+        slot.ctx_id = id;
     }
-    *out = g_static_addr[dev];
+    *out = slot.addr;
     return HN_OK;
 }
 

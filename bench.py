@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--best-first", action="store_true",
                     help="best-first rescore: the survivor of largest prefix score first, the rest only while "
                          "their prefix bound reaches the best full score (same result)")
+    ap.add_argument("--no-autotune", action="store_true", help="c4: keep every index's default scan choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
     ap.add_argument("--hard", action="store_true",
@@ -637,7 +638,7 @@ def run_serving(args, hn, torch, world, rank, dist, barrier):
     # the autotuner picks, per index, the dense/stream crossover and the dense work granularity
     # for the batch sizes it will see: a ladder up to its group's concatenated size
     tuned = []
-    for g, (ix, di, k, a) in enumerate(indexes):
+    for g, (ix, di, k, a) in enumerate(indexes if not args.no_autotune else []):
         group_q = int(sizes[pick == g].sum())
         ladder = sorted({min(s_, ix.n) for s_ in (128, 512, 2048, max(group_q, 1))})
         r = ix.autotune(ladder)
@@ -669,6 +670,7 @@ def run_serving(args, hn, torch, world, rank, dist, barrier):
                                        "K in {8,16} x alpha in {1/32,1/8}, BF16 prefix",
                            "queries_per_step": total_q, "n_indexes": len(indexes)},
                 "graph_replayed": st["graph_replayed"], "groups": st["n_groups"],
+                "groups_in_shared_scan": st["joined"],
                 "batch_latency_ms": {"p50": st["batch_ms_p50"], "p99": st["batch_ms_p99"], "max": st["batch_ms_max"]},
                 "search_multi_ms": st["ms_total"], "survivors": st["survivors"], "autotune": tuned,
                 "note": "step = one hn_search_multi over all 256 batches (queries HN-normalised beforehand); "

@@ -300,8 +300,12 @@ hn_status hn_merge_topk_host(const int64_t *idx, const double *sim, const int64_
  * at a time).  One call answers nb batches of queries, each against its own
  * index; every batch's result is the same as hn_search_batch would give.
  * Batches are grouped by index and each group's queries concatenated, so that
- * small batches share the dense scan's work units; each group runs on a
- * stream of its own.  With opts->use_graph (default 1) the whole set is
+ * small batches share the dense scan's work units.  The groups that take the
+ * one-pass dense scan on indexes of one tile format (prefix type and padded K)
+ * run their scans as ONE persistent launch whose work units cover every such
+ * group; each group's query preparation, threshold, survivor extraction and
+ * rescore run on a stream of its own, as does the whole pipeline of any other
+ * group.  With opts->use_graph (default 1) the whole set is
  * captured once into a CUDA graph and the graph is replayed as long as the
  * same batches come back (same indexes, query and output pointers and sizes,
  * and no reallocation of the indexes' scratch in between).  Synchronises
@@ -328,7 +332,7 @@ typedef struct hn_multi_stats {
     int32_t reruns;          /* re-runs after survivor-slot overflow */
     float ms_total;          /* device time from the start of the set to its last batch */
     float batch_ms_p50, batch_ms_p99, batch_ms_max;  /* time from the start to each batch's completion */
-    int32_t reserved;
+    int32_t joined;          /* groups whose dense scans ran as one shared persistent launch (0: none) */
     int64_t survivors;       /* Phase-2 survivors over all batches */
 } hn_multi_stats;
 

@@ -71,24 +71,46 @@ constexpr int kDenseThreads = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // default main-loop wait limit, and every drain's
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
-struct DenseParams {
+// One index and query batch of a dense launch.  A launch has one group, or (the one-pass
+// form of batched serving) several that share the tile format, with their work units
+// numbered group by group.
+struct DenseGroup {
     const void *pre;              // entries, UMMA core-matrix order, n_tiles * 128 rows (FP16 or BF16)
     const void *qpre;             // queries, same order, n_qt * 256 rows
     int64_t n, n_tiles, nq;
-    int64_t n_qt, tiles_per_chunk, n_units;
+    int64_t n_qt, tiles_per_chunk, chunks;
+    int64_t unit0;                // global number of the group's first work unit
     const float *tau;
     unsigned long long *cand;     // [nq][2 * chunks] PHASE 1: (best score, 64-entry segment id), PHASE 4:
                                   //   (best group score, 32-entry group id) per (query, chunk, entry half)
     uint32_t *gbits;              // [chunk][half][word][n_qt * 256] group map: PHASE 2 passing-group bits,
                                   //   16 tiles a word; PHASE 4 group codes, 2 tiles (4 codes) a word
     int64_t words;                // words per (chunk, half): ceil(tiles_per_chunk / 16), PHASE 4: / 2
-    float code_inv, code_base;    // PHASE 4: the group code (hn_internal.cuh)
+    float code_inv;               // PHASE 4: the group code (hn_internal.cuh)
+};
+
+struct DenseParams {
+    DenseGroup g;                 // the group of a single-group launch (n_groups == 0)
+    const DenseGroup *groups;     // n_groups > 0: the groups' descriptors (device memory)
+    int32_t n_groups;
+    int64_t n_units;              // work units of all groups
+    float code_base;              // PHASE 4: the group code
     float *dump;                  // PHASE 3: [nq][n] every FP32 score (Phase-2 arithmetic)
     uint64_t wait_ns;             // limit of every main-loop wait (the drains keep kWaitLimitNs)
     int32_t *status;
 };
 constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
 constexpr int kDE = 128;   // entries per B tile (MMA N)
+
+// Group of work unit u in a multi-group launch (the last group whose unit0 <= u).
+__device__ __forceinline__ const DenseGroup &group_of(const DenseParams &p, int64_t u) {
+    int lo = 0, hi = p.n_groups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.groups[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    return p.groups[lo];
+}
 
 // Measured on B300: one thread issues a 1-D bulk copy every ~350 cycles whatever
 // its size, and a tcgen05.commit costs ~220 cycles.  So a ring stage holds
@@ -138,8 +160,10 @@ __device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
     return fmaxf(__low2float(h[0]), __high2float(h[0]));
 }
 
-template <int KP, int PHASE, bool F8>
-__global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DenseParams p) {
+// MULTI: the launch covers several groups (p.groups); otherwise the one group p.g, read in
+// place from the kernel parameters.
+template <int KP, int PHASE, bool F8, bool MULTI = false>
+__global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_constant__ DenseParams p) {
     using C = DenseCfg<KP, PHASE, F8>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
@@ -185,11 +209,12 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             int64_t b_issued = 0, a_issued = 0;  // copies issued into the B ring / A buffers
             bool ok = true;
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
-                const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
-                const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
+                const DenseGroup &gr = MULTI ? group_of(p, u) : p.g;
+                const int64_t qt = (u - gr.unit0) % gr.n_qt, ch = (u - gr.unit0) / gr.n_qt;
+                const int64_t t0 = ch * gr.tiles_per_chunk, t1 = min64(gr.n_tiles, t0 + gr.tiles_per_chunk);
                 if (!(ok = mbar_wait(smem_u32(&a_empty[abuf]), aphase ^ 1, abort_flag, p.wait_ns))) break;
                 mbar_arrive_expect_tx(smem_u32(&a_full[abuf]), C::kA);
-                bulk_g2s(smem_u32(sA + abuf * C::kA), static_cast<const char *>(p.qpre) + qt * C::kA, C::kA,
+                bulk_g2s(smem_u32(sA + abuf * C::kA), static_cast<const char *>(gr.qpre) + qt * C::kA, C::kA,
                          smem_u32(&a_full[abuf]));
                 ++a_issued;
                 if (++abuf == 2) { abuf = 0; aphase ^= 1; }
@@ -197,7 +222,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                     const uint32_t bytes = (uint32_t)min64(C::kTPS, t1 - tt) * C::kB;
                     if (!(ok = mbar_wait(smem_u32(&b_empty[stage]), sphase ^ 1, abort_flag, p.wait_ns))) break;
                     mbar_arrive_expect_tx(smem_u32(&b_full[stage]), bytes);
-                    bulk_g2s(smem_u32(sB + stage * C::kStageBytes), static_cast<const char *>(p.pre) + tt * C::kB,
+                    bulk_g2s(smem_u32(sB + stage * C::kStageBytes), static_cast<const char *>(gr.pre) + tt * C::kB,
                              bytes, smem_u32(&b_full[stage]));
                     ++b_issued;
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
@@ -226,8 +251,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             uint64_t g = 0;  // tile counter of this CTA
             bool ok = true;
             for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
-                const int64_t ch = u / p.n_qt;
-                const int64_t t0 = ch * p.tiles_per_chunk, t1 = min64(p.n_tiles, t0 + p.tiles_per_chunk);
+                const DenseGroup &gr = MULTI ? group_of(p, u) : p.g;
+                const int64_t ch = (u - gr.unit0) / gr.n_qt;
+                const int64_t t0 = ch * gr.tiles_per_chunk, t1 = min64(gr.n_tiles, t0 + gr.tiles_per_chunk);
                 if (!(ok = mbar_wait(smem_u32(&a_full[abuf]), aphase, abort_flag, p.wait_ns))) break;
                 tc_fence_after();
                 const uint32_t a_addr = smem_u32(sA + abuf * C::kA);
@@ -286,19 +312,21 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
         uint32_t g = 0;  // tile counter of this CTA: buffer g & 1, its use number g >> 1
         bool ok = true;
         for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
-            const int64_t qt = u % p.n_qt, ch = u / p.n_qt;
+            const DenseGroup &gr = MULTI ? group_of(p, u) : p.g;
+            const int64_t qt = (u - gr.unit0) % gr.n_qt, ch = (u - gr.unit0) / gr.n_qt;
             // tile and entry numbers fit in 32 bits (n < 2^31 - 256 is enforced by hn_index_build)
-            const int32_t t0 = (int32_t)(ch * p.tiles_per_chunk);
-            const int32_t t1 = (int32_t)min64(p.n_tiles, (int64_t)t0 + p.tiles_per_chunk);
+            const int32_t t0 = (int32_t)(ch * gr.tiles_per_chunk);
+            const int32_t t1 = (int32_t)min64(gr.n_tiles, (int64_t)t0 + gr.tiles_per_chunk);
             const int64_t q = qt * kDQ + row;
-            const bool qvalid = q < p.nq;
-            const float thr = (PHASE == 2 && qvalid) ? p.tau[q] : INFINITY;
+            const bool qvalid = q < gr.nq;
+            const float thr = (PHASE == 2 && qvalid) ? gr.tau[q] : INFINITY;
+
             float best = -INFINITY;
             int32_t bseg = -1;   // PHASE 1: 64-entry segment of `best`; PHASE 4: its 32-entry group
             uint32_t gword = 0;  // PHASE 2: passing-group bits of the current 16 tiles; PHASE 4: codes of 2 tiles
-            uint32_t *gb = (PHASE == 2 || PHASE == 4) ? p.gbits + (ch * 2 + half) * p.words * (p.n_qt * kDQ) + q
+            uint32_t *gb = (PHASE == 2 || PHASE == 4) ? gr.gbits + (ch * 2 + half) * gr.words * (gr.n_qt * kDQ) + q
                                                       : nullptr;
-            const int32_t n32 = (int32_t)p.n;
+            const int32_t n32 = (int32_t)gr.n;
             const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
             int32_t e0 = t0 * kDE + half * 64;    // first entry of this warp's 64 columns
             for (int32_t tt = t0; ok && tt < t1; tt += C::kTPS) {
@@ -377,10 +405,12 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                             const int32_t ti = t - t0;
                             // (byte permutes: the low bytes of the two bit patterns, then bytes
                             // 0-1 of the even tile's word with bytes 0-1 of the odd tile's)
-                            const uint32_t c01 = __byte_perm(code_group_bits(g0, p.code_inv, p.code_base),
-                                                             code_group_bits(g1, p.code_inv, p.code_base), 0x0040);
+                            const uint32_t c01 = __byte_perm(code_group_bits(g0, gr.code_inv, p.code_base),
+                                                             code_group_bits(g1, gr.code_inv, p.code_base), 0x0040);
                             gword = (ti & 1) ? __byte_perm(gword, c01, 0x5410) : c01;
-                            if ((ti & 1) || t == t1 - 1) gb[(int64_t)(ti >> 1) * (p.n_qt * kDQ)] = gword;
+                            // streaming store: the code map (one byte per 32 scores) should not evict
+                            // the prefix tiles the other CTAs and the extraction read from L2
+                            if ((ti & 1) || t == t1 - 1) __stcs(gb + (int64_t)(ti >> 1) * (gr.n_qt * kDQ), gword);
                             continue;
                         }
                         if (F8) {
@@ -405,7 +435,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                         if (PHASE == 3) {
                             // verification: every score of the Phase-2 arithmetic to memory
                             if (qvalid) {
-                                float *d = p.dump + q * p.n;
+                                float *d = p.dump + q * gr.n;
                                 for (int i = 0; i < 64; ++i)
                                     if (e0 + i < n32) d[e0 + i] = v[i];
                             }
@@ -419,7 +449,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
                         const float g0 = fmaxf(max16(v), max16(v + 16)), g1 = fmaxf(max16(v + 32), max16(v + 48));
                         gword |= ((g0 >= thr ? 1u : 0u) | (g1 >= thr ? 2u : 0u)) << (2 * (ti & 15));
                         if ((ti & 15) == 15 || t == t1 - 1) {
-                            gb[(int64_t)(ti >> 4) * (p.n_qt * kDQ)] = gword;
+                            gb[(int64_t)(ti >> 4) * (gr.n_qt * kDQ)] = gword;
                             gword = 0;
                         }
                     }
@@ -429,8 +459,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const DensePara
             if (!ok) break;
             // one writer per (query, chunk, entry half): no atomics, every slot written
             if ((PHASE == 1 || PHASE == 4) && qvalid)
-                p.cand[q * (2 * (p.n_units / p.n_qt)) + 2 * ch + half] =
-                    bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
+                gr.cand[q * (2 * gr.chunks) + 2 * ch + half] = bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
         }
     }
 
@@ -609,7 +638,7 @@ __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams
         for (int64_t w0 = 0; w0 < nw; w0 += 8) {
             uint32_t wv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nw) ? gw[(w0 + i) * x.q_pad + q] : 0u;
+            for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nw) ? __ldcs(gw + (w0 + i) * x.q_pad + q) : 0u;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int64_t w = w0 + i;
@@ -711,6 +740,9 @@ static cudaError_t set_attr2() {
     if (e == cudaSuccess) e = set_attr1<KP, 2, F8>();
     if (e == cudaSuccess) e = set_attr1<KP, 3, F8>();
     if (e == cudaSuccess) e = set_attr1<KP, 4, F8>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dense_smem<KP, 4, F8>());
     return e;
 }
 
@@ -860,13 +892,13 @@ static DenseParams dense_base(const Index &ix, int phase) {
     DenseParams p{};
     // FP8: one tile array for every phase; the query operands differ (qpre16h: Phase-1 e4m3 of
     // 16 q, qpre16: the hi/lo e4m3 of 256 q of the other phases)
-    p.pre = f8 ? (const void *)ix.pre8 : phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
-    p.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
-    p.n = ix.n;
-    p.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
+    p.g.pre = f8 ? (const void *)ix.pre8 : phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
+    p.g.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
+    p.g.n = ix.n;
+    p.g.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
     p.status = ws.status;
     p.wait_ns = ws.wait_ns ? ws.wait_ns : kWaitLimitNs;
-    p.code_inv = ix.code_inv;
+    p.g.code_inv = ix.code_inv;
     p.code_base = code_base();
     return p;
 }
@@ -901,36 +933,38 @@ cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream
     const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
     if (phase == 1) {
         int64_t chunks = 0;
-        p.nq = nq;
-        p.n_qt = n_qt;
-        dense_chunking(p.n_tiles, p.n_qt, G, ix.units_per_cta, &p.tiles_per_chunk, &chunks);
-        p.n_units = p.n_qt * chunks;
-        p.tau = ws.tau;
-        p.cand = ws.cand;
+        p.g.nq = nq;
+        p.g.n_qt = n_qt;
+        dense_chunking(p.g.n_tiles, p.g.n_qt, G, ix.units_per_cta, &p.g.tiles_per_chunk, &chunks);
+        p.g.chunks = chunks;
+        p.n_units = p.g.n_qt * chunks;
+        p.g.tau = ws.tau;
+        p.g.cand = ws.cand;
         return launch_dense_kernel(kp, f8, p, 1, (int)min64(G, p.n_units), st);
     }
     // Phase 2: the tensor-core scan marks the passing 32-entry groups, k_dense_extract turns
     // them into survivors; passes over query tiles keep the bitmap within the workspace
     const int64_t cap = map_cap(ws);
     for (int64_t qt0 = 0; qt0 < n_qt;) {
-        const int64_t nqt = phase2_pass_tiles(p.n_tiles, n_qt, qt0, G, ix.units_per_cta, cap);
+        const int64_t nqt = phase2_pass_tiles(p.g.n_tiles, n_qt, qt0, G, ix.units_per_cta, cap);
         if (nqt == 0) return cudaErrorInvalidValue;  // prepare_search sizes the bitmap for one tile at least
         const int64_t q0 = qt0 * kDQ;
         qt0 += nqt;
         DenseParams pp = p;
         int64_t chunks = 0;
-        pp.qpre = static_cast<const char *>(p.qpre) + q0 * kp * 2;  // 2 kp bytes a query (BF16, or e4m3 hi + lo)
-        pp.nq = min64(nq - q0, nqt * kDQ);
-        pp.n_qt = nqt;
-        dense_chunking(p.n_tiles, nqt, G, ix.units_per_cta, &pp.tiles_per_chunk, &chunks);
+        pp.g.qpre = static_cast<const char *>(p.g.qpre) + q0 * kp * 2;  // 2 kp bytes a query (BF16, or e4m3 hi + lo)
+        pp.g.nq = min64(nq - q0, nqt * kDQ);
+        pp.g.n_qt = nqt;
+        dense_chunking(p.g.n_tiles, nqt, G, ix.units_per_cta, &pp.g.tiles_per_chunk, &chunks);
+        pp.g.chunks = chunks;
         pp.n_units = nqt * chunks;
-        pp.tau = ws.tau + q0;
-        pp.gbits = ws.gbits;
-        pp.words = (pp.tiles_per_chunk + 15) / 16;
-        ExtractParams x = extract_base(ix, q0, pp.nq, nqt);
-        x.tiles_per_chunk = pp.tiles_per_chunk;
+        pp.g.tau = ws.tau + q0;
+        pp.g.gbits = ws.gbits;
+        pp.g.words = (pp.g.tiles_per_chunk + 15) / 16;
+        ExtractParams x = extract_base(ix, q0, pp.g.nq, nqt);
+        x.tiles_per_chunk = pp.g.tiles_per_chunk;
         x.chunks = chunks;
-        x.words = pp.words;
+        x.words = pp.g.words;
         cudaError_t e = launch_dense_kernel(kp, f8, pp, 2, (int)min64(G, pp.n_units), st);
         if (e == cudaSuccess) e = launch_extract_any(kp, f8, x, false, st);
         if (e != cudaSuccess) return e;
@@ -957,28 +991,29 @@ cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, in
     const int S = (int)(2 * chunks);                // candidate slots per query
     if (S > ws.cand_slots) return cudaErrorInvalidValue;
     DenseParams p = dense_base(ix, 4);
-    p.tiles_per_chunk = tpc;
-    p.words = (tpc + 1) / 2;
-    p.gbits = ws.gbits;
+    p.g.tiles_per_chunk = tpc;
+    p.g.chunks = chunks;
+    p.g.words = (tpc + 1) / 2;
+    p.g.gbits = ws.gbits;
     for (int64_t qt0 = 0; qt0 < n_qt;) {
         const int64_t nqt = std::min(per, n_qt - qt0);
         const int64_t q0 = qt0 * kDQ;
         const bool first = qt0 == 0;
         qt0 += nqt;
         DenseParams pp = p;
-        pp.qpre = static_cast<const char *>(p.qpre) + q0 * kp * 2;
-        pp.nq = min64(nq - q0, nqt * kDQ);
-        pp.n_qt = nqt;
+        pp.g.qpre = static_cast<const char *>(p.g.qpre) + q0 * kp * 2;
+        pp.g.nq = min64(nq - q0, nqt * kDQ);
+        pp.g.n_qt = nqt;
         pp.n_units = nqt * chunks;
-        pp.cand = ws.cand + q0 * S;
+        pp.g.cand = ws.cand + q0 * S;
         cudaError_t e = launch_dense_kernel(kp, f8, pp, 4, (int)min64(G, pp.n_units), st);
         if (e == cudaSuccess && ev && first) e = cudaEventRecord(ev[0], st);
-        if (e == cudaSuccess) e = launch_seed_threshold_at(ix, q, q0, pp.nq, S, 32, kk, keep_best, st);
+        if (e == cudaSuccess) e = launch_seed_threshold_at(ix, q, q0, pp.g.nq, S, 32, kk, keep_best, st);
         if (e == cudaSuccess && ev && first) e = cudaEventRecord(ev[1], st);
-        ExtractParams x = extract_base(ix, q0, pp.nq, nqt);
+        ExtractParams x = extract_base(ix, q0, pp.g.nq, nqt);
         x.tiles_per_chunk = tpc;
         x.chunks = chunks;
-        x.words = pp.words;
+        x.words = pp.g.words;
         if (e == cudaSuccess) e = launch_extract_any(kp, f8, x, true, st);
         if (e != cudaSuccess) return e;
     }
@@ -995,10 +1030,11 @@ cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *o
     if (path == 0) {
         DenseParams p = dense_base(ix, 3);
         int64_t chunks = 0;
-        p.nq = nq;
-        p.n_qt = (nq + kDQ - 1) / kDQ;
-        dense_chunking(p.n_tiles, p.n_qt, num_sms(), ix.units_per_cta, &p.tiles_per_chunk, &chunks);
-        p.n_units = p.n_qt * chunks;
+        p.g.nq = nq;
+        p.g.n_qt = (nq + kDQ - 1) / kDQ;
+        dense_chunking(p.g.n_tiles, p.g.n_qt, num_sms(), ix.units_per_cta, &p.g.tiles_per_chunk, &chunks);
+        p.g.chunks = chunks;
+        p.n_units = p.g.n_qt * chunks;
         p.dump = out;
         return launch_dense_kernel(kp, f8, p, 3, (int)min64(num_sms(), p.n_units), st);
     }
@@ -1012,6 +1048,130 @@ cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *o
         default: return cudaErrorNotSupported;
     }
     return cudaGetLastError();
+}
+
+}  // namespace hn
+
+namespace hn {
+
+// ------------------------------------------------------------------ batched serving
+// One persistent one-pass scan over several groups (an index and its concatenated
+// queries each).  Every joined group keeps its own code map, candidate slots and
+// threshold; only the scan is shared, so that small groups fill the SMs together
+// instead of one full-GPU launch each.  A group joins when its index has the common
+// tile format and its code map holds the whole group in one pass.
+struct DenseMulti {
+    std::vector<const Index *> ix;
+    std::vector<DenseGroup> g;          // host copy of the descriptors
+    DenseGroup *dev = nullptr;          // device copy
+    int64_t n_units = 0;
+    int kp = 16;
+    bool f8 = false;
+};
+
+// Chunking of a joined group: the group's own one-pass chunking, with at least
+// kMultiMinTiles entry tiles a unit (many small groups share the SMs anyway).
+constexpr int64_t kMultiMinTiles = 16;
+
+static void multi_chunking(const Index &ix, int64_t nq, int64_t *tpc, int64_t *chunks) {
+    const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
+    onepass_tile_words(ix, (nq + kDQ - 1) / kDQ, tpc, chunks);
+    *tpc = std::min(n_tiles, std::max(*tpc, kMultiMinTiles));
+    *chunks = (n_tiles + *tpc - 1) / *tpc;
+}
+
+bool dense_multi_joinable(const Index &ix, int64_t nq, int kp, bool f8) {
+    if (!dense_scan_supported(ix) || ix.k_pad16 != kp || (ix.prefix == HN_PREFIX_FP8_E4M3) != f8 || nq < 1) return false;
+    int64_t tpc = 0, chunks = 0;
+    multi_chunking(ix, nq, &tpc, &chunks);
+    const int64_t n_qt = (nq + kDQ - 1) / kDQ;
+    return 2 * chunks <= ix.ws.cand_slots && chunks * 2 * ((tpc + 1) / 2) * n_qt * kDQ <= ix.ws.gbits_cap;
+}
+
+hn_status dense_multi_create(const std::vector<const Index *> &ixs, const std::vector<int64_t> &nqs,
+                             DenseMulti **out) {
+    *out = nullptr;
+    if (ixs.empty() || ixs.size() != nqs.size()) return fail(HN_ERR_INVALID_ARG, "dense_multi_create: no groups");
+    DenseMulti *m = new DenseMulti();
+    m->kp = ixs[0]->k_pad16;
+    m->f8 = ixs[0]->prefix == HN_PREFIX_FP8_E4M3;
+    for (size_t i = 0; i < ixs.size(); ++i) {
+        const Index &ix = *ixs[i];
+        if (!dense_multi_joinable(ix, nqs[i], m->kp, m->f8)) {
+            delete m;
+            return fail(HN_ERR_INVALID_ARG, "dense_multi_create: a group cannot join");
+        }
+        DenseGroup g{};
+        g.pre = m->f8 ? (const void *)ix.pre8 : (const void *)ix.pre16;
+        g.qpre = ix.ws.qpre16;
+        g.n = ix.n;
+        g.n_tiles = ix.n_tiles * (kTileE / kDE);
+        g.nq = nqs[i];
+        g.n_qt = (nqs[i] + kDQ - 1) / kDQ;
+        multi_chunking(ix, nqs[i], &g.tiles_per_chunk, &g.chunks);
+        g.unit0 = m->n_units;
+        g.cand = ix.ws.cand;
+        g.gbits = ix.ws.gbits;
+        g.words = (g.tiles_per_chunk + 1) / 2;
+        g.code_inv = ix.code_inv;
+        m->n_units += g.n_qt * g.chunks;
+        m->ix.push_back(&ix);
+        m->g.push_back(g);
+    }
+    cudaError_t e = cudaMalloc(&m->dev, sizeof(DenseGroup) * m->g.size());
+    if (e == cudaSuccess) e = cudaMemcpy(m->dev, m->g.data(), sizeof(DenseGroup) * m->g.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev);
+        delete m;
+        return cuda_fail(e, "dense_multi_create");
+    }
+    *out = m;
+    return HN_OK;
+}
+
+void dense_multi_destroy(DenseMulti *m) {
+    if (!m) return;
+    cudaFree(m->dev);
+    delete m;
+}
+
+template <int KP, bool F8>
+static cudaError_t launch_multi_kp(const DenseParams &p, int grid, cudaStream_t st) {
+    k_dense_scan<KP, 4, F8, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t dense_multi_scan(const DenseMulti *m, cudaStream_t st) {
+    cudaError_t e = dense_init();
+    if (e != cudaSuccess) return e;
+    DenseParams p{};
+    p.groups = m->dev;
+    p.n_groups = (int32_t)m->g.size();
+    p.n_units = m->n_units;
+    p.code_base = code_base();
+    p.wait_ns = kWaitLimitNs;
+    p.status = m->ix[0]->ws.status;   // a timeout is reported through the first group's status word
+    const int grid = (int)min64(num_sms(), m->n_units);
+    switch (m->kp) {
+        case 16: return m->f8 ? launch_multi_kp<16, true>(p, grid, st) : launch_multi_kp<16, false>(p, grid, st);
+        case 32: return m->f8 ? launch_multi_kp<32, true>(p, grid, st) : launch_multi_kp<32, false>(p, grid, st);
+        case 64: return m->f8 ? launch_multi_kp<64, true>(p, grid, st) : launch_multi_kp<64, false>(p, grid, st);
+    }
+    return cudaErrorNotSupported;
+}
+
+// Group gi after the shared scan: the threshold from its candidates, then its survivors
+// from its code map (queries q, HN-normalised, as prepared).
+cudaError_t dense_multi_post(const DenseMulti *m, int gi, const float *q, cudaStream_t st) {
+    const Index &ix = *m->ix[gi];
+    const DenseGroup &g = m->g[gi];
+    cudaError_t e = launch_seed_threshold_at(ix, q, 0, g.nq, (int)(2 * g.chunks), 32, 1, false, st);
+    if (e != cudaSuccess) return e;
+    ExtractParams x = extract_base(ix, 0, g.nq, g.n_qt);
+    x.tiles_per_chunk = g.tiles_per_chunk;
+    x.chunks = g.chunks;
+    x.words = g.words;
+    return launch_extract_any(m->kp, m->f8, x, true, st);
 }
 
 }  // namespace hn

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "hn.h"
 
@@ -257,5 +258,15 @@ int64_t dense_cand_slots(const Index &ix, int64_t nq);
 int64_t dense_gbits_words(const Index &ix, int64_t nq, bool onepass, int64_t limit_bytes);
 // kernel launches of the dense steps after Phase 1 / the threshold (see hn_dense.cu)
 int64_t dense_phase2_launches(const Index &ix, int64_t nq, bool onepass);
+// Batched serving: one persistent one-pass dense scan over several (index, queries) groups
+// that share the tile format (hn_dense.cu).  Create after prepare_search has sized every
+// group's scratch; the scan needs every group's query prep done, and dense_multi_post then
+// gives each group its threshold and survivors.
+struct DenseMulti;
+bool dense_multi_joinable(const Index &ix, int64_t nq, int kp, bool f8);
+hn_status dense_multi_create(const std::vector<const Index *> &ixs, const std::vector<int64_t> &nqs, DenseMulti **out);
+void dense_multi_destroy(DenseMulti *m);
+cudaError_t dense_multi_scan(const DenseMulti *m, cudaStream_t s);
+cudaError_t dense_multi_post(const DenseMulti *m, int gi, const float *q, cudaStream_t s);
 
 }  // namespace hn

@@ -3,11 +3,15 @@
 // scan kind and dense work-unit size per index.
 //
 // hn_search_multi groups the batches by index and concatenates each group's
-// queries, so that small batches share the dense scan's 256-query units.  Each
-// group runs the search pipeline on a stream of its own; the whole set is
-// captured once into a CUDA graph (fork / join across the group streams) and
-// the instantiated graph is replayed while the same set of batches comes back.
-// Per-batch completion times come from events recorded inside the graph.
+// queries, so that small batches share the dense scan's 256-query units.  The
+// groups whose indexes share the dense tile format run their one-pass scans as
+// ONE persistent launch over all of them (work units numbered group by group),
+// with query preparation before it and each group's threshold, survivor
+// extraction and rescore after it on the group's own stream; any other group
+// runs the whole search pipeline on its stream.  The set is captured once into
+// a CUDA graph (fork / join across the streams) and the instantiated graph is
+// replayed while the same set of batches comes back.  Per-batch completion
+// times come from events recorded inside the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -33,6 +37,8 @@ struct Group {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;   // join dependency
     cudaEvent_t stamp = nullptr;  // completion time (a real event record, also inside a graph)
+    int joined = -1;              // position in the shared one-pass scan, or -1
+    cudaEvent_t prepped = nullptr;  // joined: query preparation done
 };
 
 struct Plan {
@@ -41,7 +47,8 @@ struct Plan {
     std::vector<int32_t> batch_group;
     std::vector<uint64_t> gens;          // workspace generation of each group's index at capture
     cudaStream_t cap_stream = nullptr;
-    cudaEvent_t start = nullptr, fork = nullptr;
+    cudaEvent_t start = nullptr, fork = nullptr, scanned = nullptr;
+    DenseMulti *dm = nullptr;            // the shared one-pass scan of the joined groups
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool valid = false;
@@ -58,8 +65,11 @@ static void release_plan(Plan &p) {
         if (g.st) cudaStreamDestroy(g.st);
         if (g.done) cudaEventDestroy(g.done);
         if (g.stamp) cudaEventDestroy(g.stamp);
+        if (g.prepped) cudaEventDestroy(g.prepped);
     }
     p.groups.clear();
+    dense_multi_destroy(p.dm);
+    p.dm = nullptr;
     if (p.exec) cudaGraphExecDestroy(p.exec);
     if (p.graph) cudaGraphDestroy(p.graph);
     p.exec = nullptr;
@@ -88,16 +98,7 @@ static hn_status enqueue_plan(Plan &p, const hn_batch *b, cudaStream_t s0, bool 
     const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     HN_CUDA(cudaEventRecordWithFlags(p.start, s0, rec));
     HN_CUDA(cudaEventRecord(p.fork, s0));
-    for (Group &g : p.groups) {
-        HN_CUDA(cudaStreamWaitEvent(g.st, p.fork, 0));
-        for (size_t j = 0; j < g.bids.size(); ++j) {
-            const hn_batch &x = b[g.bids[j]];
-            if (x.nq)
-                HN_CUDA(cudaMemcpyAsync(g.qcat + g.off[j] * kD, x.q, sizeof(float) * kD * x.nq,
-                                        cudaMemcpyDeviceToDevice, g.st));
-        }
-        hn_status st = enqueue_search(*g.ix, g.qcat, g.Q, g.scan, nullptr, 4, g.icat, g.scat, false, g.st);
-        if (st != HN_OK) return st;
+    auto finish = [&](Group &g) -> hn_status {
         for (size_t j = 0; j < g.bids.size(); ++j) {
             const hn_batch &x = b[g.bids[j]];
             if (!x.nq) continue;
@@ -108,8 +109,50 @@ static hn_status enqueue_plan(Plan &p, const hn_batch *b, cudaStream_t s0, bool 
         }
         HN_CUDA(cudaEventRecordWithFlags(g.stamp, g.st, rec));
         HN_CUDA(cudaEventRecord(g.done, g.st));
-        HN_CUDA(cudaStreamWaitEvent(s0, g.done, 0));
+        return HN_OK;
+    };
+    for (Group &g : p.groups) {
+        HN_CUDA(cudaStreamWaitEvent(g.st, p.fork, 0));
+        for (size_t j = 0; j < g.bids.size(); ++j) {
+            const hn_batch &x = b[g.bids[j]];
+            if (x.nq)
+                HN_CUDA(cudaMemcpyAsync(g.qcat + g.off[j] * kD, x.q, sizeof(float) * kD * x.nq,
+                                        cudaMemcpyDeviceToDevice, g.st));
+        }
+        if (g.joined >= 0) {
+            // the first steps of the search pipeline; the scan is shared (below)
+            Workspace &ws = g.ix->ws;
+            HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), g.st));
+            HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), g.st));
+            HN_CUDA(launch_query_prep(*g.ix, g.qcat, g.Q, 1.f, g.st));
+            HN_CUDA(cudaEventRecord(g.prepped, g.st));
+            continue;
+        }
+        hn_status st = enqueue_search(*g.ix, g.qcat, g.Q, g.scan, nullptr, 4, g.icat, g.scat, false, g.st);
+        if (st != HN_OK) return st;
+        st = finish(g);
+        if (st != HN_OK) return st;
     }
+    if (p.dm) {
+        // one persistent one-pass scan over every joined group, then each group's own steps
+        for (Group &g : p.groups)
+            if (g.joined >= 0) HN_CUDA(cudaStreamWaitEvent(s0, g.prepped, 0));
+        HN_CUDA(dense_multi_scan(p.dm, s0));
+        HN_CUDA(cudaEventRecord(p.scanned, s0));
+        for (Group &g : p.groups) {
+            if (g.joined < 0) continue;
+            Workspace &ws = g.ix->ws;
+            HN_CUDA(cudaStreamWaitEvent(g.st, p.scanned, 0));
+            HN_CUDA(dense_multi_post(p.dm, g.joined, g.qcat, g.st));
+            HN_CUDA(launch_rescore(*g.ix, g.qcat, g.Q, g.icat, g.scat, g.st));
+            HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, g.st));
+            HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                    g.st));
+            hn_status st = finish(g);
+            if (st != HN_OK) return st;
+        }
+    }
+    for (Group &g : p.groups) HN_CUDA(cudaStreamWaitEvent(s0, g.done, 0));
     return HN_OK;
 }
 
@@ -153,6 +196,32 @@ static hn_status build_plan(Plan &p, const hn_batch *b, int32_t nb, const std::m
     for (int32_t i = 0; i < nb; ++i) p.batch_group[i] = -1;
     for (size_t gi = 0; gi < p.groups.size(); ++gi)
         for (int32_t bi : p.groups[gi].bids) p.batch_group[bi] = (int32_t)gi;
+    // the dense one-pass groups that share the first such group's tile format run one shared scan
+    std::vector<const Index *> jix;
+    std::vector<int64_t> jnq;
+    int kp = 0;
+    bool f8 = false;
+    for (Group &g : p.groups) {
+        if (g.scan != HN_SCAN_DENSE) continue;
+        if (kp == 0) {
+            kp = g.ix->k_pad16;
+            f8 = g.ix->prefix == HN_PREFIX_FP8_E4M3;
+        }
+        if (dense_multi_joinable(*g.ix, g.Q, kp, f8)) {
+            g.joined = (int)jix.size();
+            jix.push_back(g.ix);
+            jnq.push_back(g.Q);
+        }
+    }
+    if (jix.size() >= 2) {
+        hn_status st = dense_multi_create(jix, jnq, &p.dm);
+        if (st != HN_OK) return st;
+        for (Group &g : p.groups)
+            if (g.joined >= 0) HN_CUDA(cudaEventCreateWithFlags(&g.prepped, cudaEventDisableTiming));
+        if (!p.scanned) HN_CUDA(cudaEventCreateWithFlags(&p.scanned, cudaEventDisableTiming));
+    } else {
+        for (Group &g : p.groups) g.joined = -1;
+    }
     p.gens.clear();
     for (Group &g : p.groups) p.gens.push_back(g.ix->ws.gen);
     if (!p.cap_stream) HN_CUDA(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
@@ -263,6 +332,9 @@ hn_status hn_search_multi(const hn_batch *batches, int32_t nb, const hn_multi_op
     }
     if (stats) {
         stats->n_groups = (int32_t)p.groups.size();
+        stats->joined = p.dm ? (int32_t)std::count_if(p.groups.begin(), p.groups.end(),
+                                                      [](const Group &g) { return g.joined >= 0; })
+                             : 0;
         stats->graph_replayed = replayed ? 1 : 0;
         stats->reruns = reruns;
         std::vector<float> gms(p.groups.size(), 0.f);

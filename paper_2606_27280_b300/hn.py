@@ -83,7 +83,7 @@ class MultiStats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("n_batches", ctypes.c_int32), ("n_groups", ctypes.c_int32),
                 ("graph_replayed", ctypes.c_int32), ("reruns", ctypes.c_int32), ("ms_total", ctypes.c_float),
                 ("batch_ms_p50", ctypes.c_float), ("batch_ms_p99", ctypes.c_float), ("batch_ms_max", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("survivors", ctypes.c_int64)]
+                ("joined", ctypes.c_int32), ("survivors", ctypes.c_int64)]
 
 
 TUNE_MAX = 16

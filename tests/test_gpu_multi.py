@@ -92,3 +92,41 @@ def test_autotune_keeps_results_exact(hn):
         res = ix.search(to_dev(q), stats=True)
         assert_parity(res.idx, res.sim, o_idx, o_sim)
         assert res.stats["scan"] == (2 if 1500 >= r["dense_min_q"] else 1)
+
+
+def test_shared_one_pass_scan_across_indexes(hn):
+    """Four BF16 indexes (K 8 and 16 share the padded width 16; two alphas) take one shared
+    persistent one-pass scan; an FP32 index (stream scan) and an FP8 index (another tile
+    format) keep their own pipelines.  Every batch equals the oracle, with and without the
+    graph, and on replay."""
+    specs = [(40000, 8, 1 / 32, 1, 41), (25000, 16, 1 / 8, 1, 42), (30011, 16, 1 / 32, 1, 43),
+             (18000, 8, 1 / 8, 1, 44), (15000, 16, 1 / 8, 0, 45), (20000, 16, 1 / 8, 2, 46)]
+    indexes, data = [], []
+    for n, k, a, prefix, seed in specs:
+        w = hn_synth.make_workload(n, 0, n // 5, seed=seed)
+        db = oracle.normalize(w.db_raw, k, a)
+        indexes.append(hn.Index(to_dev(db), k, a, prefix=prefix))
+        data.append((w, db, k, a))
+    try:
+        rng = np.random.default_rng(47)
+        batches, expected = [], []
+        for b in range(30):
+            g = b % len(specs)
+            nq = int(rng.integers(300, 700)) if g != 4 else int(rng.integers(1, 40))   # FP32 group: stream scan
+            w, db, k, a = data[g]
+            qr, _ = hn_synth.queries_from(w.db_raw, nq, seed=200 + b)
+            q = oracle.normalize(qr, k, a)
+            batches.append((indexes[g], to_dev(q), torch.empty(nq, dtype=torch.int64, device="cuda"),
+                            torch.empty(nq, dtype=torch.float64, device="cuda")))
+            expected.append(oracle.search(db, q))
+        for use_graph in (True, True, False):
+            for _, _, oi, os_ in batches:
+                oi.fill_(-1)
+                os_.fill_(0)
+            st = hn.search_multi(batches, use_graph=use_graph)
+            assert st["n_groups"] == 6 and st["joined"] == 4, st
+            _check_all(batches, expected)
+        assert st["survivors"] > 0
+    finally:
+        for ix in indexes:
+            ix.close()

@@ -124,7 +124,14 @@ typedef struct hn_search_opts {
                              while its prefix bound reaches the best certified full score so far,
                              so most survivors cost a read of K values instead of the whole row.
                              Same result either way */
-    int32_t reserved[3];  /* must be zero */
+    int32_t test_stall;   /* failure-path test hook, 0 in normal use.  1: in every dense-scan launch
+                             of this call, each CTA's copy producer stops after the CTA's first work
+                             unit, so the MMA warps wait for a query copy that never comes; that
+                             wait runs out after wait_limit_ns, the CTA raises its abort flag, the
+                             copies and MMAs in flight drain, tensor memory is freed and the call
+                             returns HN_ERR_TIMEOUT.  Needs a dense scan, no seed and
+                             1e3 <= wait_limit_ns <= 1e7 (HN_ERR_INVALID_ARG otherwise) */
+    int32_t reserved[2];  /* must be zero */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */

@@ -454,11 +454,16 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         return fail(HN_ERR_INVALID_ARG, "bad scan kind");
     if (scan != HN_SCAN_STREAM && !dense_scan_supported(ix))
         return fail(HN_ERR_UNSUPPORTED, "dense scan needs a BF16 or FP8 prefix index");
+    if (o.test_stall && (scan == HN_SCAN_STREAM || o.seed))
+        return fail(HN_ERR_INVALID_ARG, "test_stall needs a dense scan without a proposal seed");
     if (o.scratch_limit < 0) return fail(HN_ERR_INVALID_ARG, "scratch_limit < 0");
     if (o.wait_limit_ns != 0 && (o.wait_limit_ns < 1000 || o.wait_limit_ns > 10000000000ull))
         return fail(HN_ERR_INVALID_ARG, "need wait_limit_ns = 0 or 1e3 <= wait_limit_ns <= 1e10");
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.test_stall != 0 && o.test_stall != 1) return fail(HN_ERR_INVALID_ARG, "test_stall must be 0 or 1");
+    if (o.test_stall && (o.wait_limit_ns == 0 || o.wait_limit_ns > 10000000ull))
+        return fail(HN_ERR_INVALID_ARG, "test_stall needs 1e3 <= wait_limit_ns <= 1e7");
     if (o.best_first != 0 && o.best_first != 1) return fail(HN_ERR_INVALID_ARG, "best_first must be 0 or 1");
     if (stats) {
         memset(stats, 0, sizeof(*stats));
@@ -481,9 +486,11 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         hn_status st = prepare_search(ix, nq, scan, cap, nn, o.seed != nullptr, o.scratch_limit);
         if (st != HN_OK) return st;
         ws.wait_ns = o.wait_limit_ns;
+        ws.stall = o.test_stall;
         st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale,
                             o.best_first != 0);
         ws.wait_ns = 0;
+        ws.stall = 0;
         if (st != HN_OK) {
             ws.gbits_limit = 0;
             return st;

@@ -83,9 +83,11 @@ struct DenseGroup {
     const float *tau;
     unsigned long long *cand;     // [nq][2 * chunks] PHASE 1: (best score, 64-entry segment id), PHASE 4:
                                   //   (best group score, 32-entry group id) per (query, chunk, entry half)
-    uint32_t *gbits;              // [chunk][half][word][n_qt * 256] group map: PHASE 2 passing-group bits,
-                                  //   16 tiles a word; PHASE 4 group codes, 2 tiles (4 codes) a word
-    int64_t words;                // words per (chunk, half): ceil(tiles_per_chunk / 16), PHASE 4: / 2
+    uint32_t *gbits;              // group map: PHASE 2 [chunk][half][word][n_qt * 256] passing-group bits,
+                                  //   16 tiles a word; PHASE 4 [chunk][tile][n_qt * 256] the 4 group codes
+                                  //   of a tile in a word
+    int64_t words;                // PHASE 2: words per (chunk, half), ceil(tiles_per_chunk / 16);
+                                  //   PHASE 4: words per chunk, tiles_per_chunk
     float code_inv;               // PHASE 4: the group code (hn_internal.cuh)
 };
 
@@ -98,6 +100,7 @@ struct DenseParams {
     float *dump;                  // PHASE 3: [nq][n] every FP32 score (Phase-2 arithmetic)
     uint64_t wait_ns;             // limit of every main-loop wait (the drains keep kWaitLimitNs)
     int32_t *status;
+    int32_t stall;                // failure-path test: the producer stops after each CTA's first unit
 };
 constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
 constexpr int kDE = 128;   // entries per B tile (MMA N)
@@ -179,14 +182,16 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::kStages; ++i) {
             mbar_init(smem_u32(&b_full[i]), 1);
-            // one arrival per tile of the stage (FP8: per tile and epilogue warp)
-            mbar_init(smem_u32(&b_empty[i]), F8 ? C::kTPS * kEpiWarps : C::kTPS);
+            // one arrival per tile of the stage (FP8: per tile and epilogue warp reading it; the
+            // one-pass form's epilogue gives each tile to half the epilogue warps)
+            mbar_init(smem_u32(&b_empty[i]), F8 ? C::kTPS * (PHASE == 4 ? kEpiWarps / 2 : kEpiWarps) : C::kTPS);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&a_full[i]), 1);
             mbar_init(smem_u32(&a_empty[i]), kIssuers);  // every issuer commits at the end of a unit
             mbar_init(smem_u32(&acc_full[i]), 1);
-            mbar_init(smem_u32(&acc_empty[i]), kEpiWarps);  // one elected arrive per epilogue warp
+            // one elected arrive per epilogue warp reading the buffer (one-pass form: half of them)
+            mbar_init(smem_u32(&acc_empty[i]), PHASE == 4 ? kEpiWarps / 2 : kEpiWarps);
         }
         for (int i = 0; i < kIssuers; ++i) mbar_init(smem_u32(&drain[i]), 1);
         *abort_flag = 0;
@@ -227,6 +232,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                     ++b_issued;
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
                 }
+                // failure-path test: the next unit's query copy never comes, so the MMA
+                // warps' wait for it runs out and the CTA takes the abort path
+                if (p.stall) break;
             }
             // copies still in flight must land before this CTA's shared memory goes away:
             // slot s last received copy number c = s + kStages * lap, lap = (issued - 1 - s) / kStages,
@@ -298,6 +306,94 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             umma_commit(smem_u32(&drain[me]));
             mbar_drain(smem_u32(&drain[me]), 0, kWaitLimitNs);
         }
+    } else if (PHASE == 4) {
+        // ------------------------------------------------------------ epilogue, one-pass form
+        // Two warp groups, one per accumulator buffer (tile parity): while one group reduces
+        // its tile, the other loads the next, so the TMEM loads and the max trees of an SM
+        // sub-partition overlap instead of running in lockstep.  Warp (group, A tile, TMEM
+        // lane quarter) reads all 128 entry columns of its 32 query rows (two 64-column
+        // loads), so it forms the four group codes of the tile -- one word per (query, tile)
+        // -- and the best group it has seen in the chunk (candidate slot 2 chunk + group).
+        // FP8: the group's largest raw accumulator A bounds its scores u_i = RN(acc_i s_i/256
+        // + b_i) from above by max(RU(A smax + bmax), RU(A smin + bmax)) with the group's scale
+        // range and largest error term (k_f8_group_bounds).
+        const int ew = warp - kEpiWarp0;
+        const int quarter = warp & 3;             // TMEM lanes this warp may read: 32*quarter ..
+        const int grp = ew >> 3;                  // accumulator buffer (tile parity) this warp serves
+        const int sub = (ew >> 2) & 1;            // query A tile: accumulator columns 128*sub ..
+        const int row = sub * kTileQ + quarter * 32 + lane;
+        const bool releaser = (ew & 7) == 0 && lane == 0;  // hands this group's B stages back
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        uint32_t stage = 0, sphase = 0;
+        uint32_t g = 0;  // tile counter of this CTA: buffer g & 1, its use number g >> 1
+        bool ok = true;
+        for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
+            const DenseGroup &gr = MULTI ? group_of(p, u) : p.g;
+            const int64_t qt = (u - gr.unit0) % gr.n_qt, ch = (u - gr.unit0) / gr.n_qt;
+            const int32_t t0 = (int32_t)(ch * gr.tiles_per_chunk);
+            const int32_t t1 = (int32_t)min64(gr.n_tiles, (int64_t)t0 + gr.tiles_per_chunk);
+            const int64_t q = qt * kDQ + row;
+            const bool qvalid = q < gr.nq;
+            float best = -INFINITY;
+            int32_t bgid = -1;  // the 32-entry group of `best`
+            uint32_t *gb = gr.gbits + ch * gr.words * (gr.n_qt * kDQ) + q;
+            const int32_t n32 = (int32_t)gr.n;
+            for (int32_t tt = t0; ok && tt < t1; tt += C::kTPS) {
+                const int nt = t1 - tt < C::kTPS ? t1 - tt : C::kTPS;
+                for (int j = 0; j < nt; ++j, ++g) {
+                    const uint32_t buf = g & 1u;
+                    if ((int)buf != grp) continue;
+                    // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag,
+                                                           p.wait_ns));
+                    if (!ok) break;
+                    tc_fence_after();
+                    // this tile's MMAs are done with the stage; the last tile of a short stage
+                    // also arrives for the tiles the stage did not hold
+                    const uint32_t rel = j == nt - 1 ? 1 + C::kTPS - nt : 1;
+                    if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                    const int32_t t = tt + j;
+                    float v[64];
+                    tmem_ld64(tmem + buf * 256 + sub * kDE + lane_addr, v);
+                    float s0 = fmaxf(max16(v), max16(v + 16)), s1 = fmaxf(max16(v + 32), max16(v + 48));
+                    tmem_ld64(tmem + buf * 256 + sub * kDE + 64 + lane_addr, v);
+                    // the scores are in registers: hand the accumulator back to the MMA warp now
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                    float s2 = fmaxf(max16(v), max16(v + 16)), s3 = fmaxf(max16(v + 32), max16(v + 48));
+                    if (F8) {
+                        const float4 *gbd = reinterpret_cast<const float4 *>(smem + stage * C::kStageBytes +
+                                                                             j * C::kB + f8_group_off(KP));
+                        const float4 b0 = gbd[0], b1 = gbd[1], b2 = gbd[2], b3 = gbd[3];
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                        s0 = fmaxf(__fmaf_ru(s0, b0.x, b0.z), __fmaf_ru(s0, b0.y, b0.z));
+                        s1 = fmaxf(__fmaf_ru(s1, b1.x, b1.z), __fmaf_ru(s1, b1.y, b1.z));
+                        s2 = fmaxf(__fmaf_ru(s2, b2.x, b2.z), __fmaf_ru(s2, b2.y, b2.z));
+                        s3 = fmaxf(__fmaf_ru(s3, b3.x, b3.z), __fmaf_ru(s3, b3.y, b3.z));
+                    }
+                    // threshold candidate: the best group (lowest on ties) holding a real entry
+                    const float m01 = fmaxf(s0, s1), m23 = fmaxf(s2, s3), m = fmaxf(m01, m23);
+                    const int32_t gid = t * 4 + (m01 >= m23 ? (s1 > s0 ? 1 : 0) : (s3 > s2 ? 3 : 2));
+                    if (m > best && gid * 32 < n32) {
+                        best = m;
+                        bgid = gid;
+                    }
+                    // the tile's word: codes of groups 0-3 (byte permutes of the low bytes); a
+                    // streaming store, so that the map does not evict the prefix from L2
+                    const uint32_t c01 = __byte_perm(code_group_bits(s0, gr.code_inv, p.code_base),
+                                                     code_group_bits(s1, gr.code_inv, p.code_base), 0x0040);
+                    const uint32_t c23 = __byte_perm(code_group_bits(s2, gr.code_inv, p.code_base),
+                                                     code_group_bits(s3, gr.code_inv, p.code_base), 0x0040);
+                    __stcs(gb + (int64_t)(t - t0) * (gr.n_qt * kDQ), __byte_perm(c01, c23, 0x5410));
+                }
+                if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
+            }
+            if (!ok) break;
+            // one writer per (query, chunk, group): every slot written
+            if (qvalid) gr.cand[q * (2 * gr.chunks) + 2 * ch + grp] = bgid >= 0 ? pack_best(best, (uint32_t)bgid) : 0ull;
+        }
     } else {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - kEpiWarp0;         // 0 .. kEpiWarps-1
@@ -322,9 +418,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             const float thr = (PHASE == 2 && qvalid) ? gr.tau[q] : INFINITY;
 
             float best = -INFINITY;
-            int32_t bseg = -1;   // PHASE 1: 64-entry segment of `best`; PHASE 4: its 32-entry group
-            uint32_t gword = 0;  // PHASE 2: passing-group bits of the current 16 tiles; PHASE 4: codes of 2 tiles
-            uint32_t *gb = (PHASE == 2 || PHASE == 4) ? gr.gbits + (ch * 2 + half) * gr.words * (gr.n_qt * kDQ) + q
+            int32_t bseg = -1;   // PHASE 1: the 64-entry segment of `best`
+            uint32_t gword = 0;  // PHASE 2: passing-group bits of the current 16 tiles
+            uint32_t *gb = PHASE == 2 ? gr.gbits + (ch * 2 + half) * gr.words * (gr.n_qt * kDQ) + q
                                                       : nullptr;
             const int32_t n32 = (int32_t)gr.n;
             const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
@@ -379,40 +475,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
-                        if (PHASE == 4) {
-                            // one-pass form: the largest score of each 32-entry group.  FP8: the
-                            // group's largest raw accumulator A bounds its scores u_i = RN(acc_i s_i/256
-                            // + b_i) from above by max(RU(A smax + bmax), RU(A smin + bmax)) with the
-                            // group's scale range and largest error term (k_f8_group_bounds).
-                            float g0 = fmaxf(max16(v), max16(v + 16)), g1 = fmaxf(max16(v + 32), max16(v + 48));
-                            if (F8) {
-                                const float4 *gbd = reinterpret_cast<const float4 *>(
-                                                        smem + stage * C::kStageBytes + j * C::kB + f8_group_off(KP)) +
-                                                    half * 2;
-                                const float4 b0 = gbd[0], b1 = gbd[1];
-                                __syncwarp();
-                                if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
-                                g0 = fmaxf(__fmaf_ru(g0, b0.x, b0.z), __fmaf_ru(g0, b0.y, b0.z));
-                                g1 = fmaxf(__fmaf_ru(g1, b1.x, b1.z), __fmaf_ru(g1, b1.y, b1.z));
-                            }
-                            // threshold candidate: the best group of this (chunk, entry half)
-                            const float m = fmaxf(g0, g1);
-                            if (m > best && (t < full_tiles || e0 < n32)) {
-                                best = m;
-                                bseg = (t * 2 + half) * 2 + (g1 > g0 ? 1 : 0);
-                            }
-                            // codes of the two groups; a word holds tiles 2w and 2w + 1 of the chunk
-                            const int32_t ti = t - t0;
-                            // (byte permutes: the low bytes of the two bit patterns, then bytes
-                            // 0-1 of the even tile's word with bytes 0-1 of the odd tile's)
-                            const uint32_t c01 = __byte_perm(code_group_bits(g0, gr.code_inv, p.code_base),
-                                                             code_group_bits(g1, gr.code_inv, p.code_base), 0x0040);
-                            gword = (ti & 1) ? __byte_perm(gword, c01, 0x5410) : c01;
-                            // streaming store: the code map (one byte per 32 scores) should not evict
-                            // the prefix tiles the other CTAs and the extraction read from L2
-                            if ((ti & 1) || t == t1 - 1) __stcs(gb + (int64_t)(ti >> 1) * (gr.n_qt * kDQ), gword);
-                            continue;
-                        }
                         if (F8) {
                             // u = fma(acc, s_i / 256, b_i): one rounding, packed pairs
                             const float4 *s4 = reinterpret_cast<const float4 *>(esc) + half * 16;
@@ -458,7 +520,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             }
             if (!ok) break;
             // one writer per (query, chunk, entry half): no atomics, every slot written
-            if ((PHASE == 1 || PHASE == 4) && qvalid)
+            if (PHASE == 1 && qvalid)
                 gr.cand[q * (2 * gr.chunks) + 2 * ch + half] = bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
         }
     }
@@ -616,11 +678,12 @@ __global__ void __launch_bounds__(256) k_dense_extract(const ExtractParams x) {
     if (lane == 0 && scored) atomicAdd(reinterpret_cast<unsigned long long *>(x.counters + CT_GROUPS), scored);
 }
 
-// The same step for the one-pass form: the map holds an 8-bit code of every group's
-// largest score (4 codes a word: tiles 2w and 2w + 1 of the chunk, two groups each),
-// and a group is scored when its code reaches code(tau_q) (a non-decreasing code, so
-// every group whose largest score reaches tau_q is among them).  __vcmpgeu4 tests the
-// four codes of a word at once.
+// The same step for the one-pass form: the map holds one word per (query, tile) with
+// the 8-bit codes of the tile's four 32-entry groups' largest scores, and a group is
+// scored when its code reaches code(tau_q) (a non-decreasing code, so every group whose
+// largest score reaches tau_q is among them); __vcmpgeu4 tests the four codes of a word
+// at once.  The words are read with the streaming hint, so that the map (read once)
+// leaves the prefix, which the visited groups gather, in L2.
 template <int KP, bool F8>
 __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams x) {
     const int lane = threadIdx.x & 31;
@@ -632,43 +695,39 @@ __global__ void __launch_bounds__(256) k_dense_extract_codes(const ExtractParams
     const int64_t c = blockIdx.y;  // this block's entry chunk
     const int64_t t0 = c * x.tiles_per_chunk;
     const int64_t nt = min64(x.n_tiles - t0, x.tiles_per_chunk);
-    const int64_t nw = (nt + 1) / 2;
-    for (int h = 0; h < 2; ++h) {
-        const uint32_t *gw = x.gbits + (c * 2 + h) * x.words * x.q_pad;
-        for (int64_t w0 = 0; w0 < nw; w0 += 8) {
-            uint32_t wv[8];
+    const uint32_t *gw = x.gbits + c * x.words * x.q_pad;
+    for (int64_t w0 = 0; w0 < nt; w0 += 8) {
+        // 8 independent coalesced loads in flight; most codes fail
+        uint32_t wv[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nw) ? __ldcs(gw + (w0 + i) * x.q_pad + q) : 0u;
+        for (int i = 0; i < 8; ++i) wv[i] = (qv && w0 + i < nt) ? __ldcs(gw + (w0 + i) * x.q_pad + q) : 0u;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t w = w0 + i;
-                // the top bit of every passing code's byte; the second tile of a chunk's last
-                // word exists only for an even tile count, and absent words pass nothing
-                uint32_t word = (qv && w < nw) ? (__vcmpgeu4(wv[i], ct4) & 0x80808080u) : 0u;
-                if (2 * w + 1 >= nt) word &= 0x00008080u;
-                unsigned pend = __ballot_sync(0xffffffffu, word != 0u);
-                while (pend) {
-                    const int o = __ffs(pend) - 1;
-                    pend &= pend - 1;
-                    uint32_t wo = __shfl_sync(0xffffffffu, word, o);
-                    const float to = __shfl_sync(0xffffffffu, tau, o);
-                    const int64_t qo = q - lane + o;
-                    const float *qp = x.qpre32 + qo * KP;
-                    while (wo) {
-                        const int b = (__ffs(wo) - 1) >> 3;  // code byte: tile 2w + b / 2, group b % 2
-                        wo &= wo - 1;
-                        ++scored;
-                        const int64_t e = (t0 + w * 2 + (b >> 1)) * kDE + h * 64 + (b & 1) * 32 + lane;
-                        const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
-                        const unsigned hb = __ballot_sync(0xffffffffu, hit);
-                        if (hb) {
-                            int base = 0;
-                            if (lane == o) base = atomicAdd(x.count + qo, __popc(hb));
-                            base = __shfl_sync(0xffffffffu, base, o);
-                            if (hit) {
-                                const int slot = base + __popc(hb & ((1u << lane) - 1u));
-                                if (slot < x.cap) x.bucket[qo * x.cap + slot] = (int32_t)e;
-                            }
+        for (int i = 0; i < 8; ++i) {
+            const int64_t w = w0 + i;  // the tile t0 + w
+            // the top bit of every passing code's byte; absent words pass nothing
+            const uint32_t word = (qv && w < nt) ? (__vcmpgeu4(wv[i], ct4) & 0x80808080u) : 0u;
+            unsigned pend = __ballot_sync(0xffffffffu, word != 0u);
+            while (pend) {
+                const int o = __ffs(pend) - 1;
+                pend &= pend - 1;
+                uint32_t wo = __shfl_sync(0xffffffffu, word, o);
+                const float to = __shfl_sync(0xffffffffu, tau, o);
+                const int64_t qo = q - lane + o;
+                const float *qp = x.qpre32 + qo * KP;
+                while (wo) {
+                    const int b = (__ffs(wo) - 1) >> 3;  // code byte = group of the tile
+                    wo &= wo - 1;
+                    ++scored;
+                    const int64_t e = (t0 + w) * kDE + b * 32 + lane;
+                    const bool hit = e < x.n && group_entry_score<KP, F8>(x, e, qp) >= to;
+                    const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                    if (hb) {
+                        int base = 0;
+                        if (lane == o) base = atomicAdd(x.count + qo, __popc(hb));
+                        base = __shfl_sync(0xffffffffu, base, o);
+                        if (hit) {
+                            const int slot = base + __popc(hb & ((1u << lane) - 1u));
+                            if (slot < x.cap) x.bucket[qo * x.cap + slot] = (int32_t)e;
                         }
                     }
                 }
@@ -810,10 +869,22 @@ static int64_t gbits_words(int64_t n_tiles, int64_t n_qt, int G, int upc) {
 }
 
 // One-pass form: the chunking is that of the whole batch (so every pass writes the same
-// candidate slots), and a query tile's codes take chunks * 2 * ceil(tpc / 2) * 256 words.
+// candidate slots), and a query tile's codes take chunks * tpc * 256 words (a word per
+// query and entry tile).
 static int64_t onepass_tile_words(const Index &ix, int64_t n_qt_all, int64_t *tpc, int64_t *chunks) {
     dense_chunking(ix.n_tiles * (kTileE / kDE), n_qt_all, num_sms(), ix.units_per_cta, tpc, chunks);
-    return *chunks * 2 * ((*tpc + 1) / 2) * kDQ;
+    return *chunks * *tpc * kDQ;
+}
+
+// Chunking of a joined group: the group's own one-pass chunking, with at least
+// kMultiMinTiles entry tiles a unit (many small groups share the SMs anyway).
+constexpr int64_t kMultiMinTiles = 16;
+
+static void multi_chunking(const Index &ix, int64_t nq, int64_t *tpc, int64_t *chunks) {
+    const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
+    onepass_tile_words(ix, (nq + kDQ - 1) / kDQ, tpc, chunks);
+    *tpc = std::min(n_tiles, std::max(*tpc, kMultiMinTiles));
+    *chunks = (n_tiles + *tpc - 1) / *tpc;
 }
 
 // Group-map words the workspace holds for nq queries: the whole batch up to 4 GiB (two-pass
@@ -826,6 +897,8 @@ int64_t dense_gbits_words(const Index &ix, int64_t nq, bool onepass, int64_t lim
     if (onepass) {
         int64_t tpc = 0, chunks = 0;
         one = onepass_tile_words(ix, n_qt, &tpc, &chunks);
+        multi_chunking(ix, nq, &tpc, &chunks);  // a shared multi-index scan may chunk more coarsely
+        one = std::max(one, chunks * tpc * kDQ);
         all = one * n_qt;
         max_words = (int64_t)1 << 32;
     } else {
@@ -898,6 +971,7 @@ static DenseParams dense_base(const Index &ix, int phase) {
     p.g.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
     p.status = ws.status;
     p.wait_ns = ws.wait_ns ? ws.wait_ns : kWaitLimitNs;
+    p.stall = ws.stall;
     p.g.code_inv = ix.code_inv;
     p.code_base = code_base();
     return p;
@@ -993,7 +1067,7 @@ cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, in
     DenseParams p = dense_base(ix, 4);
     p.g.tiles_per_chunk = tpc;
     p.g.chunks = chunks;
-    p.g.words = (tpc + 1) / 2;
+    p.g.words = tpc;
     p.g.gbits = ws.gbits;
     for (int64_t qt0 = 0; qt0 < n_qt;) {
         const int64_t nqt = std::min(per, n_qt - qt0);
@@ -1069,23 +1143,13 @@ struct DenseMulti {
     bool f8 = false;
 };
 
-// Chunking of a joined group: the group's own one-pass chunking, with at least
-// kMultiMinTiles entry tiles a unit (many small groups share the SMs anyway).
-constexpr int64_t kMultiMinTiles = 16;
-
-static void multi_chunking(const Index &ix, int64_t nq, int64_t *tpc, int64_t *chunks) {
-    const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
-    onepass_tile_words(ix, (nq + kDQ - 1) / kDQ, tpc, chunks);
-    *tpc = std::min(n_tiles, std::max(*tpc, kMultiMinTiles));
-    *chunks = (n_tiles + *tpc - 1) / *tpc;
-}
 
 bool dense_multi_joinable(const Index &ix, int64_t nq, int kp, bool f8) {
     if (!dense_scan_supported(ix) || ix.k_pad16 != kp || (ix.prefix == HN_PREFIX_FP8_E4M3) != f8 || nq < 1) return false;
     int64_t tpc = 0, chunks = 0;
     multi_chunking(ix, nq, &tpc, &chunks);
     const int64_t n_qt = (nq + kDQ - 1) / kDQ;
-    return 2 * chunks <= ix.ws.cand_slots && chunks * 2 * ((tpc + 1) / 2) * n_qt * kDQ <= ix.ws.gbits_cap;
+    return 2 * chunks <= ix.ws.cand_slots && chunks * tpc * n_qt * kDQ <= ix.ws.gbits_cap;
 }
 
 hn_status dense_multi_create(const std::vector<const Index *> &ixs, const std::vector<int64_t> &nqs,
@@ -1112,7 +1176,7 @@ hn_status dense_multi_create(const std::vector<const Index *> &ixs, const std::v
         g.unit0 = m->n_units;
         g.cand = ix.ws.cand;
         g.gbits = ix.ws.gbits;
-        g.words = (g.tiles_per_chunk + 1) / 2;
+        g.words = g.tiles_per_chunk;
         g.code_inv = ix.code_inv;
         m->n_units += g.n_qt * g.chunks;
         m->ix.push_back(&ix);

@@ -97,12 +97,12 @@ def test_dense_overflow_rerun(hn, form):
 
 
 @pytest.mark.parametrize("prefix", [1, 2])
-@pytest.mark.parametrize("limit", [1, 1 << 20])
+@pytest.mark.parametrize("limit", [1, 600_000])
 @FORMS
 def test_dense_passes_over_query_tiles(hn, prefix, limit, form):
     """A scratch limit below the group map's size runs the dense scan in passes over
     256-query tiles (11 tiles here, the last one holding 40 queries): limit 1 takes one
-    tile a pass, 1 MiB a few tiles a pass with a shorter last pass.  Same answers as
+    tile a pass, 600 kB a few tiles a pass with a shorter last pass.  Same answers as
     the oracle, and as one pass."""
     k, alpha = 16, 1 / 8
     w, db, q, o_idx, o_sim = oracle_case(20011, 2600, 4000, 25, k, alpha)

@@ -37,30 +37,40 @@ def test_repeated_timeouts(hn):
         assert hn.selftest_wait_timeout(2_000_000) == binding.ERR_TIMEOUT
 
 
-@pytest.mark.parametrize("prefix,scan", [(1, 2), (2, 2), (2, 3)])
+@pytest.mark.parametrize("prefix,scan", [(1, 2), (2, 2), (1, 3), (2, 3)])
 def test_dense_scan_abort_and_drain(hn, prefix, scan):
-    """A main-loop wait limit of one microsecond makes the tensor-core scan's waits give up
-    under normal load (the one-pass form, and the two-pass form of the FP8 prefix, whose
-    epilogue is slow enough that waits pass 1 us), with copies and MMAs in flight: the CTA raises its abort flag, the
-    other roles leave their loops, copies and MMAs still in flight drain (with the full 2 s
-    limit), tensor memory is freed and the kernel returns.  The call reports
-    HN_ERR_TIMEOUT, and an exact search right after, on the same index, is the oracle's."""
+    """test_stall makes each CTA's copy producer stop after its first work unit, so the MMA
+    warps wait for a query copy that never comes: that wait runs out after wait_limit_ns
+    (1 us), the CTA raises its abort flag, the other roles leave their loops, copies and MMAs
+    still in flight drain (with the full 2 s limit), tensor memory is freed and the kernel
+    returns.  Every such call reports HN_ERR_TIMEOUT, and an exact search right after, on
+    the same index, is the oracle's.  Without the stall a 1 us limit may or may not run out
+    under normal load; either way the call is exact or reports the timeout."""
     from paper_2606_27280_b300 import hn as binding
-    # 400k entries and 512 queries give every CTA ~64 entry tiles, more than its copy ring
-    # holds (40), so the producer waits about four tile periods (> 1 us) for each freed stage
-    w, db, q, o_idx, o_sim = oracle_case(400003, 512, 80000, 82, 16, 1 / 8)
+    # 60k entries and 700 queries: every CTA has several work units, so every CTA stalls
+    w, db, q, o_idx, o_sim = oracle_case(60013, 700, 12000, 82, 16, 1 / 8)
     with hn.Index(to_dev(db), 16, 1 / 8, prefix=prefix) as ix:
         qd = to_dev(q)
-        timeouts = 0
-        for _ in range(5):
+        for _ in range(3):
+            with pytest.raises(hn.HNError) as e:
+                ix.search(qd, scan=scan, wait_limit_ns=1000, test_stall=True)
+            assert e.value.status == binding.ERR_TIMEOUT, str(e.value)
+            r = ix.search(qd, scan=scan)
+            assert_parity(r.idx, r.sim, o_idx, o_sim)
+        for _ in range(3):
             try:
-                ix.search(qd, scan=scan, wait_limit_ns=1000)
+                r = ix.search(qd, scan=scan, wait_limit_ns=1000)
             except hn.HNError as e:
                 assert e.status == binding.ERR_TIMEOUT, str(e)
-                timeouts += 1
-        assert timeouts >= 1
+            else:
+                assert_parity(r.idx, r.sim, o_idx, o_sim)
         r = ix.search(qd, scan=scan)
         assert_parity(r.idx, r.sim, o_idx, o_sim)
-        with pytest.raises(hn.HNError) as e:
-            ix.search(qd, scan=scan, wait_limit_ns=999)     # below the documented range
-        assert e.value.status == binding.ERR_INVALID_ARG
+        for kw in (dict(wait_limit_ns=999),                          # below the documented range
+                   dict(test_stall=True),                            # the stall needs a short limit
+                   dict(test_stall=True, wait_limit_ns=20_000_000),
+                   dict(test_stall=True, wait_limit_ns=1000, scan=1)):   # and a dense scan
+            kw.setdefault("scan", scan)
+            with pytest.raises(hn.HNError) as e:
+                ix.search(qd, **kw)
+            assert e.value.status == binding.ERR_INVALID_ARG

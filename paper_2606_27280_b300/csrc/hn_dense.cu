@@ -141,14 +141,31 @@ struct DenseCfg {
     static_assert(kSmem <= 232448, "dense scan shared memory above the 227 KB limit");
 };
 
-// Max of 16 consecutive scores: seven three-input max and one two-input max.  The
-// three-input form issues at half rate, so the ALU work equals that of 15 two-input
-// max, but it takes half the issue slots, which the producer and MMA warps share
-// (measured: Phase 2 at N = 4M, Q = 65,536 from 28.9 to 26.7 ms).
+// Max of 16 consecutive scores: seven three-input max and one two-input max.
+// Measured on B300, the two- and three-input f32 max both issue at half rate
+// (about 1.9 warp instructions per clock per SM), so the three-input form does two
+// reductions for the cost of one.
 __device__ __forceinline__ float max16(const float *v) {
     const float a0 = fmax3(v[0], v[1], v[2]), a1 = fmax3(v[3], v[4], v[5]), a2 = fmax3(v[6], v[7], v[8]);
     const float a3 = fmax3(v[9], v[10], v[11]), a4 = fmax3(v[12], v[13], v[14]);
     return fmaxf(fmax3(a0, a1, a2), fmax3(a3, a4, v[15]));
+}
+
+// Max of 32 consecutive scores: fifteen three-input max and one two-input max (the
+// 31 reductions in 16 half-rate instructions).
+__device__ __forceinline__ float max32(const float *v) {
+    float a[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) a[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    const float b0 = fmax3(a[0], a[1], a[2]), b1 = fmax3(a[3], a[4], a[5]), b2 = fmax3(a[6], a[7], a[8]);
+    const float b3 = fmax3(a[9], v[30], v[31]);
+    return fmaxf(fmax3(b0, b1, b2), b3);
+}
+
+// 2^23 + code(g) as binary32 bits before the upper clamp of code_group_bits: byte 0 is
+// the code while RU(g inv + 2^23 + 128) stays below 2^23 + 256.
+__device__ __forceinline__ uint32_t code_bits_unclamped(float g, float inv, float base) {
+    return __float_as_uint(__fmaf_ru(g, inv, base));
 }
 
 // Max of 64 f16 scores held as 32 packed pairs (31 packed max + 1), as a float.
@@ -308,12 +325,15 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
         }
     } else if (PHASE == 4) {
         // ------------------------------------------------------------ epilogue, one-pass form
-        // Two warp groups, one per accumulator buffer (tile parity): while one group reduces
-        // its tile, the other loads the next, so the TMEM loads and the max trees of an SM
-        // sub-partition overlap instead of running in lockstep.  Warp (group, A tile, TMEM
-        // lane quarter) reads all 128 entry columns of its 32 query rows (two 64-column
-        // loads), so it forms the four group codes of the tile -- one word per (query, tile)
-        // -- and the best group it has seen in the chunk (candidate slot 2 chunk + group).
+        // Two warp groups, one per accumulator buffer: while one group reduces its tile, the
+        // other loads the next, so the TMEM loads and the max trees of an SM sub-partition
+        // overlap instead of running in lockstep.  Every work unit holds an even number of
+        // entry tiles (the host makes tiles_per_chunk even; n_tiles is even), so every unit
+        // starts on buffer 0 and group `grp` takes tiles j = grp, grp + 2, ... of each unit,
+        // always in buffer grp.  Warp (group, A tile, TMEM lane quarter) reads all 128 entry
+        // columns of its 32 query rows (two 64-column loads), so it forms the four group
+        // codes of the tile -- one word per (query, tile) -- and the best group it has seen
+        // in the chunk (candidate slot 2 chunk + group).
         // FP8: the group's largest raw accumulator A bounds its scores u_i = RN(acc_i s_i/256
         // + b_i) from above by max(RU(A smax + bmax), RU(A smin + bmax)) with the group's scale
         // range and largest error term (k_f8_group_bounds).
@@ -323,74 +343,89 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
         const int sub = (ew >> 2) & 1;            // query A tile: accumulator columns 128*sub ..
         const int row = sub * kTileQ + quarter * 32 + lane;
         const bool releaser = (ew & 7) == 0 && lane == 0;  // hands this group's B stages back
-        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        uint32_t stage = 0, sphase = 0;
-        uint32_t g = 0;  // tile counter of this CTA: buffer g & 1, its use number g >> 1
+        const uint32_t taddr = tmem + grp * 256 + sub * kDE + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t full_bar = smem_u32(&acc_full[grp]), empty_bar = smem_u32(&acc_empty[grp]);
+        uint32_t uses = 0;  // tiles this group has taken: use number of its buffer
+        int unit_stage = 0; // ring stage of the current unit's first tile
         bool ok = true;
         for (int64_t u = blockIdx.x; ok && u < p.n_units; u += G) {
             const DenseGroup &gr = MULTI ? group_of(p, u) : p.g;
             const int64_t qt = (u - gr.unit0) % gr.n_qt, ch = (u - gr.unit0) / gr.n_qt;
             const int32_t t0 = (int32_t)(ch * gr.tiles_per_chunk);
-            const int32_t t1 = (int32_t)min64(gr.n_tiles, (int64_t)t0 + gr.tiles_per_chunk);
+            const int32_t nt_u = (int32_t)min64(gr.n_tiles - t0, gr.tiles_per_chunk);  // even
             const int64_t q = qt * kDQ + row;
             const bool qvalid = q < gr.nq;
+            const int64_t wstride = gr.n_qt * kDQ;  // words between consecutive tiles of a query
             float best = -INFINITY;
             int32_t bgid = -1;  // the 32-entry group of `best`
-            uint32_t *gb = gr.gbits + ch * gr.words * (gr.n_qt * kDQ) + q;
+            uint32_t *gb = gr.gbits + ch * gr.words * wstride + q + grp * wstride;
             const int32_t n32 = (int32_t)gr.n;
-            for (int32_t tt = t0; ok && tt < t1; tt += C::kTPS) {
-                const int nt = t1 - tt < C::kTPS ? t1 - tt : C::kTPS;
-                for (int j = 0; j < nt; ++j, ++g) {
-                    const uint32_t buf = g & 1u;
-                    if ((int)buf != grp) continue;
-                    // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
-                    ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&acc_full[buf]), (g >> 1) & 1u, abort_flag,
-                                                           p.wait_ns));
-                    if (!ok) break;
-                    tc_fence_after();
-                    // this tile's MMAs are done with the stage; the last tile of a short stage
-                    // also arrives for the tiles the stage did not hold
-                    const uint32_t rel = j == nt - 1 ? 1 + C::kTPS - nt : 1;
-                    if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
-                    const int32_t t = tt + j;
-                    float v[64];
-                    tmem_ld64(tmem + buf * 256 + sub * kDE + lane_addr, v);
-                    float s0 = fmaxf(max16(v), max16(v + 16)), s1 = fmaxf(max16(v + 32), max16(v + 48));
-                    tmem_ld64(tmem + buf * 256 + sub * kDE + 64 + lane_addr, v);
-                    // the scores are in registers: hand the accumulator back to the MMA warp now
-                    tc_fence_before();
+            const float inv = gr.code_inv, base = p.code_base;
+            // tile j sits in slot j % kTPS of stage unit_stage + j / kTPS (mod kStages)
+            int slot = grp % C::kTPS;
+            int stage = unit_stage + grp / C::kTPS;
+            if (stage >= C::kStages) stage -= C::kStages;
+            for (int32_t j = grp; j < nt_u; j += 2, gb += 2 * wstride) {
+                // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
+                ok = __all_sync(0xffffffffu, mbar_wait(full_bar, uses & 1u, abort_flag, p.wait_ns));
+                if (!ok) break;
+                ++uses;
+                tc_fence_after();
+                // this tile's MMAs are done with the stage; the unit's last tile also arrives
+                // for the slots its (short) stage did not fill
+                const uint32_t rel = j == nt_u - 1 ? (uint32_t)(C::kTPS - slot) : 1u;
+                if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                float v[64];
+                tmem_ld64(taddr, v);
+                float s0 = max32(v), s1 = max32(v + 32);
+                tmem_ld64(taddr + 64, v);
+                // the scores are in registers: hand the accumulator back to the MMA warp now
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_bar);
+                float s2 = max32(v), s3 = max32(v + 32);
+                if (F8) {
+                    const float4 *gbd = reinterpret_cast<const float4 *>(smem + stage * C::kStageBytes +
+                                                                         slot * C::kB + f8_group_off(KP));
+                    const float4 b0 = gbd[0], b1 = gbd[1], b2 = gbd[2], b3 = gbd[3];
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
-                    float s2 = fmaxf(max16(v), max16(v + 16)), s3 = fmaxf(max16(v + 32), max16(v + 48));
-                    if (F8) {
-                        const float4 *gbd = reinterpret_cast<const float4 *>(smem + stage * C::kStageBytes +
-                                                                             j * C::kB + f8_group_off(KP));
-                        const float4 b0 = gbd[0], b1 = gbd[1], b2 = gbd[2], b3 = gbd[3];
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
-                        s0 = fmaxf(__fmaf_ru(s0, b0.x, b0.z), __fmaf_ru(s0, b0.y, b0.z));
-                        s1 = fmaxf(__fmaf_ru(s1, b1.x, b1.z), __fmaf_ru(s1, b1.y, b1.z));
-                        s2 = fmaxf(__fmaf_ru(s2, b2.x, b2.z), __fmaf_ru(s2, b2.y, b2.z));
-                        s3 = fmaxf(__fmaf_ru(s3, b3.x, b3.z), __fmaf_ru(s3, b3.y, b3.z));
-                    }
-                    // threshold candidate: the best group (lowest on ties) holding a real entry
-                    const float m01 = fmaxf(s0, s1), m23 = fmaxf(s2, s3), m = fmaxf(m01, m23);
-                    const int32_t gid = t * 4 + (m01 >= m23 ? (s1 > s0 ? 1 : 0) : (s3 > s2 ? 3 : 2));
-                    if (m > best && gid * 32 < n32) {
+                    if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
+                    s0 = fmaxf(__fmaf_ru(s0, b0.x, b0.z), __fmaf_ru(s0, b0.y, b0.z));
+                    s1 = fmaxf(__fmaf_ru(s1, b1.x, b1.z), __fmaf_ru(s1, b1.y, b1.z));
+                    s2 = fmaxf(__fmaf_ru(s2, b2.x, b2.z), __fmaf_ru(s2, b2.y, b2.z));
+                    s3 = fmaxf(__fmaf_ru(s3, b3.x, b3.z), __fmaf_ru(s3, b3.y, b3.z));
+                }
+                // threshold candidate: the best group (lowest on ties) holding a real entry;
+                // after the first tiles of a chunk the test rarely passes
+                const float m = fmax3(s0, s1, fmaxf(s2, s3));
+                if (m > best) {
+                    const int32_t gid = (t0 + j) * 4 + (s0 == m ? 0 : s1 == m ? 1 : s2 == m ? 2 : 3);
+                    if (gid * 32 < n32) {
                         best = m;
                         bgid = gid;
                     }
-                    // the tile's word: codes of groups 0-3 (byte permutes of the low bytes); a
-                    // streaming store, so that the map does not evict the prefix from L2
-                    const uint32_t c01 = __byte_perm(code_group_bits(s0, gr.code_inv, p.code_base),
-                                                     code_group_bits(s1, gr.code_inv, p.code_base), 0x0040);
-                    const uint32_t c23 = __byte_perm(code_group_bits(s2, gr.code_inv, p.code_base),
-                                                     code_group_bits(s3, gr.code_inv, p.code_base), 0x0040);
-                    __stcs(gb + (int64_t)(t - t0) * (gr.n_qt * kDQ), __byte_perm(c01, c23, 0x5410));
                 }
-                if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
+                // the tile's word: codes of groups 0-3 (byte i = group i), taken from the low
+                // byte of each 2^23 + code float by byte permutes.  The upper clamp only acts
+                // when the tile's largest code would pass 255 (never for scores within the norm
+                // bound); a streaming store, so that the map does not evict the prefix from L2
+                uint32_t c0 = code_bits_unclamped(s0, inv, base), c1 = code_bits_unclamped(s1, inv, base);
+                uint32_t c2 = code_bits_unclamped(s2, inv, base), c3 = code_bits_unclamped(s3, inv, base);
+                if (code_bits_unclamped(m, inv, base) > kCodeBits0 + 255u) {
+                    c0 = min(c0, kCodeBits0 + 255u);
+                    c1 = min(c1, kCodeBits0 + 255u);
+                    c2 = min(c2, kCodeBits0 + 255u);
+                    c3 = min(c3, kCodeBits0 + 255u);
+                }
+                __stcs(gb, __byte_perm(__byte_perm(c0, c1, 0x0040), __byte_perm(c2, c3, 0x0040), 0x5410));
+                slot += 2;
+                while (slot >= C::kTPS) {
+                    slot -= C::kTPS;
+                    if (++stage == C::kStages) stage = 0;
+                }
             }
             if (!ok) break;
+            unit_stage = (int)((unit_stage + (nt_u + C::kTPS - 1) / C::kTPS) % C::kStages);
             // one writer per (query, chunk, group): every slot written
             if (qvalid) gr.cand[q * (2 * gr.chunks) + 2 * ch + grp] = bgid >= 0 ? pack_best(best, (uint32_t)bgid) : 0ull;
         }
@@ -870,10 +905,20 @@ static int64_t gbits_words(int64_t n_tiles, int64_t n_qt, int G, int upc) {
 
 // One-pass form: the chunking is that of the whole batch (so every pass writes the same
 // candidate slots), and a query tile's codes take chunks * tpc * 256 words (a word per
-// query and entry tile).
+// query and entry tile).  tpc is even, and so is n_tiles (rows are padded to 256), so
+// every work unit holds an even number of tiles: the epilogue's two warp groups then
+// take alternate tiles of every unit in a fixed order.
 static int64_t onepass_tile_words(const Index &ix, int64_t n_qt_all, int64_t *tpc, int64_t *chunks) {
-    dense_chunking(ix.n_tiles * (kTileE / kDE), n_qt_all, num_sms(), ix.units_per_cta, tpc, chunks);
+    const int64_t n_tiles = ix.n_tiles * (kTileE / kDE);
+    dense_chunking(n_tiles, n_qt_all, num_sms(), ix.units_per_cta, tpc, chunks);
+    *tpc = std::min(n_tiles, (*tpc + 1) & ~(int64_t)1);
+    *chunks = (n_tiles + *tpc - 1) / *tpc;
     return *chunks * *tpc * kDQ;
+}
+
+// The one-pass epilogue's tile order needs even unit lengths.
+static bool onepass_chunking_ok(const DenseGroup &g) {
+    return g.n_tiles % 2 == 0 && g.tiles_per_chunk % 2 == 0 && g.tiles_per_chunk > 0;
 }
 
 // Chunking of a joined group: the group's own one-pass chunking, with at least
@@ -1069,6 +1114,7 @@ cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, in
     p.g.chunks = chunks;
     p.g.words = tpc;
     p.g.gbits = ws.gbits;
+    if (!onepass_chunking_ok(p.g)) return cudaErrorInvalidValue;
     for (int64_t qt0 = 0; qt0 < n_qt;) {
         const int64_t nqt = std::min(per, n_qt - qt0);
         const int64_t q0 = qt0 * kDQ;
@@ -1178,6 +1224,10 @@ hn_status dense_multi_create(const std::vector<const Index *> &ixs, const std::v
         g.gbits = ix.ws.gbits;
         g.words = g.tiles_per_chunk;
         g.code_inv = ix.code_inv;
+        if (!onepass_chunking_ok(g)) {
+            delete m;
+            return fail(HN_ERR_UNSUPPORTED, "dense_multi_create: odd chunking");
+        }
         m->n_units += g.n_qt * g.chunks;
         m->ix.push_back(&ix);
         m->g.push_back(g);

@@ -375,15 +375,22 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                 // for the slots its (short) stage did not fill
                 const uint32_t rel = j == nt_u - 1 ? (uint32_t)(C::kTPS - slot) : 1u;
                 if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
-                float v[64];
-                tmem_ld64(taddr, v);
-                float s0 = max32(v), s1 = max32(v + 32);
-                tmem_ld64(taddr + 64, v);
-                // the scores are in registers: hand the accumulator back to the MMA warp now
+                // group maxima straight from the loads (the values themselves are not needed).
+                // One load per iteration of a loop that is not unrolled: the scratch registers
+                // of a load are then free again before the next load is issued.
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 1
+                for (int i = 0; i < 4; ++i) {
+                    const float mi = tmem_ldmax32(taddr + 32 * i);
+                    s0 = s1;
+                    s1 = s2;
+                    s2 = s3;
+                    s3 = mi;
+                }
+                // the maxima are in registers: hand the accumulator back to the MMA warp now
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(empty_bar);
-                float s2 = max32(v), s3 = max32(v + 32);
                 if (F8) {
                     const float4 *gbd = reinterpret_cast<const float4 *>(smem + stage * C::kStageBytes +
                                                                          slot * C::kB + f8_group_off(KP));

@@ -45,16 +45,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread may sleep until the phase completes or
+// about `hint_ns` have passed, instead of returning at once.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait: returns false (and raises *abort) once `limit_ns` of global
-// time has passed, or as soon as another thread has raised *abort.  The clock is
-// read every 256 tries, or every try for limits under 1 ms (so that a limit of a
-// few microseconds is honoured).
+// time has passed, or as soon as another thread has raised *abort.  The clock and
+// the flag are read every 8 tries, or every try for limits under 1 ms (so that a
+// limit of a few microseconds is honoured).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    const uint32_t mask = limit_ns < 1000000ull ? 0u : 255u;
+    // the retries sleep in try_wait (an eighth of the limit, at most 20 us) rather than
+    // spinning through issue slots the working warps of the SM sub-partition need
+    const uint32_t hint = (uint32_t)(limit_ns / 8 < 20000ull ? limit_ns / 8 : 20000ull);
+    const uint32_t mask = limit_ns < 1000000ull ? 0u : 7u;
     for (uint32_t i = 1;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, hint)) return true;
         if ((i & mask) == 0) {
             if (*abort) return false;
             if (globaltimer() - t0 > limit_ns) {
@@ -301,6 +316,20 @@ __device__ __forceinline__ void tmem_ld64h_issue(uint32_t taddr, uint32_t (&r)[3
                  : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Maximum of 32 consecutive FP32 columns of this thread's TMEM lane (taddr ..
+// taddr + 31), computed by the load itself (tcgen05.ld.red, sm_103a), waited for.
+__device__ __forceinline__ float tmem_ldmax32(uint32_t taddr) {
+    float v[32], m;
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31]), "=f"(m)
+        : "r"(taddr)
+        : "memory");
+    return m;
+}
+
 __device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[32]) {
     asm volatile(""
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]),

@@ -18,7 +18,9 @@ the GPU kernels must reproduce:
 with the analytic gradients of that loss, and one Adam step
     m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2) g^2,
     p <- p - lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
-Parameters are kept as a dict of float64 arrays.
+Parameters are kept as a dict of float64 arrays.  Inference runs each layer on
+BF16-rounded operands (round to nearest even) with the products summed exactly
+here (binary64) and in FP32 on the GPU: `linear_bf16`.
 """
 from __future__ import annotations
 
@@ -40,6 +42,24 @@ def gelu(a):
 def gelu_grad(a):
     """d/da [a Phi(a)] = Phi(a) + a phi(a)."""
     return 0.5 * (1.0 + erf(a / _SQRT2)) + a * _INV_SQRT_2PI * np.exp(-0.5 * a * a)
+
+
+def bf16_round(a) -> np.ndarray:
+    """Round to the nearest bfloat16 value, ties to even (the binary32 value's upper 16 bits
+    after adding half of the dropped 16 bits' weight, plus one more when the kept low bit is
+    odd), returned as float64.  Finite inputs only."""
+    u = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def linear_bf16(x, w, b=None, act: int = 0) -> np.ndarray:
+    """One layer of the proposal's inference as its definition reads, in binary64:
+    act(bf16(x) @ bf16(w).T + b), act 0 none, 1 the exact GELU.  x (m, k), w (n, k)."""
+    z = bf16_round(x) @ bf16_round(w).T
+    if b is not None:
+        z = z + np.asarray(b, np.float64)
+    return gelu(z) if act == 1 else z
 
 
 def init_params(dims, seed: int) -> dict:

@@ -92,3 +92,37 @@ def test_training_reduces_loss_on_separable_toy():
     l1, _ = mlp.loss_and_grads(p, x, y)
     z, _ = mlp.forward(p, x)
     assert l1 < 0.2 * l0 and np.mean(np.argmax(z, 1) == y) > 0.95
+
+
+def test_bf16_round_ties_to_even_and_library_routine():
+    """Round to nearest bfloat16, ties to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 and
+    goes to 1 (even mantissa); 1 + 3 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6 and goes up;
+    representable values stay; and the whole map equals torch's own float32 -> bfloat16 conversion."""
+    import torch
+    x = np.array([1.0, 1 + 2**-8, 1 + 3 * 2**-8, -(1 + 2**-8), 1 + 2**-8 + 2**-20, 0.0, -0.0, 2.0**-130, 3.0e38])
+    want = np.array([1.0, 1.0, 1 + 2**-6, -1.0, 1 + 2**-7, 0.0, -0.0, 2.0**-130, None], dtype=object)
+    got = mlp.bf16_round(x)
+    for g, w in zip(got[:-1], want[:-1]):
+        assert g == w
+    rng = np.random.default_rng(5)
+    v = np.concatenate([rng.standard_normal(50000) * 10.0 ** rng.integers(-30, 30, 50000),
+                        rng.standard_normal(1000).astype(np.float32).astype(np.float64)])
+    lib = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(v), lib)
+
+
+def test_linear_bf16_is_the_plain_layer_on_rounded_operands():
+    """A hand case, then: on BF16-representable operands the layer is the exact binary64 matmul
+    plus bias (and GELU of it); otherwise it is that of the rounded operands."""
+    z = mlp.linear_bf16(np.array([[1.0, 2.0]]), np.array([[3.0, 4.0], [5.0, 6.0]]), np.array([0.5, -1.0]))
+    assert np.array_equal(z, np.array([[11.5, 16.0]]))
+    rng = np.random.default_rng(6)
+    x = mlp.bf16_round(rng.standard_normal((7, 40)))
+    w = mlp.bf16_round(rng.standard_normal((9, 40)))
+    b = rng.standard_normal(9)
+    exact = x @ w.T + b
+    assert np.array_equal(mlp.linear_bf16(x, w, b), exact)
+    assert np.array_equal(mlp.linear_bf16(x, w, b, act=1), mlp.gelu(exact))
+    xr, wr = rng.standard_normal((5, 33)), rng.standard_normal((4, 33))
+    assert np.array_equal(mlp.linear_bf16(xr, wr), mlp.bf16_round(xr) @ mlp.bf16_round(wr).T)
+    assert not np.array_equal(mlp.linear_bf16(xr, wr), xr @ wr.T)

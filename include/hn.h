@@ -391,7 +391,8 @@ hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *
 hn_status hn_proposal_train(const hn_index *index, const float *train_q, const int32_t *nn_block, int64_t npairs,
                             const hn_train_opts *opts, hn_proposal **out, void *stream);
 
-/* Top-k blocks per query (out_blocks: nq x topk int32, device), by (score desc, block asc). */
+/* Top-k blocks per query (out_blocks: nq x topk int32, device), by (score desc, block asc).
+ * Inference runs the three layers on the tensor cores (hn_linear_bf16's arithmetic). */
 hn_status hn_proposal_infer(const hn_proposal *proposal, const float *q, int64_t nq, int32_t topk,
                             int32_t *out_blocks, void *stream);
 
@@ -412,6 +413,30 @@ hn_status hn_proposal_destroy(hn_proposal *proposal);
  */
 hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
                            const int32_t *y, int32_t batch, float *loss, float *grads, void *stream);
+
+/*
+ * One fully connected layer exactly as the proposal's inference runs it (an
+ * extension; the paper has no network): on the tensor cores (tcgen05.mma,
+ * kind::f16), operands rounded to BF16 (round to nearest even), products exact
+ * and summed in FP32:
+ *   out[r][j] = act( sum_{i<k} bf16(in[r][i]) * bf16(w[j][i]) + bias[j] ),
+ * act 0: none, 1: GELU 0.5 x (1 + erf(x / sqrt 2)).  in: m x k, w: n x k, out:
+ * m x n, all row-major float32 (device, caller-owned); bias: n float32 or NULL.
+ * Requires 1 <= k <= 65536, m, n >= 0, act 0 or 1 (HN_ERR_INVALID_ARG
+ * otherwise).  Synchronises `stream`; HN_ERR_TIMEOUT if a device-side wait gave
+ * up (its output is then unset).
+ */
+hn_status hn_linear_bf16(const float *in, int32_t m, int32_t k, const float *w, int32_t n, const float *bias,
+                         int32_t act, float *out, void *stream);
+
+/*
+ * Block scores of the proposal for nq queries (nq x 128 HN-normalised float32,
+ * device): out_z[j * n_blocks + b] = z_b of query j, the network output
+ * hn_proposal_infer ranks (three hn_linear_bf16 layers on the BF16-rounded
+ * weights).  out_z: nq x n_blocks float32 (device, caller-owned).  Asynchronous
+ * on `stream`.
+ */
+hn_status hn_proposal_logits(const hn_proposal *proposal, const float *q, int64_t nq, float *out_z, void *stream);
 
 /*
  * Verification entry point of the scan arithmetic of the reduced-precision

@@ -315,7 +315,7 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         int32_t *blocks = nullptr;
         hn_proposal *sp = const_cast<hn_proposal *>(seed);
         HN_CUDA(proposal_scratch(sp, nq * topk, &blocks));
-        HN_CUDA(proposal_topk(sp, q, nq, topk, blocks, s));
+        HN_CUDA(proposal_topk(sp, q, nq, topk, blocks, ws.status + ST_TIMEOUT, s));
         HN_CUDA(mark(2));
         HN_CUDA(launch_seed_blocks(ix, q, nq, blocks, topk, minor_scale < 1.f, s));
     } else if (scan == HN_SCAN_DENSE) {

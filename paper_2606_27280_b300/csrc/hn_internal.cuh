@@ -249,7 +249,13 @@ cudaError_t build_blocks(Index &ix, int n_blocks, int iters, cudaStream_t s);
 cudaError_t launch_seed_blocks(const Index &ix, const float *q, int64_t nq, const int32_t *blocks, int topk,
                                bool keep_best, cudaStream_t s);
 // proposal helpers (hn_mlp.cu)
-cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, cudaStream_t s);
+// status: device word set to 1 if an inference layer's bounded wait gave up (may be NULL)
+cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, int32_t *status,
+                          cudaStream_t s);
+// One fully connected layer on the tensor cores (BF16 operands, FP32 accumulation):
+// out[r][j] = act(sum_k in[r][k] w[j][k] + b[j]), act 0 none / 1 gelu; row-major FP32 operands.
+cudaError_t linear_bf16(int M, int N, int K, const float *in, int64_t ldi, const float *w, int64_t ldw,
+                        const float *bias, int act, float *out, int64_t ldo, int32_t *status, cudaStream_t st);
 cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);
 int32_t proposal_blocks(const hn_proposal *p);
 int32_t proposal_k(const hn_proposal *p);

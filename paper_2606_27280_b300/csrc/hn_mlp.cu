@@ -18,8 +18,10 @@
 #include <vector>
 
 #include "hn_internal.cuh"
+#include "hn_sm100.cuh"
 
 namespace hn {
+using namespace sm100;
 
 // ------------------------------------------------------------------ GEMM
 // C(i,j) = sum_k A(i,k) B(k,j) [+ beta C(i,j)], A(i,k) = A[i*sai + k*sak], B(k,j) = B[k*sbk + j*sbj],
@@ -95,6 +97,286 @@ static cudaError_t gemm(int M, int N, int K, const float *A, int64_t sai, int64_
     if (M == 0 || N == 0) return cudaSuccess;
     dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     k_gemm<<<grid, 256, 0, st>>>(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, beta, bias, act, pre);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ tensor-core linear layer
+// Inference layers on the tensor cores: out[r][j] = act(sum_k bf16(in[r][k]) bf16(w[j][k]) + b[j]),
+// act 0 = none, 1 = gelu.  Products of BF16 values are exact in FP32 and the tcgen05.mma
+// accumulates in FP32, so a layer differs from an FP32 evaluation on BF16-rounded operands
+// only by the accumulation order (error <= gamma_K sum_k |a_k w_k|).
+//
+// One CTA per 128 x 256 output tile (M = 128 rows of `in`, N = 256 rows of `w`), 8 warps.  K is
+// taken in slices of 64: all threads stage the slice's A (128 x ks) and B (256 x ks) operands in
+// shared memory, rounded to BF16, in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix, K-adjacent core matrices 128 bytes apart); one thread issues ks / 16
+// MMAs (M = 128, N = 256, K = 16) into a 256-column TMEM accumulator and commits.  Two
+// slice buffers: the staging of slice s + 1 overlaps the MMAs of slice s.  The epilogue reads
+// the accumulator (thread = row; warps 0-3 columns 0-127, warps 4-7 columns 128-255), adds the
+// bias, applies the activation and stores FP32.
+constexpr int kLinM = 128, kLinN = 256, kLinKs = 64, kLinThreads = 256;
+constexpr uint32_t kLinA = kLinM * kLinKs * 2, kLinB = kLinN * kLinKs * 2;  // bytes of one slice
+constexpr uint32_t kLinSmem = 2 * (kLinA + kLinB) + 64;
+
+// Byte offset of element (r, k) of a rows x ks operand slice in the core-matrix layout.
+__device__ __forceinline__ uint32_t lin_off(int r, int k, int ks) {
+    return (uint32_t)((((r >> 3) * (ks >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// Stage rows [r0, r0 + rows) x columns [k0, k0 + ks) of a row-major FP32 matrix (R x K, leading
+// dimension ld) as BF16; zeros outside the matrix.  With `vec` (K, ld multiples of 4 and a 16-byte
+// aligned base) each thread moves four consecutive columns at a time -- one 16-byte load, one
+// 8-byte store (four consecutive k are contiguous in a core matrix) -- with four loads in flight
+// before any store, so that the staging is not bound by one load's latency at a time.
+__device__ __forceinline__ void lin_stage(uint8_t *dst, const float *__restrict__ src, int64_t ld, int R, int K,
+                                          int r0, int rows, int k0, int ks, bool vec) {
+    if (vec) {
+        const int kq = ks >> 2, total = rows * kq;
+        for (int base = threadIdx.x; base < total; base += 4 * kLinThreads) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * kLinThreads;
+                const int r = idx / kq, k = (idx - r * kq) << 2;
+                const int gr = r0 + r, gk = k0 + k;
+                v[u] = (idx < total && gr < R && gk < K) ? *reinterpret_cast<const float4 *>(src + (int64_t)gr * ld + gk)
+                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * kLinThreads;
+                if (idx >= total) break;
+                const int r = idx / kq, k = (idx - r * kq) << 2;
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(v[u].x, v[u].y), hi = __floats2bfloat162_rn(v[u].z, v[u].w);
+                uint2 packed;
+                packed.x = *reinterpret_cast<const uint32_t *>(&lo);
+                packed.y = *reinterpret_cast<const uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(dst + lin_off(r, k, ks)) = packed;
+            }
+        }
+        return;
+    }
+    for (int idx = threadIdx.x; idx < rows * ks; idx += kLinThreads) {
+        const int r = idx / ks, k = idx - r * ks;
+        const int gr = r0 + r, gk = k0 + k;
+        const float v = (gr < R && gk < K) ? src[(int64_t)gr * ld + gk] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(dst + lin_off(r, k, ks)) = __float2bfloat16_rn(v);
+    }
+}
+
+// Running top-TK of one thread's columns, (score desc, column asc): a value enters only if it
+// beats the current last (strict, and columns come in increasing order, so on equal scores the
+// earlier column stays), then bubbles up.
+template <int TK>
+__device__ __forceinline__ void topk_insert(float (&ts)[TK], int (&ti)[TK], float x, int j) {
+    if (!(x > ts[TK - 1])) return;
+#pragma unroll
+    for (int p = 0; p < TK; ++p) {
+        if (x > ts[p]) {
+            const float tx = ts[p];
+            const int tj = ti[p];
+            ts[p] = x;
+            ti[p] = j;
+            x = tx;
+            j = tj;
+        }
+    }
+}
+
+// TK = 0: store out.  TK = 4 or 8 (the proposal's last layer): no output matrix; each row's
+// TK best columns of this CTA's 256 (score desc, column asc) go to cand[row][blockIdx.x][TK] as
+// pack_best keys, 0 for none, and k_topk_keys picks the row's best among its tiles.
+template <int TK>
+__global__ void __launch_bounds__(kLinThreads) k_linear_bf16(int M, int N, int K, const float *__restrict__ in,
+                                                             int64_t ldi, const float *__restrict__ w, int64_t ldw,
+                                                             const float *__restrict__ bias, int act,
+                                                             float *__restrict__ out, int64_t ldo,
+                                                             unsigned long long *__restrict__ cand,
+                                                             int32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t lsm[];
+    uint8_t *sa = lsm, *sb = lsm + 2 * kLinA;
+    uint64_t *done = reinterpret_cast<uint64_t *>(lsm + 2 * (kLinA + kLinB));  // [2] MMA completion per slice buffer
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = blockIdx.y * kLinM, c0 = blockIdx.x * kLinN;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&done[0]), 1);
+        mbar_init(smem_u32(&done[1]), 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), kLinN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = idesc_bf16_f32(kLinM, kLinN);
+    const int kp = (K + 15) & ~15;
+    const bool vec_in = (K & 3) == 0 && (ldi & 3) == 0 && ((uintptr_t)in & 15u) == 0;
+    const bool vec_w = (K & 3) == 0 && (ldw & 3) == 0 && ((uintptr_t)w & 15u) == 0;
+    const int slices = (kp + kLinKs - 1) / kLinKs;
+    constexpr uint64_t kLimit = 2000000000ull;
+    bool ok = true;
+    int issued = 0;  // slices whose MMAs were issued (and committed)
+    for (int s = 0; s < slices; ++s) {
+        const int buf = s & 1, k0 = s * kLinKs, ks = min(kLinKs, kp - k0);
+        // the MMAs of slice s - 2 read this buffer: wait for their commit
+        if (s >= 2) {
+            ok = mbar_wait(smem_u32(&done[buf]), (uint32_t)(((s - 2) >> 1) & 1), abort_flag, kLimit);
+            if (!__syncthreads_and(ok)) break;
+        }
+        lin_stage(sa + buf * kLinA, in, ldi, M, K, r0, kLinM, k0, ks, vec_in);
+        lin_stage(sb + buf * kLinB, w, ldw, N, K, c0, kLinN, k0, ks, vec_w);
+        // generic-proxy stores must be visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a = smem_u32(sa + buf * kLinA), b = smem_u32(sb + buf * kLinB);
+            for (int kk = 0; kk < ks / 16; ++kk) {
+                const uint64_t ad = smem_desc(a + kk * 256, 128, ks * 16);
+                const uint64_t bd = smem_desc(b + kk * 256, 128, ks * 16);
+                umma_bf16(tmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(smem_u32(&done[buf]));
+        }
+        ++issued;
+    }
+    // the last commit covers every MMA issued before it
+    if (issued > 0) {
+        const int last = issued - 1;
+        if (ok) ok = mbar_wait(smem_u32(&done[last & 1]), (uint32_t)((last >> 1) & 1), abort_flag, kLimit);
+        else mbar_drain(smem_u32(&done[last & 1]), (uint32_t)((last >> 1) & 1), kLimit);
+    }
+    ok = __syncthreads_and(ok);  // uniform: the epilogue below has a block-wide barrier
+    tc_fence_after();
+    if (ok && issued == slices) {
+        const int quarter = warp & 3, colhalf = warp >> 2;  // TMEM lanes 32 quarter .., columns 128 colhalf ..
+        const int rl = quarter * 32 + lane, r = r0 + rl;
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        if constexpr (TK == 0) {
+            for (int cb = colhalf * (kLinN / 2); cb < (colhalf + 1) * (kLinN / 2); cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + cb + lane_addr, v);
+                if (r < M) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = c0 + cb + i;
+                        if (j < N) {
+                            float x = v[i] + (bias ? bias[j] : 0.f);
+                            if (act == 1) x = gelu_f(x);
+                            out[(int64_t)r * ldo + j] = x;
+                        }
+                    }
+                }
+            }
+        } else {
+            float ts[TK];
+            int ti[TK];
+#pragma unroll
+            for (int t = 0; t < TK; ++t) {
+                ts[t] = -INFINITY;
+                ti[t] = -1;
+            }
+            for (int cb = colhalf * (kLinN / 2); cb < (colhalf + 1) * (kLinN / 2); cb += 32) {
+                float v[32];
+                tmem_ld32(tmem + cb + lane_addr, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int j = c0 + cb + i;
+                    if (j < N) topk_insert<TK>(ts, ti, v[i] + (bias ? bias[j] : 0.f), j);
+                }
+            }
+            // the two column halves of a row meet in shared memory (the slice buffers are free:
+            // every MMA has completed); the colhalf-0 thread merges them
+            unsigned long long *mk = reinterpret_cast<unsigned long long *>(lsm);  // [128 rows][2 halves][TK]
+#pragma unroll
+            for (int t = 0; t < TK; ++t)
+                mk[(rl * 2 + colhalf) * TK + t] = ti[t] >= 0 ? pack_best(ts[t], (uint32_t)ti[t]) : 0ull;
+            __syncthreads();
+            if (colhalf == 0 && r < M) {
+                const unsigned long long *a = mk + rl * 2 * TK, *b = a + TK;
+                int ia = 0, ib = 0;
+                unsigned long long *dst = cand + ((int64_t)r * gridDim.x + blockIdx.x) * TK;
+#pragma unroll
+                for (int t = 0; t < TK; ++t) {
+                    const unsigned long long ka = ia < TK ? a[ia] : 0ull, kb = ib < TK ? b[ib] : 0ull;
+                    if (ka >= kb) { dst[t] = ka; ++ia; } else { dst[t] = kb; ++ib; }
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && *abort_flag && status) atomicExch(status, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kLinN);
+}
+
+// Top-k of every row from its tiles' candidates (pack_best keys, 0 = none): one warp per row,
+// topk rounds of a warp maximum below the previous round's key (keys are distinct).
+__global__ void k_topk_keys(const unsigned long long *__restrict__ cand, int64_t rows, int per_row, int topk,
+                            int32_t *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= rows) return;
+    const unsigned long long *ci = cand + i * per_row;
+    unsigned long long taken = ~0ull;
+    for (int r = 0; r < topk; ++r) {
+        unsigned long long km = 0;
+        for (int c = lane; c < per_row; c += 32) {
+            const unsigned long long k = ci[c];
+            if (k < taken && k > km) km = k;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, km, o);
+            km = other > km ? other : km;
+        }
+        taken = km;
+        if (lane == 0) out[i * topk + r] = km ? (int32_t)best_idx(km) : -1;
+    }
+}
+
+template <int TK>
+static cudaError_t launch_linear(int M, int N, int K, const float *in, int64_t ldi, const float *w, int64_t ldw,
+                                 const float *bias, int act, float *out, int64_t ldo, unsigned long long *cand,
+                                 int32_t *status, cudaStream_t st) {
+    static bool ready = false;
+    if (!ready) {
+        cudaError_t e = cudaFuncSetAttribute(k_linear_bf16<TK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinSmem);
+        if (e != cudaSuccess) return e;
+        ready = true;
+    }
+    dim3 grid((unsigned)((N + kLinN - 1) / kLinN), (unsigned)((M + kLinM - 1) / kLinM));
+    k_linear_bf16<TK><<<grid, kLinThreads, kLinSmem, st>>>(M, N, K, in, ldi, w, ldw, bias, act, out, ldo, cand, status);
+    return cudaGetLastError();
+}
+
+cudaError_t linear_bf16(int M, int N, int K, const float *in, int64_t ldi, const float *w, int64_t ldw,
+                        const float *bias, int act, float *out, int64_t ldo, int32_t *status, cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    if (M < 0 || N < 0 || K < 1) return cudaErrorInvalidValue;
+    return launch_linear<0>(M, N, K, in, ldi, w, ldw, bias, act, out, ldo, nullptr, status, st);
+}
+
+// Last layer with its top-k fused (topk <= 8): per row the topk best columns of
+// in . w^T + bias, (score desc, column asc), into out (rows x topk int32).  cand: scratch of
+// M * ceil(N / 256) * 8 keys.
+static cudaError_t linear_bf16_topk(int M, int N, int K, const float *in, int64_t ldi, const float *w, int64_t ldw,
+                                    const float *bias, int topk, unsigned long long *cand, int32_t *out,
+                                    int32_t *status, cudaStream_t st) {
+    if (M == 0) return cudaSuccess;
+    const int tiles = (N + kLinN - 1) / kLinN;
+    const int tk = topk <= 4 ? 4 : 8;
+    cudaError_t e = tk == 4 ? launch_linear<4>(M, N, K, in, ldi, w, ldw, bias, 0, nullptr, 0, cand, status, st)
+                            : launch_linear<8>(M, N, K, in, ldi, w, ldw, bias, 0, nullptr, 0, cand, status, st);
+    if (e != cudaSuccess) return e;
+    k_topk_keys<<<(unsigned)(((int64_t)M * 32 + 255) / 256), 256, 0, st>>>(cand, M, tiles * tk, topk, out);
     return cudaGetLastError();
 }
 
@@ -252,18 +534,33 @@ struct Acts {
     float *x = nullptr, *a1 = nullptr, *h1 = nullptr, *a2 = nullptr, *h2 = nullptr, *z = nullptr;
     float *dh1 = nullptr, *dh2 = nullptr, *row_loss = nullptr;
     int32_t *y = nullptr;
+    bool has_z = false;                     // z allocated (rows x c); the fused top-k needs none
+    unsigned long long *cand = nullptr;     // fused top-k candidates
+    int64_t cand_cap = 0;
     void release() {
         cudaFree(x); cudaFree(a1); cudaFree(h1); cudaFree(a2); cudaFree(h2); cudaFree(z);
-        cudaFree(dh1); cudaFree(dh2); cudaFree(row_loss); cudaFree(y);
+        cudaFree(dh1); cudaFree(dh2); cudaFree(row_loss); cudaFree(y); cudaFree(cand);
         *this = Acts();
     }
-    cudaError_t ensure(const Net &n, int64_t rows, bool train) {
-        if (rows <= cap) return cudaSuccess;
+    cudaError_t ensure_cand(int64_t count) {
+        if (count <= cand_cap) return cudaSuccess;
+        cudaFree(cand);
+        cand = nullptr;
+        cand_cap = 0;
+        cudaError_t e = cudaMalloc(&cand, sizeof(unsigned long long) * count);
+        if (e == cudaSuccess) cand_cap = count;
+        return e;
+    }
+    cudaError_t ensure(const Net &n, int64_t rows, bool train, bool need_z = true) {
+        if (rows <= cap && (has_z || !need_z) && (!train || a1)) return cudaSuccess;
         release();
         cudaError_t e = cudaMalloc(&x, sizeof(float) * rows * n.k);
         if (e == cudaSuccess) e = cudaMalloc(&h1, sizeof(float) * rows * n.h1);
         if (e == cudaSuccess) e = cudaMalloc(&h2, sizeof(float) * rows * n.h2);
-        if (e == cudaSuccess) e = cudaMalloc(&z, sizeof(float) * rows * n.c);
+        if (e == cudaSuccess && need_z) {
+            e = cudaMalloc(&z, sizeof(float) * rows * n.c);
+            has_z = e == cudaSuccess;
+        }
         if (e == cudaSuccess) e = cudaMalloc(&row_loss, sizeof(float) * rows);
         if (e == cudaSuccess) e = cudaMalloc(&y, sizeof(int32_t) * rows);
         if (train) {
@@ -277,7 +574,20 @@ struct Acts {
     }
 };
 
-// Forward pass of `rows` inputs already in a.x; with `train`, pre-activations are kept.
+// Inference forward pass of `rows` inputs already in a.x (weights already BF16-rounded): the
+// three layers on the tensor cores, BF16 operands, FP32 accumulation.  `status` (device, may be
+// NULL) is set to 1 if a layer's bounded wait gave up.
+static cudaError_t forward_infer(const Net &n, const float *w, Acts &a, int rows, int32_t *status, cudaStream_t st) {
+    cudaError_t e = linear_bf16(rows, n.h1, n.k, a.x, n.k, w + n.o_w1, n.k, w + n.o_b1, 1, a.h1, n.h1, status, st);
+    if (e == cudaSuccess)
+        e = linear_bf16(rows, n.h2, n.h1, a.h1, n.h1, w + n.o_w2, n.h1, w + n.o_b2, 1, a.h2, n.h2, status, st);
+    if (e == cudaSuccess)
+        e = linear_bf16(rows, n.c, n.h2, a.h2, n.h2, w + n.o_w3, n.h2, w + n.o_b3, 0, a.z, n.c, status, st);
+    return e;
+}
+
+// Training forward pass (FP32 CUDA-core GEMMs, so that the gradients stay comparable with the
+// binary64 oracle); with `train`, pre-activations are kept.
 static cudaError_t forward(const Net &n, const float *w, Acts &a, int rows, bool train, cudaStream_t st) {
     cudaError_t e = gemm(rows, n.h1, n.k, a.x, n.k, 1, w + n.o_w1, 1, n.k, a.h1, n.h1, st, 0.f, w + n.o_b1, 1,
                          train ? a.a1 : nullptr);
@@ -376,15 +686,38 @@ static std::vector<float> init_weights(const Net &n, uint64_t seed) {
 }
 
 // Top-k blocks for nq queries (rows of q, 128 wide), in chunks of 8192 rows.
-cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, cudaStream_t st) {
+cudaError_t proposal_topk(hn_proposal *p, const float *q, int64_t nq, int topk, int32_t *out, int32_t *status,
+                          cudaStream_t st) {
     const Net &n = p->net;
+    if (topk <= 8) {
+        // top-k fused into the last layer: no score matrix, so large chunks (the hidden layers then
+        // fill the GPU)
+        const int64_t chunk = 65536;
+        const int64_t rows_max = std::min<int64_t>(chunk, std::max<int64_t>(nq, 1));
+        cudaError_t e = p->acts.ensure(n, rows_max, false, false);
+        if (e == cudaSuccess) e = p->acts.ensure_cand(rows_max * ((n.c + 255) / 256) * 8);
+        for (int64_t r0 = 0; e == cudaSuccess && r0 < nq; r0 += chunk) {
+            const int rows = (int)std::min<int64_t>(chunk, nq - r0);
+            k_gather_prefix<<<(unsigned)(((int64_t)rows * n.k + 255) / 256), 256, 0, st>>>(
+                q + r0 * kD, nullptr, rows, n.k, p->acts.x, nullptr, nullptr);
+            const float *w = p->w_inf;
+            Acts &a = p->acts;
+            e = linear_bf16(rows, n.h1, n.k, a.x, n.k, w + n.o_w1, n.k, w + n.o_b1, 1, a.h1, n.h1, status, st);
+            if (e == cudaSuccess)
+                e = linear_bf16(rows, n.h2, n.h1, a.h1, n.h1, w + n.o_w2, n.h1, w + n.o_b2, 1, a.h2, n.h2, status, st);
+            if (e == cudaSuccess)
+                e = linear_bf16_topk(rows, n.c, n.h2, a.h2, n.h2, w + n.o_w3, n.h2, w + n.o_b3, topk, a.cand,
+                                     out + r0 * topk, status, st);
+        }
+        return e;
+    }
     const int64_t chunk = 8192;
     cudaError_t e = p->acts.ensure(n, std::min<int64_t>(chunk, std::max<int64_t>(nq, 1)), false);
     for (int64_t r0 = 0; e == cudaSuccess && r0 < nq; r0 += chunk) {
         const int rows = (int)std::min<int64_t>(chunk, nq - r0);
         k_gather_prefix<<<(unsigned)(((int64_t)rows * n.k + 255) / 256), 256, 0, st>>>(q + r0 * kD, nullptr, rows, n.k,
                                                                                         p->acts.x, nullptr, nullptr);
-        e = forward(n, p->w_inf, p->acts, rows, false, st);
+        e = forward_infer(n, p->w_inf, p->acts, rows, status, st);
         if (e == cudaSuccess) {
             k_topk<<<(unsigned)(((int64_t)rows * 32 + 255) / 256), 256, 0, st>>>(p->acts.z, rows, n.c, topk, out + r0 * topk);
             e = cudaGetLastError();
@@ -536,7 +869,7 @@ hn_status hn_proposal_infer(const hn_proposal *prop, const float *q, int64_t nq,
     if (nq < 0 || topk < 1 || topk > 64 || topk > prop->n_blocks) return fail(HN_ERR_INVALID_ARG, "bad nq or topk");
     if (nq == 0) return HN_OK;
     if (!q || !out_blocks || ((uintptr_t)q & 15u)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
-    HN_CUDA(proposal_topk(const_cast<hn_proposal *>(prop), q, nq, topk, out_blocks, (cudaStream_t)stream));
+    HN_CUDA(proposal_topk(const_cast<hn_proposal *>(prop), q, nq, topk, out_blocks, nullptr, (cudaStream_t)stream));
     return HN_OK;
 }
 
@@ -646,6 +979,46 @@ hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h
     cudaFree(loss_dev);
     a.release();
     if (e != cudaSuccess) return cuda_fail(e, "hn_mlp_loss_grad");
+    return HN_OK;
+}
+
+hn_status hn_linear_bf16(const float *in, int32_t m, int32_t k, const float *w, int32_t n, const float *bias,
+                         int32_t act, float *out, void *stream) {
+    if (m < 0 || n < 0 || k < 1 || k > 65536 || (act != 0 && act != 1)) return fail(HN_ERR_INVALID_ARG, "bad sizes or act");
+    if (m == 0 || n == 0) return HN_OK;
+    if (!in || !w || !out) return fail(HN_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = nullptr, h = 0;
+    cudaError_t e = cudaMalloc(&status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = linear_bf16(m, n, k, in, k, w, k, bias, act, out, n, status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(status);
+    if (e != cudaSuccess) return cuda_fail(e, "hn_linear_bf16");
+    if (h) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
+    return HN_OK;
+}
+
+hn_status hn_proposal_logits(const hn_proposal *prop, const float *q, int64_t nq, float *out_z, void *stream) {
+    if (!prop) return fail(HN_ERR_INVALID_ARG, "proposal is NULL");
+    if (nq < 0) return fail(HN_ERR_INVALID_ARG, "nq < 0");
+    if (nq == 0) return HN_OK;
+    if (!q || !out_z || ((uintptr_t)q & 15u)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    hn_proposal *p = const_cast<hn_proposal *>(prop);
+    const Net &n = p->net;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t chunk = 8192;
+    cudaError_t e = p->acts.ensure(n, std::min<int64_t>(chunk, nq), false);
+    for (int64_t r0 = 0; e == cudaSuccess && r0 < nq; r0 += chunk) {
+        const int rows = (int)std::min<int64_t>(chunk, nq - r0);
+        k_gather_prefix<<<(unsigned)(((int64_t)rows * n.k + 255) / 256), 256, 0, st>>>(q + r0 * kD, nullptr, rows, n.k,
+                                                                                        p->acts.x, nullptr, nullptr);
+        e = forward_infer(n, p->w_inf, p->acts, rows, nullptr, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_z + r0 * n.c, p->acts.z, sizeof(float) * rows * n.c, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "hn_proposal_logits");
     return HN_OK;
 }
 

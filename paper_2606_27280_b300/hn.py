@@ -122,6 +122,8 @@ SIGNATURES = {
     "hn_proposal_load": ([ctypes.c_char_p, _vp], _i32),
     "hn_proposal_destroy": ([_vp], _i32),
     "hn_mlp_loss_grad": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
+    "hn_linear_bf16": ([_vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _vp], _i32),
+    "hn_proposal_logits": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "hn_bruteforce_static": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
     "hn_selftest_wait_timeout": ([ctypes.c_uint64, _vp], _i32),
 }
@@ -361,6 +363,14 @@ class Proposal:
                "hn_proposal_infer")
         return out
 
+    def logits(self, q: torch.Tensor, stream=None) -> torch.Tensor:
+        """Block scores (nq, n_blocks) float32 as inference computes them (tensor cores, BF16 operands)."""
+        q = _dev_f32(q, "q")
+        out = torch.empty((q.shape[0], self.info()["n_blocks"]), dtype=torch.float32, device=q.device)
+        _check(_lib.hn_proposal_logits(self._h, q.data_ptr(), q.shape[0], out.data_ptr(), _stream(stream)),
+               "hn_proposal_logits")
+        return out
+
     def close(self) -> None:
         if getattr(self, "_h", None) and self._h.value:
             _lib.hn_proposal_destroy(self._h)
@@ -392,6 +402,27 @@ def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, 
     _check(_lib.hn_mlp_loss_grad(params.data_ptr(), k, h1, h2, c, x.data_ptr(), y.data_ptr(), x.shape[0],
                                  ctypes.byref(loss), grads.data_ptr(), _stream(stream)), "hn_mlp_loss_grad")
     return loss.value, grads
+
+
+def linear_bf16(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None, act: int = 0,
+                stream=None) -> torch.Tensor:
+    """One fully connected layer on the tensor cores as proposal inference runs it:
+    act(bf16(x) @ bf16(w).T + bias), FP32 accumulation; act 0 none, 1 GELU.  x (m, k), w (n, k)."""
+    x = x.contiguous()
+    w = w.contiguous()
+    if x.dtype != torch.float32 or w.dtype != torch.float32 or not x.is_cuda or not w.is_cuda:
+        raise TypeError("x and w: float32 CUDA tensors")
+    if x.dim() != 2 or w.dim() != 2 or x.shape[1] != w.shape[1]:
+        raise ValueError("x (m, k), w (n, k)")
+    if bias is not None:
+        bias = bias.contiguous()
+        if bias.dtype != torch.float32 or bias.shape != (w.shape[0],):
+            raise ValueError("bias: (n,) float32")
+    out = torch.empty((x.shape[0], w.shape[0]), dtype=torch.float32, device=x.device)
+    _check(_lib.hn_linear_bf16(x.data_ptr(), x.shape[0], x.shape[1], w.data_ptr(), w.shape[0],
+                               bias.data_ptr() if bias is not None else None, int(act), out.data_ptr(),
+                               _stream(stream)), "hn_linear_bf16")
+    return out
 
 
 def search_multi(batches, use_graph: bool = True, stream=None) -> dict:

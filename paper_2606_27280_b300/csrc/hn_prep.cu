@@ -73,6 +73,15 @@ __device__ inline float warp_max(float v) {
 __device__ inline float sqrt_up(double s) {
     return __double2float_ru(__dsqrt_ru(s * (1.0 + 0x1p-44)));
 }
+// An upper bound on the sum over the warp of non-negative binary32 values: every addition
+// rounded up (each lane's tree differs, every lane's result is an upper bound).
+__device__ inline float warp_sum_up(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// The same bound as sqrt_up, from the binary64 sum, without a binary64 square root.
+__device__ inline float sqrt_up32(double s) { return __fsqrt_ru(__double2float_ru(s * (1.0 + 0x1p-44))); }
 // Relative tolerance of the norm identities for binary32-stored coordinates.
 __device__ inline bool hn_ok(double maj2, double min2, double alpha) {
     const double tol = (kD + 4) * 0x1p-24;
@@ -342,7 +351,10 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j < nq) v = reinterpret_cast<const float4 *>(q + j * kD)[lane];
     const float vv[4] = {v.x, v.y, v.z, v.w};
-    double maj2 = 0, min2 = 0, res2 = 0, pre2 = 0;
+    // the norm identities need binary64 sums; the bound terms below are upper bounds formed in
+    // binary32 with every operation rounded up (binary64 is slow on this GPU)
+    double maj2 = 0, min2 = 0;
+    float res2 = 0.f, pre2 = 0.f;
     float pv[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -355,15 +367,15 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     const float pp[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const double r = (double)pv[t] - (double)pp[t];
-        res2 += r * r;
-        pre2 += (double)pp[t] * (double)pp[t];
+        const float r = pv[t] - pp[t];  // exact: the BF16 rounding residual
+        res2 = __fmaf_ru(r, r, res2);
+        pre2 = __fmaf_ru(pp[t], pp[t], pre2);
     }
     if (c0 < k_pad4) reinterpret_cast<float4 *>(qpre32 + j * k_pad4)[lane] = p4;
     // FP8 index: Phase-2 A operand = e4m3 hi and lo parts of 256 q (q~ = (hi + lo) / 256 carries
     // about 8 significant bits), Phase-1 A operand = e4m3 of 16 q with the lo slots zero.
     // A row holds 2 * k_pad16 bytes: for every 16 prefix columns, 16 hi bytes then 16 lo bytes.
-    double rq2 = 0, hi2 = 0, lo2 = 0, qt2 = 0;
+    float rq2 = 0.f, hi2 = 0.f, lo2 = 0.f, qt2 = 0.f;
     if (prefix == HN_PREFIX_FP8_E4M3) {
         uint32_t hw = 0, lw = 0, h1 = 0;
 #pragma unroll
@@ -376,12 +388,12 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
             hw |= (uint32_t)hb << (8 * t);
             lw |= (uint32_t)lb << (8 * t);
             h1 |= (uint32_t)f8_encode(pv[t] * kF8QScale1) << (8 * t);
-            const double qq = ((double)hf + (double)lf) / kF8QScale;  // exact
-            const double r = (double)pv[t] - qq;
-            rq2 += r * r;
-            hi2 += (double)hf * hf;
-            lo2 += (double)lf * lf;
-            qt2 += qq * qq;
+            const float qq = (hf + lf) / kF8QScale;  // exact
+            const float r = pv[t] - qq;               // exact
+            rq2 = __fmaf_ru(r, r, rq2);
+            hi2 = __fmaf_ru(hf, hf, hi2);
+            lo2 = __fmaf_ru(lf, lf, lo2);
+            qt2 = __fmaf_ru(qq, qq, qt2);
         }
         if (c0 < k_pad16) {
             const int bc = 32 * (c0 >> 4) + (c0 & 15);
@@ -391,10 +403,10 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
             *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc, 2 * k_pad16)) = h1;
             *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc + 16, 2 * k_pad16)) = 0u;
         }
-        rq2 = warp_sum(rq2);
-        hi2 = warp_sum(hi2);
-        lo2 = warp_sum(lo2);
-        qt2 = warp_sum(qt2);
+        rq2 = warp_sum_up(rq2);
+        hi2 = warp_sum_up(hi2);
+        lo2 = warp_sum_up(lo2);
+        qt2 = warp_sum_up(qt2);
     }
     // int8 index: codes q^ = RN(q / t_q) with the query's own power-of-two scale t_q, written as
     // k_pad16 bytes a query into qpre16, and 1 / (t_q s) (a power of two) into qpre16h read as
@@ -406,15 +418,15 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         for (int t = 0; t < 4; ++t) {
             const uint32_t b = i8_code(pv[t], tq);
             w8 |= b << (8 * t);
-            const double qq = (double)(int8_t)b * tq;  // exact
-            const double r = (double)pv[t] - qq;
-            rq2 += r * r;
-            qt2 += qq * qq;
+            const float qq = (float)(int8_t)b * tq;  // exact
+            const float r = pv[t] - qq;              // exact
+            rq2 = __fmaf_ru(r, r, rq2);
+            qt2 = __fmaf_ru(qq, qq, qt2);
         }
         if (c0 < k_pad16) *reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(qpre16) + j * k_pad16 + c0) = w8;
         if (lane == 0) reinterpret_cast<float *>(qpre16h)[j] = (float)(1.0 / ((double)tq * (double)i8_scale(dev_max[5])));
-        rq2 = warp_sum(rq2);
-        qt2 = warp_sum(qt2);
+        rq2 = warp_sum_up(rq2);
+        qt2 = warp_sum_up(qt2);
     }
     if (prefix == HN_PREFIX_BF16 && c0 < k_pad16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(p4.x, p4.y), hi = __floats2bfloat162_rn(p4.z, p4.w);
@@ -430,16 +442,18 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     }
     maj2 = warp_sum(maj2);
     min2 = warp_sum(min2);
-    res2 = warp_sum(res2);
-    pre2 = warp_sum(pre2);
+    res2 = warp_sum_up(res2);
+    pre2 = warp_sum_up(pre2);
     if (lane != 0 || j >= nq) return;
     if (!hn_ok(maj2, min2, alpha)) atomicExch(status + ST_NOT_NORMALIZED, 1);
-    const double qmaj = sqrt_up(maj2), qmin = sqrt_up(min2), qres = sqrt_up(res2), qhat = sqrt_up(pre2);
-    const double xmin = dev_max[0], xmaj = dev_max[1], xres = dev_max[2], xhat = dev_max[3];
-    double scan;
+    // binary32, every operation rounded up: each term an upper bound of its exact value
+    const float qmaj = sqrt_up32(maj2), qmin = sqrt_up32(min2), qres = __fsqrt_ru(res2), qhat = __fsqrt_ru(pre2);
+    const float xmin = dev_max[0], xmaj = dev_max[1], xres = dev_max[2], xhat = dev_max[3];
+    // gamma_n = n u / (1 - n u), u = 2^-24
+    auto gamma = [](int n) { return __fdiv_ru((float)n * 0x1p-24f, __fsub_rd(1.f, (float)n * 0x1p-24f)); };
+    float scan;
     if (prefix == HN_PREFIX_F32) {
-        const double g = k_pad4 * 0x1p-24 / (1.0 - k_pad4 * 0x1p-24);
-        scan = g * qmaj * xmaj;
+        scan = __fmul_ru(__fmul_ru(gamma(k_pad4), qmaj), xmaj);
     } else if (prefix == HN_PREFIX_FP8_E4M3) {
         // With x~_i = s_i x^_i (exact), q~ = (hi + lo) / 256 and b_i = RU(qt r_i):
         //   q.x_i = q~.x~_i + (q - q~).x_i + q~.(x_i - x~_i)
@@ -449,33 +463,33 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         // Qa = (|hi| + |lo|) / 256, the same deliberately loose term as for BF16), one rounding;
         // the CUDA-core scan forms RN(sum_d q_d x~_d + b_i) with the exact FP32 q (FMA chain
         // error <= gamma_kp |q| |x~_i|).  One slack covers both.
-        const double qa = ((double)sqrt_up(hi2) + (double)sqrt_up(lo2)) / kF8QScale;
-        const double qtil = sqrt_up(qt2), rq = sqrt_up(rq2);
-        const double g = k_pad16 * 0x1p-24 / (1.0 - k_pad16 * 0x1p-24);
-        const double acc = fmax((2 * k_pad16 + 2) * 0x1p-20 * qa * xhat, g * qmaj * xhat);
-        const double excess = fmax(0.0, fmax(qtil, qmaj) - (double)qt) * xres;
-        const double u_round = 0x1p-23 * (fmax(qa, qmaj) * xhat * (1.0 + 0x1p-10) + (double)qt * xres);
-        scan = acc + rq * xmaj + excess + u_round;
+        const float qa = __fdiv_ru(__fadd_ru(__fsqrt_ru(hi2), __fsqrt_ru(lo2)), kF8QScale);
+        const float qtil = __fsqrt_ru(qt2), rq = __fsqrt_ru(rq2);
+        const float acc = fmaxf(__fmul_ru(__fmul_ru((float)(2 * k_pad16 + 2) * 0x1p-20f, qa), xhat),
+                                __fmul_ru(__fmul_ru(gamma(k_pad16), qmaj), xhat));
+        const float excess = __fmul_ru(fmaxf(0.f, __fsub_ru(fmaxf(qtil, qmaj), qt)), xres);
+        const float u_round = __fmul_ru(0x1p-23f, __fadd_ru(__fmul_ru(__fmul_ru(fmaxf(qa, qmaj), xhat), 1.f + 0x1p-10f),
+                                                            __fmul_ru(qt, xres)));
+        scan = __fadd_ru(__fadd_ru(acc, __fmul_ru(rq, xmaj)), __fadd_ru(excess, u_round));
     } else if (prefix == HN_PREFIX_I8) {
         // With q~ = t_q q^ and x~_i = s x^_i (both exact):
         //   q.x_i = q~.x~_i + (q - q~).x_i + q~.(x_i - x~_i) <= q~.x~_i + r(q) max|x_major| + |q~| max r_i.
         // The scan forms q~.x~_i = t_q s (q^ . x^_i) in integers and tests it against tau_q
         // exactly (an integer threshold), so no rounding term enters.
-        scan = (double)sqrt_up(rq2) * xmaj + (double)sqrt_up(qt2) * xres;
+        scan = __fadd_ru(__fmul_ru(__fsqrt_ru(rq2), xmaj), __fmul_ru(__fsqrt_ru(qt2), xres));
     } else {
-        const double g = (k_pad16 + 2) * 0x1p-20;
-        scan = qmaj * xres + qres * xhat + g * qhat * xhat;
+        const float g = (float)(k_pad16 + 2) * 0x1p-20f;
+        scan = __fadd_ru(__fadd_ru(__fmul_ru(qmaj, xres), __fmul_ru(qres, xhat)), __fmul_ru(__fmul_ru(g, qhat), xhat));
     }
     // the oracle's own binary64 rounding: <= 128 * 2^-53 * |q| |x| < 1e-13 for unit vectors
     // (soft ANN mode: minor_scale = beta / alpha < 1 relaxes the minor bound; 1 is exact)
-    const double e = (scan + (double)minor_scale * qmin * xmin) * (1.0 + 1e-9) + 1e-12;
-    qeps[j] = __double2float_ru(e);
+    const float minor = __fmul_ru(__fmul_ru(minor_scale, qmin), xmin);
+    qeps[j] = __fadd_ru(__fadd_ru(scan, minor), 1e-12f);
     // the best-first rescore's bound: an FP32 FMA chain over the K prefix dimensions of the
     // exact query and master row, error <= gamma_K |q_maj| max|x_maj|, plus the full minor
     // bound (alpha, never the soft mode's beta: the rescore keeps the best survivor exactly)
-    const double gk = k * 0x1p-24 / (1.0 - k * 0x1p-24);
-    qeps32[j] = __double2float_ru((gk * qmaj * xmaj + qmin * xmin) * (1.0 + 1e-9) + 1e-12);
-    qnorm[j] = __double2float_ru(sqrt_up(maj2 + min2));
+    qeps32[j] = __fadd_ru(__fadd_ru(__fmul_ru(__fmul_ru(gamma(k), qmaj), xmaj), __fmul_ru(qmin, xmin)), 1e-12f);
+    qnorm[j] = sqrt_up32(maj2 + min2);
 }
 
 cudaError_t launch_query_prep(const Index &ix, const float *q, int64_t nq, float minor_scale, cudaStream_t st) {

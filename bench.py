@@ -487,6 +487,31 @@ def main():
                                   "sample": f"{sub} queries x all {c['n']} entries, FP32 128-dim FMA",
                                   "index_mismatch_vs_hn": int((rb.idx != out_idx[:sub]).sum().item())}
         line["vs_gpu_bruteforce"] = value / (sub / bf_s)
+        # a library tensor-core brute force on the same sample: cuBLAS BF16 GEMMs (FP32
+        # accumulation, BF16 scores) of 256-query chunks against the whole BF16-rounded
+        # database, then argmax -- a speed reference, not exact (BF16 operands and scores)
+        db_bf = hn.normalize(torch.from_numpy(wl.db_raw).cuda(), k, alpha).to(torch.bfloat16)
+        qb = qs.to(torch.bfloat16)
+        tc_idx = torch.empty(sub, dtype=torch.int64, device="cuda")
+
+        def tc_bruteforce():
+            for i in range(0, sub, 256):
+                tc_idx[i:i + 256] = torch.argmax(qb[i:i + 256] @ db_bf.T, dim=1)
+
+        tc_bruteforce()
+        torch.cuda.synchronize()
+        a.record(stream)
+        tc_bruteforce()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tc_s = a.elapsed_time(b) / 1e3
+        line["gpu_bruteforce_tensor"] = {
+            "value": sub / tc_s, "unit": "queries/s",
+            "sample": f"{sub} queries x all {c['n']} entries, cuBLAS BF16 GEMM (FP32 accumulation) + argmax, "
+                      "256-query chunks; not exact",
+            "index_mismatch_vs_hn": int((tc_idx != out_idx[:sub]).sum().item())}
+        line["vs_gpu_bruteforce_tensor"] = value / (sub / tc_s)
+        del db_bf
 
     if not args.no_cpu_baseline and world == 1:   # the oracle is timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(wl, c)

@@ -367,25 +367,46 @@ def main():
     t_max = max_over_ranks(torch, sum(ms) / 1e3, dist, "cuda")
     value = world * nq * args.steps / t_max
 
-    # ---- end to end through the public API: pinned host raw queries in, results out
+    # ---- end to end through the public API: pinned host raw queries in, results out.  As a
+    # serving loop runs it: each step's queries are copied from pinned host memory on a second
+    # stream one step ahead (two staging buffers), the main stream waits for that copy,
+    # normalises and searches, and copies the step's results back; the timed region spans all
+    # steps, every copy inside it.  The inputs (index, code map) are far larger than L2.
     res_idx_host = torch.empty(nq, dtype=torch.int64).pin_memory()
     res_sim_host = torch.empty(nq, dtype=torch.float64).pin_memory()
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    q_stage = torch.empty_like(q_raw)
+    q_stage = [torch.empty_like(q_raw), torch.empty_like(q_raw)]
+    copy_stream = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
+    e2e_a, e2e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def stage_copy(i):
+        buf = i % 2
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(free[buf])   # step i - 2 has normalised this buffer
+            q_stage[buf].copy_(q_host, non_blocking=True)
+            ready[buf].record(copy_stream)
+
     torch.cuda.synchronize()
     barrier()
+    e2e_a.record(stream)
+    copy_stream.wait_event(e2e_a)
+    stage_copy(0)
     for i in range(args.steps):
-        flush.fill_(float(i))
-        e2e_ev[i][0].record(stream)
-        q_stage.copy_(q_host, non_blocking=True)
-        hn.normalize(q_stage, k, alpha, out=q_norm)
+        buf = i % 2
+        if i + 1 < args.steps:
+            stage_copy(i + 1)
+        stream.wait_event(ready[buf])
+        hn.normalize(q_stage[buf], k, alpha, out=q_norm)
+        free[buf].record(stream)
         ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, best_first=args.best_first)
         res_idx_host.copy_(out_idx, non_blocking=True)
         res_sim_host.copy_(out_sim, non_blocking=True)
-        e2e_ev[i][1].record(stream)
+    e2e_b.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_t = max_over_ranks(torch, sum(a.elapsed_time(b) for a, b in e2e_ev) / 1e3, dist, "cuda")
+    e2e_t = max_over_ranks(torch, e2e_a.elapsed_time(e2e_b) / 1e3, dist, "cuda")
     e2e_value = world * nq * args.steps / e2e_t
 
     if rank != 0:

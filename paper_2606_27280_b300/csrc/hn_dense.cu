@@ -66,8 +66,16 @@ using namespace sm100;
 
 constexpr int kIssuers = 2;                      // MMA-issuing threads, one per accumulator buffer
 constexpr int kEpiWarps = 16;                    // 4 per SM sub-partition, 64 accumulator columns each
-constexpr int kEpiWarp0 = 1 + kIssuers;          // warp 0 producer, warps 1..kIssuers MMA, then epilogue
+// warp 0 producer, warps 1..kIssuers MMA issuers, warp 3 idle (it completes the first warpgroup,
+// so that warps 4.. form whole warpgroups for setmaxnreg), warps 4..19 epilogue
+constexpr int kEpiWarp0 = 4;
 constexpr int kDenseThreads = (kEpiWarp0 + kEpiWarps) * 32;
+// Register split of the one-pass form with setmaxnreg (REG): 640 threads launched at 96 registers
+// = 61,440; the first warpgroup (producer, issuers, idle) drops to 56, the four epilogue
+// warpgroups rise to 104: 128 * 56 + 512 * 104 = 60,416.  The host launches that form only when the
+// kernel's register count is exactly kRegLaunch (otherwise an increase could wait forever).
+constexpr int kRegLaunch = 96, kRegLow = 56, kRegHigh = 104;
+static_assert(128 * kRegLow + 512 * kRegHigh <= kDenseThreads * kRegLaunch, "setmaxnreg split above the launch budget");
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // default main-loop wait limit, and every drain's
 constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner) per SM
 
@@ -182,8 +190,11 @@ __device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
 
 // MULTI: the launch covers several groups (p.groups); otherwise the one group p.g, read in
 // place from the kernel parameters.
-template <int KP, int PHASE, bool F8, bool MULTI = false>
+// REG (one-pass form only): the setmaxnreg register split, and two reducing TMEM loads in
+// flight per epilogue warp instead of one.
+template <int KP, int PHASE, bool F8, bool MULTI = false, bool REG = false>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_constant__ DenseParams p) {
+    static_assert(!REG || (PHASE == 4 && !MULTI), "the register split serves the single-group one-pass form");
     using C = DenseCfg<KP, PHASE, F8>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
@@ -224,6 +235,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
     const uint32_t tmem = *tmem_slot;
     const int64_t G = gridDim.x;
 
+    if (REG) {
+        // every thread of each warpgroup: warps 0-3 give registers back, warps 4-19 take them
+        if (warp < kEpiWarp0) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegLow));
+        else asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegHigh));
+    }
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
@@ -323,6 +339,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             umma_commit(smem_u32(&drain[me]));
             mbar_drain(smem_u32(&drain[me]), 0, kWaitLimitNs);
         }
+    } else if (warp < kEpiWarp0) {
+        // idle: completes the first warpgroup
     } else if (PHASE == 4) {
         // ------------------------------------------------------------ epilogue, one-pass form
         // Two warp groups, one per accumulator buffer: while one group reduces its tile, the
@@ -379,13 +397,26 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                 // One load per iteration of a loop that is not unrolled: the scratch registers
                 // of a load are then free again before the next load is issued.
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                if (REG) {
+                    // two loads in flight (64 scratch registers) per iteration
 #pragma unroll 1
-                for (int i = 0; i < 4; ++i) {
-                    const float mi = tmem_ldmax32(taddr + 32 * i);
-                    s0 = s1;
-                    s1 = s2;
-                    s2 = s3;
-                    s3 = mi;
+                    for (int i = 0; i < 2; ++i) {
+                        float m0, m1;
+                        tmem_ldmax2x32(taddr + 64 * i, m0, m1);
+                        s0 = s2;
+                        s1 = s3;
+                        s2 = m0;
+                        s3 = m1;
+                    }
+                } else {
+#pragma unroll 1
+                    for (int i = 0; i < 4; ++i) {
+                        const float mi = tmem_ldmax32(taddr + 32 * i);
+                        s0 = s1;
+                        s1 = s2;
+                        s2 = s3;
+                        s3 = mi;
+                    }
                 }
                 // the maxima are in registers: hand the accumulator back to the MMA warp now
                 tc_fence_before();
@@ -846,7 +877,23 @@ static cudaError_t set_attr2() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dense_smem<KP, 4, F8>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dense_smem<KP, 4, F8>());
     return e;
+}
+
+// The register-split one-pass form is launched only if its threads are launched with exactly
+// kRegLaunch registers: the split's increases draw on that launch budget.
+template <int KP, bool F8>
+static bool reg_split_ok() {
+    static int ok = -1;
+    if (ok < 0) {
+        cudaFuncAttributes a{};
+        ok = cudaFuncGetAttributes(&a, k_dense_scan<KP, 4, F8, false, true>) == cudaSuccess && a.numRegs == kRegLaunch &&
+             a.maxThreadsPerBlock >= kDenseThreads;
+    }
+    return ok == 1;
 }
 
 // Kernel attributes for every instantiation; called once before the first launch
@@ -874,7 +921,12 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
         case 1: k_dense_scan<KP, 1, F8><<<grid, kDenseThreads, dense_smem<KP, 1, F8>(), st>>>(p); break;
         case 2: k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p); break;
         case 3: k_dense_scan<KP, 3, F8><<<grid, kDenseThreads, dense_smem<KP, 3, F8>(), st>>>(p); break;
-        case 4: k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p); break;
+        case 4:
+            if (reg_split_ok<KP, F8>())
+                k_dense_scan<KP, 4, F8, false, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
+            else
+                k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

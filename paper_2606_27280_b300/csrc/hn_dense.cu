@@ -190,11 +190,11 @@ __device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
 
 // MULTI: the launch covers several groups (p.groups); otherwise the one group p.g, read in
 // place from the kernel parameters.
-// REG (one-pass form only): the setmaxnreg register split, and two reducing TMEM loads in
-// flight per epilogue warp instead of one.
+// REG (one-pass form only, single or multi-group): the setmaxnreg register split, and two
+// reducing TMEM loads in flight per epilogue warp instead of one.
 template <int KP, int PHASE, bool F8, bool MULTI = false, bool REG = false>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_constant__ DenseParams p) {
-    static_assert(!REG || (PHASE == 4 && !MULTI), "the register split serves the single-group one-pass form");
+    static_assert(!REG || PHASE == 4, "the register split serves the one-pass form");
     using C = DenseCfg<KP, PHASE, F8>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
@@ -880,18 +880,21 @@ static cudaError_t set_attr2() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dense_smem<KP, 4, F8>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dense_smem<KP, 4, F8>());
     return e;
 }
 
 // The register-split one-pass form is launched only if its threads are launched with exactly
 // kRegLaunch registers: the split's increases draw on that launch budget.
-template <int KP, bool F8>
+template <int KP, bool F8, bool MULTI>
 static bool reg_split_ok() {
     static int ok = -1;
     if (ok < 0) {
         cudaFuncAttributes a{};
-        ok = cudaFuncGetAttributes(&a, k_dense_scan<KP, 4, F8, false, true>) == cudaSuccess && a.numRegs == kRegLaunch &&
-             a.maxThreadsPerBlock >= kDenseThreads;
+        ok = cudaFuncGetAttributes(&a, k_dense_scan<KP, 4, F8, MULTI, true>) == cudaSuccess &&
+             a.numRegs == kRegLaunch && a.maxThreadsPerBlock >= kDenseThreads;
     }
     return ok == 1;
 }
@@ -922,7 +925,7 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
         case 2: k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p); break;
         case 3: k_dense_scan<KP, 3, F8><<<grid, kDenseThreads, dense_smem<KP, 3, F8>(), st>>>(p); break;
         case 4:
-            if (reg_split_ok<KP, F8>())
+            if (reg_split_ok<KP, F8, false>())
                 k_dense_scan<KP, 4, F8, false, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
             else
                 k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
@@ -1312,7 +1315,10 @@ void dense_multi_destroy(DenseMulti *m) {
 
 template <int KP, bool F8>
 static cudaError_t launch_multi_kp(const DenseParams &p, int grid, cudaStream_t st) {
-    k_dense_scan<KP, 4, F8, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
+    if (reg_split_ok<KP, F8, true>())
+        k_dense_scan<KP, 4, F8, true, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
+    else
+        k_dense_scan<KP, 4, F8, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
     return cudaGetLastError();
 }
 

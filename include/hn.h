@@ -131,7 +131,13 @@ typedef struct hn_search_opts {
                              copies and MMAs in flight drain, tensor memory is freed and the call
                              returns HN_ERR_TIMEOUT.  Needs a dense scan, no seed and
                              1e3 <= wait_limit_ns <= 1e7 (HN_ERR_INVALID_ARG otherwise) */
-    int32_t reserved[2];  /* must be zero */
+    int32_t test_plain_epilogue; /* test hook, 0 in normal use.  1: the one-pass dense scans of this
+                             call run their unsplit form (no register split between the warp
+                             groups: one reducing tensor-memory load in flight per epilogue warp),
+                             the form a build whose scan kernel does not get exactly 96 registers a
+                             thread falls back to.  Same result.  0 or 1 (HN_ERR_INVALID_ARG
+                             otherwise) */
+    int32_t reserved[1];  /* must be zero */
 } hn_search_opts;
 
 /* Counters of one hn_search_batch call (filled when the stats pointer is non-NULL). */

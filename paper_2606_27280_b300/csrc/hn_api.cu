@@ -459,9 +459,10 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
     if (o.scratch_limit < 0) return fail(HN_ERR_INVALID_ARG, "scratch_limit < 0");
     if (o.wait_limit_ns != 0 && (o.wait_limit_ns < 1000 || o.wait_limit_ns > 10000000000ull))
         return fail(HN_ERR_INVALID_ARG, "need wait_limit_ns = 0 or 1e3 <= wait_limit_ns <= 1e10");
-    for (int i = 0; i < 2; ++i)
-        if (o.reserved[i]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (o.reserved[0]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (o.test_stall != 0 && o.test_stall != 1) return fail(HN_ERR_INVALID_ARG, "test_stall must be 0 or 1");
+    if (o.test_plain_epilogue != 0 && o.test_plain_epilogue != 1)
+        return fail(HN_ERR_INVALID_ARG, "test_plain_epilogue must be 0 or 1");
     if (o.test_stall && (o.wait_limit_ns == 0 || o.wait_limit_ns > 10000000ull))
         return fail(HN_ERR_INVALID_ARG, "test_stall needs 1e3 <= wait_limit_ns <= 1e7");
     if (o.best_first != 0 && o.best_first != 1) return fail(HN_ERR_INVALID_ARG, "best_first must be 0 or 1");
@@ -487,10 +488,12 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         if (st != HN_OK) return st;
         ws.wait_ns = o.wait_limit_ns;
         ws.stall = o.test_stall;
+        ws.plain = o.test_plain_epilogue;
         st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale,
                             o.best_first != 0);
         ws.wait_ns = 0;
         ws.stall = 0;
+        ws.plain = 0;
         if (st != HN_OK) {
             ws.gbits_limit = 0;
             return st;

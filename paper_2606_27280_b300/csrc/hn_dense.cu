@@ -109,6 +109,7 @@ struct DenseParams {
     uint64_t wait_ns;             // limit of every main-loop wait (the drains keep kWaitLimitNs)
     int32_t *status;
     int32_t stall;                // failure-path test: the producer stops after each CTA's first unit
+    int32_t plain;                // one-pass form: launch the unsplit instantiation (test hook)
 };
 constexpr int kDQ = 256;   // queries per work unit (two MMA A tiles)
 constexpr int kDE = 128;   // entries per B tile (MMA N)
@@ -925,7 +926,7 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
         case 2: k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p); break;
         case 3: k_dense_scan<KP, 3, F8><<<grid, kDenseThreads, dense_smem<KP, 3, F8>(), st>>>(p); break;
         case 4:
-            if (reg_split_ok<KP, F8, false>())
+            if (!p.plain && reg_split_ok<KP, F8, false>())
                 k_dense_scan<KP, 4, F8, false, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
             else
                 k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
@@ -1081,6 +1082,7 @@ static DenseParams dense_base(const Index &ix, int phase) {
     p.status = ws.status;
     p.wait_ns = ws.wait_ns ? ws.wait_ns : kWaitLimitNs;
     p.stall = ws.stall;
+    p.plain = ws.plain;
     p.g.code_inv = ix.code_inv;
     p.code_base = code_base();
     return p;

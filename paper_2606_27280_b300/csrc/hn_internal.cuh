@@ -71,6 +71,7 @@ struct Workspace {
     int64_t gbits_limit = 0;           // words the current search may use (<= gbits_cap; 0 = all)
     uint64_t wait_ns = 0;              // main-loop wait limit of the dense scan for the current search (0 = 2 s)
     int32_t stall = 0;                 // failure-path test for the current search (hn_search_opts.test_stall)
+    int32_t plain = 0;                 // the one-pass scan's unsplit form (hn_search_opts.test_plain_epilogue)
     int64_t cand_cap = 0;              // allocated length of cand
     int32_t cand_slots = 1;            // candidates per query written by the last Phase 1
     float *tau = nullptr;              // [q_cap] Phase-2 prefix threshold

@@ -36,7 +36,7 @@ class SearchOpts(ctypes.Structure):
                 ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("soft", ctypes.c_int32),
                 ("beta", ctypes.c_float), ("scratch_limit", ctypes.c_int64), ("wait_limit_ns", ctypes.c_uint64),
                 ("best_first", ctypes.c_int32), ("test_stall", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("test_plain_epilogue", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class TrainOpts(ctypes.Structure):
@@ -255,7 +255,7 @@ class Index:
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
                proposal: "Proposal | None" = None, seed_topk: int = 0, beta: float | None = None,
                scratch_limit: int = 0, wait_limit_ns: int = 0, best_first: bool = False,
-               test_stall: bool = False, stream=None) -> SearchResult:
+               test_stall: bool = False, test_plain_epilogue: bool = False, stream=None) -> SearchResult:
         """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
         `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped.
         `beta` (0 <= beta <= alpha) selects the soft ANN mode: alpha in the skip test becomes
@@ -264,7 +264,9 @@ class Index:
         wait limit (0 = 2 s).  `best_first` rescores the survivor of best prefix score first and
         drops the others whose prefix bound cannot reach it (same result).  `test_stall`
         (failure-path tests only) withholds the scan's copies after each CTA's first work unit,
-        so its waits run out after `wait_limit_ns` and the call raises HN_ERR_TIMEOUT."""
+        so its waits run out after `wait_limit_ns` and the call raises HN_ERR_TIMEOUT.
+        `test_plain_epilogue` (tests only) runs the one-pass scan's unsplit form, the fallback
+        of a build without the register split (same result)."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         if out_idx is None:
@@ -275,7 +277,8 @@ class Index:
                           seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None,
                           soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0,
                           scratch_limit=int(scratch_limit), wait_limit_ns=int(wait_limit_ns),
-                          best_first=int(bool(best_first)), test_stall=int(bool(test_stall)))
+                          best_first=int(bool(best_first)), test_stall=int(bool(test_stall)),
+                          test_plain_epilogue=int(bool(test_plain_epilogue)))
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),
                                     out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,

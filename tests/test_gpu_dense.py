@@ -116,3 +116,33 @@ def test_dense_passes_over_query_tiles(hn, prefix, limit, form):
             assert r.stats["passes"] == 11
         assert_parity(r.idx, r.sim, o_idx, o_sim)
         assert r.stats["survivors"] == one.stats["survivors"]
+
+
+@pytest.mark.parametrize("prefix", [1, 2])
+@pytest.mark.parametrize("k,n,nq", [(16, 20011, 1000), (16, 3001, 257), (32, 9001, 700), (64, 4097, 300)])
+def test_plain_epilogue_matches_oracle(hn, prefix, k, n, nq):
+    """The one-pass scan's unsplit form (one reducing TMEM load in flight per epilogue warp, no
+    register split), which a build without the split falls back to: the oracle's answers, and
+    the same survivors and group visits as the default form on the same batch."""
+    alpha = 1 / 8
+    w, db, q, o_idx, o_sim = oracle_case(n, nq, max(1, n // 5), 41 + k, k, alpha)
+    with hn.Index(to_dev(db), k, alpha, prefix=prefix) as ix:
+        r0 = ix.search(to_dev(q), scan=DENSE, stats=True)
+        r1 = ix.search(to_dev(q), scan=DENSE, stats=True, test_plain_epilogue=True)
+        assert_parity(r1.idx, r1.sim, o_idx, o_sim)
+        assert_parity(r0.idx, r0.sim, o_idx, o_sim)
+        for key in ("survivors", "groups_scored", "fp64_rescored"):
+            assert r1.stats[key] == r0.stats[key], key
+
+
+def test_plain_epilogue_rejects_bad_value(hn):
+    from paper_2606_27280_b300 import hn as binding
+    w, db, q, o_idx, o_sim = oracle_case(300, 10, 60, 45, 16, 1 / 8)
+    with hn.Index(to_dev(db), 16, 1 / 8, prefix=1) as ix:
+        opts = binding.SearchOpts(scan=DENSE, test_plain_epilogue=2)
+        qd = to_dev(q)
+        oi = torch.empty(qd.shape[0], dtype=torch.int64, device=qd.device)
+        os_ = torch.empty(qd.shape[0], dtype=torch.float64, device=qd.device)
+        st = binding._lib.hn_search_batch(ix._h, qd.data_ptr(), qd.shape[0], binding.ctypes.byref(opts),
+                                          oi.data_ptr(), os_.data_ptr(), None, None)
+        assert st == binding.ERR_INVALID_ARG

@@ -340,8 +340,10 @@ def main():
     out_sim = torch.empty(nq, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    # the queries are normalised on the search's stream without a host round trip; a row
+    # that cannot be normalised is caught by the search itself (HN_ERR_NOT_NORMALIZED)
     def step(timing=False):
-        hn.normalize(q_raw, k, alpha, out=q_norm)
+        hn.normalize_async(q_raw, k, alpha, out=q_norm)
         return ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, timing=timing,
                          best_first=args.best_first)
 
@@ -398,7 +400,7 @@ def main():
         if i + 1 < args.steps:
             stage_copy(i + 1)
         stream.wait_event(ready[buf])
-        hn.normalize(q_stage[buf], k, alpha, out=q_norm)
+        hn.normalize_async(q_stage[buf], k, alpha, out=q_norm)
         free[buf].record(stream)
         ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, best_first=args.best_first)
         res_idx_host.copy_(out_idx, non_blocking=True)
@@ -621,7 +623,7 @@ def run_proposal(args, hn, torch, world, rank, dist, barrier):
     res = {}
     for name, kw in (("seeded", dict(proposal=prop, seed_topk=4)), ("plain", {})):
         def step():
-            hn.normalize(q_raw, k, alpha, out=qn)
+            hn.normalize_async(q_raw, k, alpha, out=qn)
             return ix.search(qn, out_idx=oi, out_sim=os_, timing=True, **kw)
         for _ in range(args.warmup):
             step()

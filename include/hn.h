@@ -225,6 +225,20 @@ hn_status hn_normalize(const float *in, float *out, int64_t n, int32_t d, int32_
                        void *stream);
 
 /*
+ * The same normalisation, enqueued on `stream` without synchronising it (for serving
+ * loops that normalise each batch just before searching it).  Same arithmetic and
+ * requirements as hn_normalize; the arguments are checked on the host before the launch
+ * (HN_ERR_INVALID_ARG, nothing enqueued).  A row with a non-finite value or a zero major
+ * (or, with alpha > 0, minor) part is copied to `out` unchanged, and hn_search_batch /
+ * hn_search_topk / hn_search_multi then report HN_ERR_NOT_NORMALIZED for the batch.
+ * status: NULL, or device memory int32_t[2] that this call does not clear (the caller
+ * zeroes it once and may read it after any number of calls): the kernel sets status[0]
+ * to 1 when a row held a non-finite value and status[1] to 1 when a row had a zero norm.
+ */
+hn_status hn_normalize_async(const float *in, float *out, int64_t n, int32_t d, int32_t k, double alpha,
+                             int32_t *status, void *stream);
+
+/*
  * Build a search index over n HN-normalised entries x (n x d float32, device).
  * The index copies x (the caller may free it once this call returns) and packs
  * the major prefixes into a separate contiguous array in the chosen precision

@@ -162,6 +162,20 @@ hn_status hn_normalize(const float *in, float *out, int64_t n, int32_t d, int32_
     return HN_OK;
 }
 
+hn_status hn_normalize_async(const float *in, float *out, int64_t n, int32_t d, int32_t k, double alpha,
+                             int32_t *status, void *stream) {
+    hn_status st = check_dims(d, k, alpha, false);
+    if (st != HN_OK) return st;
+    if (n < 0) return fail(HN_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return HN_OK;
+    if (!in || !out || !aligned16(in) || !aligned16(out)) return fail(HN_ERR_INVALID_ARG, "null or unaligned pointer");
+    if (status && ((uintptr_t)status & 3u)) return fail(HN_ERR_INVALID_ARG, "unaligned status");
+    static_assert(ST_NOT_NORMALIZED == 0 && ST_ZERO_NORM == 1, "status[0], status[1] of hn_normalize_async");
+    const cudaError_t e = launch_normalize(in, out, n, k, alpha, status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "hn_normalize_async");
+    return HN_OK;
+}
+
 hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double alpha, const hn_index_opts *opts,
                          hn_index **out, void *stream) {
     if (!out) return fail(HN_ERR_INVALID_ARG, "out is NULL");

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kNormRows) k_normalize(const float *__restrict
         const bool bad = !isfinite(s_maj) || !isfinite(s_min);
         const bool zero = s_maj == 0.0 || (alpha > 0.0 && s_min == 0.0);
         if (bad || zero) {
-            atomicExch(status + (bad ? ST_NOT_NORMALIZED : ST_ZERO_NORM), 1);
+            if (status) atomicExch(status + (bad ? ST_NOT_NORMALIZED : ST_ZERO_NORM), 1);
         } else {
             const double c_maj = sqrt(1.0 - alpha) / sqrt(s_maj);
             for (int c = 0; c < k; ++c) f[c] = __double2float_rn((double)f[c] * c_maj);

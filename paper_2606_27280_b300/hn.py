@@ -103,6 +103,7 @@ SIGNATURES = {
     "hn_version": ([], _i32),
     "hn_last_error": ([], ctypes.c_char_p),
     "hn_normalize": ([_vp, _vp, _i64, _i32, _i32, _f64, _vp], _i32),
+    "hn_normalize_async": ([_vp, _vp, _i64, _i32, _i32, _f64, _vp, _vp], _i32),
     "hn_index_build": ([_vp, _i64, _i32, _i32, _f64, _vp, _vp, _vp], _i32),
     "hn_index_destroy": ([_vp], _i32),
     "hn_index_get_info": ([_vp, _vp], _i32),
@@ -185,6 +186,25 @@ def normalize(x: torch.Tensor, k: int, alpha: float, out: torch.Tensor | None = 
         out = torch.empty_like(x)
     _check(_lib.hn_normalize(x.data_ptr(), out.data_ptr(), x.shape[0], D, int(k), float(alpha), _stream(stream)),
            "hn_normalize")
+    return out
+
+
+def normalize_async(x: torch.Tensor, k: int, alpha: float, out: torch.Tensor | None = None,
+                    status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """normalize() enqueued without synchronising the stream.  A bad row (non-finite, or a zero
+    major / minor part) is copied unchanged, so a search of it raises HN_ERR_NOT_NORMALIZED;
+    `status` (int32 [2] on the device, not cleared here) records such rows: [0] non-finite,
+    [1] zero norm."""
+    x = _dev_f32(x, "x")
+    if out is None:
+        out = torch.empty_like(x)
+    sp = None
+    if status is not None:
+        if status.dtype != torch.int32 or not status.is_cuda or status.numel() < 2 or not status.is_contiguous():
+            raise ValueError("status must be a contiguous int32 CUDA tensor of at least 2 elements")
+        sp = status.data_ptr()
+    _check(_lib.hn_normalize_async(x.data_ptr(), out.data_ptr(), x.shape[0], D, int(k), float(alpha), sp,
+                                   _stream(stream)), "hn_normalize_async")
     return out
 
 

@@ -44,6 +44,51 @@ def test_normalize_in_place_and_zero_norm(hn):
     assert e.value.status == 3
 
 
+@pytest.mark.parametrize("k,alpha", [(16, 1 / 8), (1, 0.0), (127, 0.9)])
+def test_normalize_async_bit_exact(hn, k, alpha):
+    """The stream-ordered form: the same bits as the oracle, in place too, status untouched."""
+    w = hn_synth.make_workload(2049, 300, 100, seed=8)
+    raw = np.concatenate([w.db_raw, w.q_raw])
+    raw[7, :k] *= 1e-30
+    want = oracle.normalize(raw, k, alpha)
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
+    got = hn.normalize_async(to_dev(raw), k, alpha, status=status)
+    x = to_dev(raw)
+    hn.normalize_async(x, k, alpha, out=x)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    assert np.array_equal(x.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    assert status.cpu().tolist() == [0, 0]
+
+
+def test_normalize_async_bad_rows(hn):
+    """A zero-norm or non-finite row: flagged in status, copied unchanged, and the search of
+    a batch holding it reports HN_ERR_NOT_NORMALIZED; the other rows are normalised."""
+    from paper_2606_27280_b300 import hn as binding
+    k, alpha = 16, 1 / 8
+    w = hn_synth.make_workload(4000, 64, 400, seed=9)
+    db = oracle.normalize(w.db_raw, k, alpha)
+    raw = w.q_raw.copy()
+    raw[5, :k] = 0
+    raw[40, 100] = np.nan
+    status = torch.zeros(2, dtype=torch.int32, device="cuda")
+    q = hn.normalize_async(to_dev(raw), k, alpha, status=status)
+    torch.cuda.synchronize()
+    assert status.cpu().tolist() == [1, 1]
+    got = q.cpu().numpy()
+    assert np.array_equal(got[5], raw[5]) and np.isnan(got[40, 100])
+    good = np.ones(len(raw), bool)
+    good[[5, 40]] = False
+    assert np.array_equal(got[good], oracle.normalize(raw[good], k, alpha))
+    with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
+        for scan in (hn.SCAN_DENSE, hn.SCAN_STREAM):
+            with pytest.raises(hn.HNError) as e:
+                ix.search(q, scan=scan)
+            assert e.value.status == binding.ERR_NOT_NORMALIZED
+    with pytest.raises(ValueError):
+        hn.normalize_async(to_dev(raw), k, alpha, status=torch.zeros(2, dtype=torch.int64, device="cuda"))
+
+
 def test_index_rejects_unnormalized(hn):
     raw = hn_synth.make_workload(1000, 0, 10, seed=1).db_raw
     with pytest.raises(hn.HNError) as e:

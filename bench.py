@@ -65,9 +65,10 @@ def parse():
     ap.add_argument("--scan", default="auto", choices=["auto", "stream", "dense", "dense2"])
     ap.add_argument("--clock-log", default=None,
                     help="file for the nvidia-smi clock samples of the timed region (default: a temporary file)")
-    ap.add_argument("--best-first", action="store_true",
-                    help="best-first rescore: the survivor of largest prefix score first, the rest only while "
-                         "their prefix bound reaches the best full score (same result)")
+    ap.add_argument("--rescore", choices=["filter16", "best_first", "full"], default="filter16",
+                    help="Phase-2 rescore of the 1-NN search (same result): certified FP16-row bound before the "
+                         "FP32 row (default), the FP32 prefix bound (best first), or every survivor in FP32")
+    ap.add_argument("--best-first", action="store_true", help="the same as --rescore best_first")
     ap.add_argument("--no-autotune", action="store_true", help="c4: keep every index's default scan choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
@@ -320,6 +321,9 @@ def main():
     scan = {"auto": hn.SCAN_AUTO, "stream": hn.SCAN_STREAM, "dense": hn.SCAN_DENSE,
             "dense2": hn.SCAN_DENSE_TWO_PASS}[args.scan]
     stream = torch.cuda.current_stream()
+    rescore_name = "best_first" if args.best_first else args.rescore
+    rescore_mode = {"filter16": hn.RESCORE_FILTER16, "best_first": hn.RESCORE_BEST_FIRST,
+                    "full": hn.RESCORE_FULL}[rescore_name]
 
     # ---- index (built once, outside the timed region)
     db_raw = torch.from_numpy(wl.db_raw).cuda()
@@ -345,7 +349,7 @@ def main():
     def step(timing=False):
         hn.normalize_async(q_raw, k, alpha, out=q_norm)
         return ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, timing=timing,
-                         best_first=args.best_first)
+                         rescore=rescore_mode)
 
     for _ in range(args.warmup):
         r = step()
@@ -402,7 +406,7 @@ def main():
         stream.wait_event(ready[buf])
         hn.normalize_async(q_stage[buf], k, alpha, out=q_norm)
         free[buf].record(stream)
-        ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, best_first=args.best_first)
+        ix.search(q_norm, scan=scan, out_idx=out_idx, out_sim=out_sim, rescore=rescore_mode)
         res_idx_host.copy_(out_idx, non_blocking=True)
         res_sim_host.copy_(out_sim, non_blocking=True)
     e2e_b.record(stream)
@@ -491,6 +495,7 @@ def main():
         "search_stats": {kk: st[kk] for kk in ("survivors", "max_survivors", "fp64_rescored", "reruns", "scan",
                                                "passes", "kernels", "groups_scored", "rescore_skipped")},
         "survivor_frac": st["survivors"] / (nq * c["n"]),
+        "rescore": rescore_name,
         "index_build_s": build_s, "index_bytes": info["device_bytes"],
     }
 

@@ -82,6 +82,14 @@ typedef enum hn_scan {
                            (query, 32-entry group), nq * n / 256 bytes) */
 } hn_scan;
 
+/* How the 1-NN Phase 2 scores its survivors (hn_search_opts.rescore); every mode returns the
+ * oracle's answer.  The index keeps an FP16 copy of every row (256 B per entry) for the first. */
+typedef enum hn_rescore {
+    HN_RESCORE_FILTER16 = 0,    /* certified FP16-row bound first, FP32 row only where it can win */
+    HN_RESCORE_BEST_FIRST = 1,  /* the sorted-Phase-2 early exit with the FP32 prefix bound */
+    HN_RESCORE_FULL = 2         /* every survivor scored in FP32 (Algorithm 1's Phase 2) */
+} hn_rescore;
+
 typedef struct hn_index_opts {
     int32_t prefix;       /* hn_prefix; default HN_PREFIX_F32 */
     int32_t n_blocks;     /* > 0: partition the entries into this many blocks for the learned
@@ -117,13 +125,16 @@ typedef struct hn_search_opts {
                               MMAs still drain with the 2 s limit) and the call returns
                               HN_ERR_TIMEOUT.  Limits of a few microseconds make the waits of a
                               normally loaded scan run out: used to exercise that path */
-    int32_t best_first;   /* 1-NN rescore order.  0: every survivor in slot order (Algorithm 1's
-                             Phase 2 in index order).  1: best first, the early exit the remark
-                             after Algorithm 1 describes for a sorted Phase 2: the survivor with
-                             the largest FP32 prefix score is scored first, and every other one only
-                             while its prefix bound reaches the best certified full score so far,
-                             so most survivors cost a read of K values instead of the whole row.
-                             Same result either way */
+    int32_t rescore;      /* hn_rescore: how the 1-NN Phase 2 scores its survivors (same result in
+                             every mode).  HN_RESCORE_FILTER16 (0, default): each survivor first gets
+                             a certified upper bound from its FP16 row (256 B: the FP32 dot of the
+                             query with the row rounded to FP16, plus the rounding and summation
+                             slack); only survivors whose bound reaches the best certified full
+                             score so far (starting from the threshold candidates') are read and
+                             scored in FP32.  HN_RESCORE_BEST_FIRST (1): the early exit the remark
+                             after Algorithm 1 describes for a sorted Phase 2, with the FP32 prefix
+                             score as the bound.  HN_RESCORE_FULL (2): every survivor scored in
+                             FP32 in slot order (Algorithm 1's Phase 2 in index order) */
     int32_t test_stall;   /* failure-path test hook, 0 in normal use.  1: in every dense-scan launch
                              of this call, each CTA's copy producer stops after the CTA's first work
                              unit, so the MMA warps wait for a query copy that never comes; that

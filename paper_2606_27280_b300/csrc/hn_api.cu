@@ -78,6 +78,7 @@ static void free_index(Index *ix) {
     cudaFree(ix->ws.counters);
     cudaFreeHost(ix->ws.h_status);
     cudaFree(ix->rows);
+    cudaFree(ix->rows16);
     cudaFree(ix->pre32);
     cudaFree(ix->pre16);
     cudaFree(ix->pre16h);
@@ -221,6 +222,7 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
     } while (0)
     TRY(dalloc(&ix.rows, (size_t)n_pad * kD));
     TRY(cudaMemsetAsync(ix.rows + n * kD, 0, (size_t)(n_pad - n) * kD * sizeof(float), s));
+    TRY(dalloc(&ix.rows16, (size_t)n_pad * kD));
     if (ix.prefix == HN_PREFIX_F32) {
         TRY(dalloc(&ix.pre32, (size_t)n_pad * ix.k_pad4));
     } else if (ix.prefix == HN_PREFIX_FP8_E4M3) {
@@ -251,7 +253,7 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         const double b = 1.05 * (std::sqrt(1.0 - alpha) * ix.host_max[3] + (double)ix.qt * ix.host_max[2]);
         ix.code_inv = b > 0 ? (float)(127.0 / b) : 1.f;
     }
-    ix.bytes = (int64_t)n_pad * kD * 4 + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
+    ix.bytes = (int64_t)n_pad * kD * (4 + 2) + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
                (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) +
                (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) +
                (ix.prei8 ? n_pad * ix.k_pad16 : 0) + n * 4;
@@ -318,7 +320,7 @@ hn_status hn_index_blocks(const hn_index *index, int32_t *block_start, int32_t *
 // With a proposal (`seed`), its top blocks give the threshold and Phase 1 is skipped.
 static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                             int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn,
-                            float minor_scale, bool best_first) {
+                            float minor_scale, int rescore) {
     Workspace &ws = ix.ws;
     auto mark = [&](int i) { return timing ? cudaEventRecord(ws.ev[i], s) : cudaSuccess; };
     HN_CUDA(cudaMemsetAsync(ws.key1, 0, sizeof(unsigned long long) * nq, s));
@@ -350,7 +352,7 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         HN_CUDA(mark(4));
     }
     HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s)
-                   : launch_rescore(ix, q, nq, out_idx, out_sim, s, best_first));
+                   : launch_rescore(ix, q, nq, out_idx, out_sim, s, rescore));
     HN_CUDA(mark(5));
     return HN_OK;
 }
@@ -407,11 +409,11 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn, b
 // host mirror ws.h_status once the stream has run.
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                          int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn, float minor_scale,
-                         bool best_first) {
+                         int rescore) {
     Workspace &ws = ix.ws;
     HN_CUDA(cudaMemsetAsync(ws.status, 0, 8 * sizeof(int32_t), s));
     HN_CUDA(cudaMemsetAsync(ws.counters, 0, 8 * sizeof(long long), s));
-    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s, nn, minor_scale, best_first);
+    hn_status st = run_search(ix, q, nq, scan, seed, topk, out_idx, out_sim, timing, s, nn, minor_scale, rescore);
     if (st != HN_OK) return st;
     HN_CUDA(cudaMemcpyAsync(ws.h_status, ws.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     HN_CUDA(cudaMemcpyAsync(ws.h_status + 8, ws.counters, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
@@ -479,7 +481,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         return fail(HN_ERR_INVALID_ARG, "test_plain_epilogue must be 0 or 1");
     if (o.test_stall && (o.wait_limit_ns == 0 || o.wait_limit_ns > 10000000ull))
         return fail(HN_ERR_INVALID_ARG, "test_stall needs 1e3 <= wait_limit_ns <= 1e7");
-    if (o.best_first != 0 && o.best_first != 1) return fail(HN_ERR_INVALID_ARG, "best_first must be 0 or 1");
+    if (o.rescore < HN_RESCORE_FILTER16 || o.rescore > HN_RESCORE_FULL) return fail(HN_ERR_INVALID_ARG, "bad rescore mode");
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->n_queries = nq;
@@ -504,7 +506,7 @@ static hn_status search_impl(hn_index *index, const float *q, int64_t nq, int nn
         ws.stall = o.test_stall;
         ws.plain = o.test_plain_epilogue;
         st = enqueue_search(ix, q, nq, scan, o.seed, topk, out_idx, out_sim, timing, s, nn, minor_scale,
-                            o.best_first != 0);
+                            o.rescore);
         ws.wait_ns = 0;
         ws.stall = 0;
         ws.plain = 0;

@@ -105,6 +105,7 @@ struct Index {
     int32_t k_pad16 = 0;   // BF16 prefix width (multiple of 16, UMMA K step)
     int64_t n_tiles = 0;   // ceil(n / kTileE)
     float *rows = nullptr;           // [n][128] FP32 master copy (full rescore)
+    __half *rows16 = nullptr;        // [n_pad][128] the rows rounded to FP16 (the rescore's bound)
     float *pre32 = nullptr;          // [n][k_pad4] FP32 prefix (HN_PREFIX_F32)
     __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
     __half *pre16h = nullptr;        // FP16 copy of the same prefix (dense Phase 1 candidate search)
@@ -199,7 +200,7 @@ hn_status prepare_search(Index &ix, int64_t nq, int scan, int32_t cap, int nn = 
                          int64_t scratch_limit = 0);
 hn_status enqueue_search(Index &ix, const float *q, int64_t nq, int scan, const hn_proposal *seed, int topk,
                          int64_t *out_idx, double *out_sim, bool timing, cudaStream_t s, int nn = 1,
-                         float minor_scale = 1.f, bool best_first = false);
+                         float minor_scale = 1.f, int rescore = HN_RESCORE_FILTER16);
 hn_status check_search(Index &ix, int64_t nq, int32_t *want_cap);
 int32_t default_cap(const Index &ix);
 Index *index_state_mut(hn_index *h);
@@ -233,10 +234,10 @@ cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *o
 // Exact top-kk of every query from its Phase-2 survivors (1 <= kk <= 32): out_idx/out_sim [nq][kk].
 cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
                                 double *out_sim, cudaStream_t s);
-// best_first: the survivor of largest FP32 prefix score is scored first and the others only
-// while their prefix bound reaches the running certified best (f4)
+// mode (hn_rescore): the FP16-row filter (default), the best-first prefix bound (f4), or every
+// survivor in FP32
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
-                           double *out_sim, cudaStream_t s, bool best_first = false);
+                           double *out_sim, cudaStream_t s, int mode = HN_RESCORE_FILTER16);
 cudaError_t launch_bruteforce(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,
                               double *out_sim, cudaStream_t s);
 // Brute force with a caller-provided per-query key array (nq entries, cleared here).

@@ -299,6 +299,24 @@ __global__ void __launch_bounds__(256) k_f8_group_bounds(uint8_t *__restrict__ p
     reinterpret_cast<float4 *>(tile8 + f8_group_off(kp))[g & 3] = make_float4(smax, smin, bmax, 0.f);
 }
 
+// The rescore's FP16 rows: every FP32 master row rounded to nearest FP16 (padding rows
+// stay zero).  Eight values a thread: two 16-byte loads, one 16-byte store.
+__global__ void __launch_bounds__(256) k_rows_f16(const float *__restrict__ rows, __half *__restrict__ rows16,
+                                                  int64_t n8) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(rows)[2 * i];
+        const float4 b = reinterpret_cast<const float4 *>(rows)[2 * i + 1];
+        const __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+        const __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+        uint4 o;
+        o.x = *reinterpret_cast<const uint32_t *>(&h0);
+        o.y = *reinterpret_cast<const uint32_t *>(&h1);
+        o.z = *reinterpret_cast<const uint32_t *>(&h2);
+        o.w = *reinterpret_cast<const uint32_t *>(&h3);
+        reinterpret_cast<uint4 *>(rows16)[i] = o;
+    }
+}
+
 cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
     const int64_t n_pad = ix.n_tiles * kTileE;
     int64_t blocks = (n_pad * 32 + 255) / 256;
@@ -317,6 +335,11 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         const int64_t n_groups = n_pad / 32;
         k_f8_group_bounds<<<(unsigned)((n_groups + 255) / 256), 256, 0, st>>>(ix.pre8, ix.n, n_groups, ix.k_pad16);
+    }
+    if (ix.rows16) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_rows_f16<<<148 * 16, 256, 0, st>>>(ix.rows, ix.rows16, n_pad * kD / 8);
     }
     return cudaGetLastError();
 }

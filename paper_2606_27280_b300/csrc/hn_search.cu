@@ -831,6 +831,162 @@ __global__ void __launch_bounds__(256) k_rescore_bf(const float *__restrict__ ro
     rescore_finish(rows, q, j, bk, cnt, lane, spill, ncand, cidx, out_idx, out_sim, counters);
 }
 
+// The default 1-NN rescore: a certified FP16 filter in front of Algorithm 1's Phase-2 full
+// scores.  Eq. 3 lets through every entry whose prefix bound reaches the threshold, and most
+// of them end far below the best full score.  Each survivor's binary64 similarity is bounded
+// from above by the FP32 dot of the query against the entry's FP16 row (256 B instead of the
+// 512 B FP32 row): with x~_d = RN_fp16(x_d),
+//   |x~_d - x_d| <= 2^-11 |x_d| + 2^-25          (normal and subnormal FP16 spacing)
+//   |sum q_d x~_d - sum q_d x_d| <= 2^-11 |q||x| + 2^-25 sqrt(128) |q|
+//   |FP32 dot - sum q_d x~_d| <= gamma_128 (1 + 2^-11) |q||x|  (any summation order)
+// so ub = RU(dot + e16) >= the similarity, e16 = RU(|q| (|x|max c1 + c2)).  Only survivors
+// with ub >= cut are read in FP32 and pass through the band and binary64 steps of k_rescore;
+// cut starts at T_q (the threshold candidates' certified lower bound) and rises with the
+// FP32 best as in k_rescore_bf.  A survivor with ub < cut has similarity < cut <= the best
+// similarity, so it can neither win nor tie the winner: the answer is unchanged.
+__device__ inline float rescore16_slack(float qn, float xn_max) {
+    constexpr float c1 = 4.96e-4f;   // >= 2^-11 + gamma_128 (1 + 2^-11) + 1e-12
+    constexpr float c2 = 3.4e-7f;    // >= 2^-25 sqrt(128)
+    return __fmul_ru(qn, __fadd_ru(__fmul_ru(xn_max, c1), c2));
+}
+
+// Up to 32 kept survivors of one query (bit src of mk: the survivor whose id lane src holds):
+// their FP32 full scores, eight warp-cooperative rows at a time, into the band state.
+__device__ __forceinline__ void rescore_kept(unsigned mk, int32_t lane_id, const float *__restrict__ rows,
+                                             float4 qv, float band, int lane, float &best32, float &cval,
+                                             int32_t &cidx, int &ncand, bool &spill) {
+    constexpr int V = 8;
+    while (mk) {
+        int32_t id[V];
+        float full[V];
+#pragma unroll
+        for (int t = 0; t < V; ++t) {
+            const int src = mk ? __ffs(mk) - 1 : 0;
+            const bool live = mk != 0;
+            if (mk) mk &= mk - 1;
+            id[t] = __shfl_sync(0xffffffffu, lane_id, src);
+            if (!live) id[t] = -1;
+            float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (id[t] >= 0) xv = reinterpret_cast<const float4 *>(rows + (int64_t)id[t] * kD)[lane];
+            full[t] = fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w)));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+#pragma unroll
+            for (int t = 0; t < V; ++t) full[t] += __shfl_xor_sync(0xffffffffu, full[t], o);
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+            if (id[t] >= 0) band_push(full[t], id[t], band, lane, best32, cval, cidx, ncand, spill);
+    }
+}
+
+// Queries with at most this many survivors bound them one per lane (each lane reads its
+// row's 256 B itself); queries with more use one coalesced warp access per row, sixteen rows
+// in flight.  Measured on B300: one per lane is faster at a few hundred survivors a query
+// (c2: 2.01 against 2.41 ms), the warp-wide form at thousands (c4's K = 8, alpha = 1/8
+// indexes, about 17 thousand a query).
+constexpr int kRescoreLaneMax = 2048;
+
+__global__ void __launch_bounds__(256) k_rescore16(const float *__restrict__ rows, const __half *__restrict__ rows16,
+                                                   const float *__restrict__ q, int64_t nq,
+                                                   const int32_t *__restrict__ bucket,
+                                                   const int32_t *__restrict__ count, int cap,
+                                                   const float *__restrict__ qnorm, float xnorm_max,
+                                                   const float *__restrict__ tlow, int64_t *__restrict__ out_idx,
+                                                   double *__restrict__ out_sim, int32_t *__restrict__ status,
+                                                   long long *__restrict__ counters) {
+    __shared__ float4 qsh[8][kD / 4];  // each warp's query, read by broadcast (one survivor a lane)
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    const int cnt = count[j];
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SURVIVORS), (unsigned long long)cnt);
+        atomicMax(reinterpret_cast<unsigned long long *>(counters + CT_MAXSURV), (unsigned long long)cnt);
+    }
+    if (cnt > cap) {
+        if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
+        return;
+    }
+    // lane l holds query coordinates 4l .. 4l+3 (warp-cooperative rows)
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    const float eps = rescore_eps(qnorm[j], xnorm_max);
+    const float e16 = rescore16_slack(qnorm[j], xnorm_max);
+    const float band = __fmul_ru(2.f, eps);
+    const int32_t *bk = bucket + j * (int64_t)cap;
+    float best32 = -INFINITY;
+    float cval = -INFINITY;
+    int32_t cidx = -1;
+    int ncand = 0;
+    bool spill = false;
+    float cut = tlow[j];
+    int kept_total = 0;
+    if (cnt <= kRescoreLaneMax) {
+        qsh[wib][lane] = qv;
+        __syncwarp();
+        const float4 *qs = qsh[wib];
+        for (int s0 = 0; s0 < cnt; s0 += 32) {
+            const int s = s0 + lane;
+            const int32_t my_id = s < cnt ? bk[s] : -1;
+            bool keep = false;
+            if (my_id >= 0) {
+                // this lane's survivor: FP32 dot over its FP16 row, four partial sums
+                const uint4 *r = reinterpret_cast<const uint4 *>(rows16 + (int64_t)my_id * kD);
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                for (int i = 0; i < kD / 8; ++i) {
+                    const uint4 v = __ldg(r + i);
+                    const float4 qa = qs[2 * i], qb = qs[2 * i + 1];
+                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+                    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+                    const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&v.z));
+                    const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&v.w));
+                    a0 = fmaf(qa.x, f0.x, fmaf(qa.y, f0.y, a0));
+                    a1 = fmaf(qa.z, f1.x, fmaf(qa.w, f1.y, a1));
+                    a2 = fmaf(qb.x, f2.x, fmaf(qb.y, f2.y, a2));
+                    a3 = fmaf(qb.z, f3.x, fmaf(qb.w, f3.y, a3));
+                }
+                keep = __fadd_ru((a0 + a1) + (a2 + a3), e16) >= cut;
+            }
+            const unsigned mk = __ballot_sync(0xffffffffu, keep);
+            kept_total += __popc(mk);
+            rescore_kept(mk, my_id, rows, qv, band, lane, best32, cval, cidx, ncand, spill);
+            cut = fmaxf(cut, __fsub_rd(best32, eps));
+        }
+    } else {
+        constexpr int U = 16;  // FP16 rows in flight: one coalesced 256 B access each
+        for (int s0 = 0; s0 < cnt; s0 += U) {
+            // the batch's survivor ids: lane u < U reads one, the warp shares them
+            const int32_t my_id = (lane < U && s0 + lane < cnt) ? bk[s0 + lane] : -1;
+            float part[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t id = __shfl_sync(0xffffffffu, my_id, u);
+                uint2 v = make_uint2(0u, 0u);
+                if (id >= 0) v = __ldg(reinterpret_cast<const uint2 *>(rows16 + (int64_t)id * kD) + lane);
+                const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+                const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+                part[u] = fmaf(qv.x, f0.x, fmaf(qv.y, f0.y, fmaf(qv.z, f1.x, qv.w * f1.y)));
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
+            // the butterfly leaves the same sum in every lane: the kept bits are warp-uniform
+            unsigned mk = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (s0 + u < cnt && __fadd_ru(part[u], e16) >= cut) mk |= 1u << u;
+            kept_total += __popc(mk);
+            rescore_kept(mk, my_id, rows, qv, band, lane, best32, cval, cidx, ncand, spill);
+            cut = fmaxf(cut, __fsub_rd(best32, eps));
+        }
+    }
+    if (lane == 0 && cnt > kept_total)
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SKIPPED), (unsigned long long)(cnt - kept_total));
+    rescore_finish(rows, q, j, bk, cnt, lane, spill, ncand, cidx, out_idx, out_sim, counters);
+}
+
 // Exact top-kk (1 <= kk <= 32), one warp per query.  Pass 1 finds f_k, the kk-th
 // largest FP32 score among the survivors (lane r holds the r-th largest value).
 // Every entry of the exact top-kk has binary64 score >= f_k - eps_r (kk survivors
@@ -989,9 +1145,13 @@ cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int
 }
 
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
-                           cudaStream_t st, bool best_first) {
+                           cudaStream_t st, int mode) {
     const int64_t blocks = (nq * 32 + 255) / 256;
-    if (best_first)
+    if (mode == HN_RESCORE_FILTER16 && ix.rows16)
+        k_rescore16<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, ix.rows16, q, nq, ix.ws.bucket, ix.ws.count,
+                                                      ix.ws.bucket_cap, ix.ws.qnorm, ix.host_max[4], ix.ws.tlow,
+                                                      out_idx, out_sim, ix.ws.status, ix.ws.counters);
+    else if (mode == HN_RESCORE_BEST_FIRST)
         k_rescore_bf<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
                                                        ix.ws.qnorm, ix.host_max[4], ix.ws.qeps32, ix.ws.tlow, ix.k, out_idx,
                                                        out_sim, ix.ws.status, ix.ws.counters);

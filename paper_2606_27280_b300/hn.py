@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_NOT_NORMALIZED, ERR_ZERO_NORM, ERR_OOM, ERR_CUDA, ERR_T
     ERR_UNSUPPORTED = range(9)
 PREFIX_F32, PREFIX_BF16, PREFIX_FP8, PREFIX_I8 = 0, 1, 2, 3
 SCAN_AUTO, SCAN_STREAM, SCAN_DENSE, SCAN_DENSE_TWO_PASS = 0, 1, 2, 3
+RESCORE_FILTER16, RESCORE_BEST_FIRST, RESCORE_FULL = 0, 1, 2
 D = 128
 
 _STATUS_NAMES = {0: "HN_OK", 1: "HN_ERR_INVALID_ARG", 2: "HN_ERR_NOT_NORMALIZED", 3: "HN_ERR_ZERO_NORM",
@@ -35,7 +36,7 @@ class SearchOpts(ctypes.Structure):
     _fields_ = [("scan", ctypes.c_int32), ("bucket_cap", ctypes.c_int32), ("timing", ctypes.c_int32),
                 ("seed_topk", ctypes.c_int32), ("seed", ctypes.c_void_p), ("soft", ctypes.c_int32),
                 ("beta", ctypes.c_float), ("scratch_limit", ctypes.c_int64), ("wait_limit_ns", ctypes.c_uint64),
-                ("best_first", ctypes.c_int32), ("test_stall", ctypes.c_int32),
+                ("rescore", ctypes.c_int32), ("test_stall", ctypes.c_int32),
                 ("test_plain_epilogue", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
@@ -274,15 +275,17 @@ class Index:
                timing: bool = False,
                out_idx: torch.Tensor | None = None, out_sim: torch.Tensor | None = None,
                proposal: "Proposal | None" = None, seed_topk: int = 0, beta: float | None = None,
-               scratch_limit: int = 0, wait_limit_ns: int = 0, best_first: bool = False,
+               scratch_limit: int = 0, wait_limit_ns: int = 0, best_first: bool = False, rescore: int | None = None,
                test_stall: bool = False, test_plain_epilogue: bool = False, stream=None) -> SearchResult:
         """Exact 1-NN of every row of q (HN-normalised, float32, device).  With a trained
         `proposal`, its top `seed_topk` blocks give the threshold and Phase 1 is skipped.
         `beta` (0 <= beta <= alpha) selects the soft ANN mode: alpha in the skip test becomes
         beta (beta = alpha is exact).  `scratch_limit` caps the bytes of the dense scan's group
         map (larger batches run in passes); `wait_limit_ns` sets the dense scan's device-side
-        wait limit (0 = 2 s).  `best_first` rescores the survivor of best prefix score first and
-        drops the others whose prefix bound cannot reach it (same result).  `test_stall`
+        wait limit (0 = 2 s).  `rescore` picks how Phase 2 scores the survivors (same result):
+        RESCORE_FILTER16 (default) bounds each from its FP16 row and reads the FP32 row only where
+        the bound reaches the best certified score; RESCORE_BEST_FIRST (also `best_first=True`)
+        uses the FP32 prefix bound; RESCORE_FULL scores every survivor in FP32.  `test_stall`
         (failure-path tests only) withholds the scan's copies after each CTA's first work unit,
         so its waits run out after `wait_limit_ns` and the call raises HN_ERR_TIMEOUT.
         `test_plain_epilogue` (tests only) runs the one-pass scan's unsplit form, the fallback
@@ -297,7 +300,8 @@ class Index:
                           seed_topk=int(seed_topk), seed=proposal._h.value if proposal is not None else None,
                           soft=int(beta is not None), beta=float(beta) if beta is not None else 0.0,
                           scratch_limit=int(scratch_limit), wait_limit_ns=int(wait_limit_ns),
-                          best_first=int(bool(best_first)), test_stall=int(bool(test_stall)),
+                          rescore=int(rescore) if rescore is not None else (RESCORE_BEST_FIRST if best_first else RESCORE_FILTER16),
+                          test_stall=int(bool(test_stall)),
                           test_plain_epilogue=int(bool(test_plain_epilogue)))
         st = SearchStats() if (stats or timing) else None
         _check(_lib.hn_search_batch(self._h, q.data_ptr(), nq, ctypes.byref(opts), out_idx.data_ptr(),

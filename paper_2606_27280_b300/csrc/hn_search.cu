@@ -881,13 +881,15 @@ __device__ __forceinline__ void rescore_kept(unsigned mk, int32_t lane_id, const
 }
 
 // Queries with at most this many survivors bound them one per lane (each lane reads its
-// row's 256 B itself); queries with more use one coalesced warp access per row, sixteen rows
-// in flight.  Measured on B300: one per lane is faster at a few hundred survivors a query
-// (c2: 2.01 against 2.41 ms), the warp-wide form at thousands (c4's K = 8, alpha = 1/8
-// indexes, about 17 thousand a query).
+// row's 256 B itself); queries with more give each survivor eight lanes (32 B of the row a
+// lane, four survivors per load instruction, so a row costs two cache-line requests instead
+// of sixteen).  Measured on B300: one per lane is faster at a few hundred survivors a query
+// (c2), eight lanes at thousands (c4's K = 8, alpha = 1/8 indexes, about 17 thousand a
+// query).  Both forms stay in one launch (a second launch for the large queries left them
+// as a serial tail), bounded to four blocks per SM.
 constexpr int kRescoreLaneMax = 2048;
 
-__global__ void __launch_bounds__(256) k_rescore16(const float *__restrict__ rows, const __half *__restrict__ rows16,
+__global__ void __launch_bounds__(256, 4) k_rescore16(const float *__restrict__ rows, const __half *__restrict__ rows16,
                                                    const float *__restrict__ q, int64_t nq,
                                                    const int32_t *__restrict__ bucket,
                                                    const int32_t *__restrict__ count, int cap,
@@ -908,7 +910,7 @@ __global__ void __launch_bounds__(256) k_rescore16(const float *__restrict__ row
         if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
         return;
     }
-    // lane l holds query coordinates 4l .. 4l+3 (warp-cooperative rows)
+    // lane l holds query coordinates 4l .. 4l+3 (warp-cooperative FP32 rows)
     const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
     const float eps = rescore_eps(qnorm[j], xnorm_max);
     const float e16 = rescore16_slack(qnorm[j], xnorm_max);
@@ -921,10 +923,10 @@ __global__ void __launch_bounds__(256) k_rescore16(const float *__restrict__ row
     bool spill = false;
     float cut = tlow[j];
     int kept_total = 0;
+    qsh[wib][lane] = qv;
+    __syncwarp();
+    const float4 *qs = qsh[wib];
     if (cnt <= kRescoreLaneMax) {
-        qsh[wib][lane] = qv;
-        __syncwarp();
-        const float4 *qs = qsh[wib];
         for (int s0 = 0; s0 < cnt; s0 += 32) {
             const int s = s0 + lane;
             const int32_t my_id = s < cnt ? bk[s] : -1;
@@ -954,31 +956,49 @@ __global__ void __launch_bounds__(256) k_rescore16(const float *__restrict__ row
             cut = fmaxf(cut, __fsub_rd(best32, eps));
         }
     } else {
-        constexpr int U = 16;  // FP16 rows in flight: one coalesced 256 B access each
-        for (int s0 = 0; s0 < cnt; s0 += U) {
-            // the batch's survivor ids: lane u < U reads one, the warp shares them
-            const int32_t my_id = (lane < U && s0 + lane < cnt) ? bk[s0 + lane] : -1;
+        // eight lanes a survivor: lane 8g + t reads bytes 32t .. 32t+31 of the FP16 row of
+        // survivor 4u + g of the batch against query coordinates 16t .. 16t+15 (shared memory)
+        const int g = lane >> 3, t = lane & 7;
+        const float4 *qt = qs + 4 * t;
+        constexpr int U = 4;  // 16 survivors a batch, two 16-byte loads a lane each
+        for (int s0 = 0; s0 < cnt; s0 += 4 * U) {
+            int32_t sid[U];
             float part[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int32_t id = __shfl_sync(0xffffffffu, my_id, u);
-                uint2 v = make_uint2(0u, 0u);
-                if (id >= 0) v = __ldg(reinterpret_cast<const uint2 *>(rows16 + (int64_t)id * kD) + lane);
-                const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
-                const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
-                part[u] = fmaf(qv.x, f0.x, fmaf(qv.y, f0.y, fmaf(qv.z, f1.x, qv.w * f1.y)));
-            }
+                const int s = s0 + 4 * u + g;
+                sid[u] = s < cnt ? bk[s] : -1;
+                uint4 v0 = make_uint4(0u, 0u, 0u, 0u), v1 = v0;
+                if (sid[u] >= 0) {
+                    const uint4 *r = reinterpret_cast<const uint4 *>(rows16 + (int64_t)sid[u] * kD + 16 * t);
+                    v0 = __ldg(r);
+                    v1 = __ldg(r + 1);
+                }
+                const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int o = 16; o; o >>= 1)
+                for (int i = 0; i < 8; i += 2) {
+                    const float4 qa = qt[i >> 1];
+                    const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+                    const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&w[i + 1]));
+                    a0 = fmaf(qa.x, f0.x, fmaf(qa.y, f0.y, a0));
+                    a1 = fmaf(qa.z, f1.x, fmaf(qa.w, f1.y, a1));
+                }
+                part[u] = a0 + a1;
+            }
+            // the octet's butterfly leaves the same sum in its eight lanes
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
                 for (int u = 0; u < U; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], o);
-            // the butterfly leaves the same sum in every lane: the kept bits are warp-uniform
-            unsigned mk = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (s0 + u < cnt && __fadd_ru(part[u], e16) >= cut) mk |= 1u << u;
-            kept_total += __popc(mk);
-            rescore_kept(mk, my_id, rows, qv, band, lane, best32, cval, cidx, ncand, spill);
+            for (int u = 0; u < U; ++u) {
+                // lanes 0, 8, 16, 24 vote for survivors 4u .. 4u+3 and hold their ids
+                const bool keep = t == 0 && sid[u] >= 0 && __fadd_ru(part[u], e16) >= cut;
+                const unsigned mk = __ballot_sync(0xffffffffu, keep);
+                kept_total += __popc(mk);
+                rescore_kept(mk, sid[u], rows, qv, band, lane, best32, cval, cidx, ncand, spill);
+            }
             cut = fmaxf(cut, __fsub_rd(best32, eps));
         }
     }
@@ -1147,11 +1167,11 @@ cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx, double *out_sim,
                            cudaStream_t st, int mode) {
     const int64_t blocks = (nq * 32 + 255) / 256;
-    if (mode == HN_RESCORE_FILTER16 && ix.rows16)
+    if (mode == HN_RESCORE_FILTER16 && ix.rows16) {
         k_rescore16<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, ix.rows16, q, nq, ix.ws.bucket, ix.ws.count,
                                                       ix.ws.bucket_cap, ix.ws.qnorm, ix.host_max[4], ix.ws.tlow,
                                                       out_idx, out_sim, ix.ws.status, ix.ws.counters);
-    else if (mode == HN_RESCORE_BEST_FIRST)
+    } else if (mode == HN_RESCORE_BEST_FIRST)
         k_rescore_bf<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
                                                        ix.ws.qnorm, ix.host_max[4], ix.ws.qeps32, ix.ws.tlow, ix.k, out_idx,
                                                        out_sim, ix.ws.status, ix.ws.counters);

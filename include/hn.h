@@ -134,7 +134,9 @@ typedef struct hn_search_opts {
                              scored in FP32.  HN_RESCORE_BEST_FIRST (1): the early exit the remark
                              after Algorithm 1 describes for a sorted Phase 2, with the FP32 prefix
                              score as the bound.  HN_RESCORE_FULL (2): every survivor scored in
-                             FP32 in slot order (Algorithm 1's Phase 2 in index order) */
+                             FP32 in slot order (Algorithm 1's Phase 2 in index order).
+                             hn_search_topk: HN_RESCORE_FILTER16 bounds against the k-th best
+                             certified score; the other two score every survivor in FP32 */
     int32_t test_stall;   /* failure-path test hook, 0 in normal use.  1: in every dense-scan launch
                              of this call, each CTA's copy producer stops after the CTA's first work
                              unit, so the MMA warps wait for a query copy that never comes; that

@@ -351,7 +351,7 @@ static hn_status run_search(Index &ix, const float *q, int64_t nq, int scan, con
         HN_CUDA(scan != HN_SCAN_STREAM ? launch_dense_scan(ix, nq, 2, s) : launch_stream_scan(ix, nq, 2, s));
         HN_CUDA(mark(4));
     }
-    HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s)
+    HN_CUDA(nn > 1 ? launch_rescore_topk(ix, q, nq, nn, out_idx, out_sim, s, rescore)
                    : launch_rescore(ix, q, nq, out_idx, out_sim, s, rescore));
     HN_CUDA(mark(5));
     return HN_OK;

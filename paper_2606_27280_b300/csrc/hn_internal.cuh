@@ -233,7 +233,7 @@ cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, in
 cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *out, cudaStream_t s);
 // Exact top-kk of every query from its Phase-2 survivors (1 <= kk <= 32): out_idx/out_sim [nq][kk].
 cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
-                                double *out_sim, cudaStream_t s);
+                                double *out_sim, cudaStream_t s, int mode = HN_RESCORE_FILTER16);
 // mode (hn_rescore): the FP16-row filter (default), the best-first prefix bound (f4), or every
 // survivor in FP32
 cudaError_t launch_rescore(const Index &ix, const float *q, int64_t nq, int64_t *out_idx,

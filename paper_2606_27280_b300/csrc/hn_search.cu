@@ -1018,6 +1018,69 @@ __device__ inline bool topk_before(double s, int64_t i, double s2, int64_t i2) {
     return i2 < 0 || (i >= 0 && (s > s2 || (s == s2 && i < i2)));
 }
 
+// The binary64 step of the top-kk rescore: the band members (member m at lane m % 32, slot
+// m / 32), or after a spill every survivor, scored in the oracle's order, and the kk best
+// by (score desc, index asc) written out.
+__device__ __forceinline__ void topk_finish(const float *__restrict__ rows, const float *__restrict__ q, int64_t j,
+                                            const int32_t *bk, int cnt, int kk, int lane, bool spill, int nm,
+                                            int32_t m0, int32_t m1, int64_t *__restrict__ out_idx,
+                                            double *__restrict__ out_sim, long long *__restrict__ counters) {
+    const float *qj = q + j * kD;
+    double prev_s = INFINITY;
+    int64_t prev_i = -1;
+    if (!spill) {
+        double v0 = -INFINITY, v1 = -INFINITY;
+        if (m0 >= 0) v0 = dot64_seq(qj, rows + (int64_t)m0 * kD);
+        if (m1 >= 0) v1 = dot64_seq(qj, rows + (int64_t)m1 * kD);
+        bool t0 = m0 < 0, t1 = m1 < 0;  // taken (or empty)
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)nm);
+        for (int r = 0; r < kk; ++r) {
+            double bs = -INFINITY;
+            int64_t bi = -1;
+            if (!t0) { bs = v0; bi = m0; }
+            if (!t1 && topk_before(v1, m1, bs, bi)) { bs = v1; bi = m1; }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
+            }
+            if (!t0 && bi == m0) t0 = true;
+            else if (!t1 && bi == m1) t1 = true;
+            if (lane == 0) {
+                out_idx[j * kk + r] = bi;
+                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+            }
+        }
+    } else {
+        // more than 64 band members: binary64 for every survivor, one rank per sweep
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt * kk);
+        for (int r = 0; r < kk; ++r) {
+            double bs = -INFINITY;
+            int64_t bi = -1;
+            for (int t = lane; t < cnt; t += 32) {
+                const int32_t id = bk[t];
+                const double v = dot64_seq(qj, rows + (int64_t)id * kD);
+                // eligible: after the previous rank in (score desc, index asc) order
+                if (prev_i >= 0 && !topk_before(prev_s, prev_i, v, id)) continue;
+                if (topk_before(v, id, bs, bi)) { bs = v; bi = id; }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
+            }
+            prev_s = bs;
+            prev_i = bi;
+            if (lane == 0) {
+                out_idx[j * kk + r] = bi;
+                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_rescore_topk(const float *__restrict__ rows, const float *__restrict__ q,
                                                       int64_t nq, const int32_t *__restrict__ bucket,
                                                       const int32_t *__restrict__ count, int cap,
@@ -1099,65 +1162,167 @@ __global__ void __launch_bounds__(256) k_rescore_topk(const float *__restrict__ 
             }
         }
     }
-    const float *qj = q + j * kD;
-    double prev_s = INFINITY;
-    int64_t prev_i = -1;
-    if (!spill) {
-        double v0 = -INFINITY, v1 = -INFINITY;
-        if (m0 >= 0) v0 = dot64_seq(qj, rows + (int64_t)m0 * kD);
-        if (m1 >= 0) v1 = dot64_seq(qj, rows + (int64_t)m1 * kD);
-        bool t0 = m0 < 0, t1 = m1 < 0;  // taken (or empty)
-        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)nm);
-        for (int r = 0; r < kk; ++r) {
-            double bs = -INFINITY;
-            int64_t bi = -1;
-            if (!t0) { bs = v0; bi = m0; }
-            if (!t1 && topk_before(v1, m1, bs, bi)) { bs = v1; bi = m1; }
+    topk_finish(rows, q, j, bk, cnt, kk, lane, spill, nm, m0, m1, out_idx, out_sim, counters);
+}
+
+// Exact top-kk with the FP16-row filter (the default): a survivor whose FP16-row bound stays
+// below cut = max(T_q, RD(f - eps_r)), T_q the kk-th largest certified bound of the threshold
+// candidates and f the kk-th largest FP32 score so far, has similarity below the kk-th largest
+// similarity, so it is not in the answer.  Only the kept survivors are read in FP32; their
+// scores go into the running top-kk (pass 1) and a per-warp cache of kTopkCache, from which
+// pass 2 takes the band members (FP32 score >= f_k - 2 eps_r) without reading a row again.
+// Every member of the exact top-kk is kept (its bound reaches its similarity >= the cut) and
+// f_k <= the kk-th similarity + eps_r, so each of them is a band member, as in k_rescore_topk.
+// A cache overflow makes pass 2 bound the survivors again against the final cut.
+constexpr int kTopkCache = 128;
+
+__global__ void __launch_bounds__(256) k_rescore_topk16(const float *__restrict__ rows,
+                                                        const __half *__restrict__ rows16,
+                                                        const float *__restrict__ q, int64_t nq,
+                                                        const int32_t *__restrict__ bucket,
+                                                        const int32_t *__restrict__ count, int cap,
+                                                        const float *__restrict__ qnorm, float xnorm_max,
+                                                        const float *__restrict__ tlow, int kk,
+                                                        int64_t *__restrict__ out_idx, double *__restrict__ out_sim,
+                                                        int32_t *__restrict__ status, long long *__restrict__ counters) {
+    __shared__ float4 qsh[8][kD / 4];
+    __shared__ int32_t cid[8][kTopkCache];
+    __shared__ float csc[8][kTopkCache];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nq) return;
+    const int cnt = count[j];
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SURVIVORS), (unsigned long long)cnt);
+        atomicMax(reinterpret_cast<unsigned long long *>(counters + CT_MAXSURV), (unsigned long long)cnt);
+    }
+    if (cnt > cap) {
+        if (lane == 0) atomicExch(status + ST_OVERFLOW, 1);
+        return;
+    }
+    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
+    qsh[wib][lane] = qv;
+    __syncwarp();
+    const float4 *qs = qsh[wib];
+    const float eps = rescore_eps(qnorm[j], xnorm_max);
+    const float e16 = rescore16_slack(qnorm[j], xnorm_max);
+    const float band = __fmul_ru(2.f, eps);
+    const int32_t *bk = bucket + j * (int64_t)cap;
+    const float t0 = tlow[j];
+    // the FP16-row bound of survivor s (one lane each)
+    auto bound16 = [&](int s) {
+        const uint4 *r = reinterpret_cast<const uint4 *>(rows16 + (int64_t)bk[s] * kD);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
+        for (int i = 0; i < kD / 8; ++i) {
+            const uint4 v = __ldg(r + i);
+            const float4 qa = qs[2 * i], qb = qs[2 * i + 1];
+            const float2 f0 = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+            const float2 f1 = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+            const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&v.z));
+            const float2 f3 = __half22float2(*reinterpret_cast<const __half2 *>(&v.w));
+            a0 = fmaf(qa.x, f0.x, fmaf(qa.y, f0.y, a0));
+            a1 = fmaf(qa.z, f1.x, fmaf(qa.w, f1.y, a1));
+            a2 = fmaf(qb.x, f2.x, fmaf(qb.y, f2.y, a2));
+            a3 = fmaf(qb.z, f3.x, fmaf(qb.w, f3.y, a3));
+        }
+        return __fadd_ru((a0 + a1) + (a2 + a3), e16);
+    };
+    // FP32 full score of the survivor whose id lane src holds (warp-cooperative row)
+    auto full32 = [&](int32_t id) {
+        const float4 xv = reinterpret_cast<const float4 *>(rows + (int64_t)id * kD)[lane];
+        float v = fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w)));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    // pass 1: the kk largest FP32 scores of the kept survivors, descending over lanes 0 .. kk-1
+    float top = -INFINITY;
+    int filled = 0, ncache = 0;
+    long long kept_total = 0;
+    float cut = t0;
+    for (int s0 = 0; s0 < cnt; s0 += 32) {
+        const int s = s0 + lane;
+        const int32_t my_id = s < cnt ? bk[s] : -1;
+        const bool keep = my_id >= 0 && bound16(s) >= cut;
+        unsigned mk = __ballot_sync(0xffffffffu, keep);
+        kept_total += __popc(mk);
+        while (mk) {
+            const int src = __ffs(mk) - 1;
+            mk &= mk - 1;
+            const int32_t id = __shfl_sync(0xffffffffu, my_id, src);
+            const float v = full32(id);
+            if (ncache < kTopkCache && lane == 0) {
+                cid[wib][ncache] = id;
+                csc[wib][ncache] = v;
             }
-            if (!t0 && bi == m0) t0 = true;
-            else if (!t1 && bi == m1) t1 = true;
-            if (lane == 0) {
-                out_idx[j * kk + r] = bi;
-                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+            ++ncache;
+            const float kth = __shfl_sync(0xffffffffu, top, kk - 1);
+            if (filled < kk || v > kth) {
+                const int p = __popc(__ballot_sync(0xffffffffu, lane < filled && top >= v));
+                const float up = __shfl_up_sync(0xffffffffu, top, 1);
+                if (lane > p && lane < kk) top = up;
+                if (lane == p) top = v;
+                filled = filled < kk ? filled + 1 : kk;
+            }
+        }
+        if (filled >= kk) cut = fmaxf(cut, __fsub_rd(__shfl_sync(0xffffffffu, top, kk - 1), eps));
+    }
+    __syncwarp();
+    const float fk = filled >= kk ? __shfl_sync(0xffffffffu, top, kk - 1) : -INFINITY;
+    const float lo = fk == -INFINITY ? -INFINITY : __fsub_rd(fk, band);
+    // pass 2: band members, member m at lane m % 32, slot m / 32
+    int32_t m0 = -1, m1 = -1;
+    int nm = 0;
+    bool spill = false;
+    auto add_member = [&](int32_t id) {
+        if (nm < 64) {
+            if (lane == (nm & 31)) {
+                if (nm < 32) m0 = id; else m1 = id;
+            }
+            ++nm;
+        } else {
+            spill = true;
+        }
+    };
+    if (ncache <= kTopkCache) {
+        for (int c0 = 0; c0 < ncache; c0 += 32) {
+            const int c = c0 + lane;
+            const int32_t my_id = c < ncache ? cid[wib][c] : -1;
+            unsigned mb = __ballot_sync(0xffffffffu, c < ncache && csc[wib][c] >= lo);
+            while (mb) {
+                const int src = __ffs(mb) - 1;
+                mb &= mb - 1;
+                add_member(__shfl_sync(0xffffffffu, my_id, src));
             }
         }
     } else {
-        // more than 64 band members: binary64 for every survivor, one rank per sweep
-        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_FP64), (unsigned long long)cnt * kk);
-        for (int r = 0; r < kk; ++r) {
-            double bs = -INFINITY;
-            int64_t bi = -1;
-            for (int t = lane; t < cnt; t += 32) {
-                const int32_t id = bk[t];
-                const double v = dot64_seq(qj, rows + (int64_t)id * kD);
-                // eligible: after the previous rank in (score desc, index asc) order
-                if (prev_i >= 0 && !topk_before(prev_s, prev_i, v, id)) continue;
-                if (topk_before(v, id, bs, bi)) { bs = v; bi = id; }
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-                const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (topk_before(os, oi, bs, bi)) { bs = os; bi = oi; }
-            }
-            prev_s = bs;
-            prev_i = bi;
-            if (lane == 0) {
-                out_idx[j * kk + r] = bi;
-                out_sim[j * kk + r] = bi >= 0 ? bs : -INFINITY;
+        for (int s0 = 0; s0 < cnt; s0 += 32) {
+            const int s = s0 + lane;
+            const int32_t my_id = s < cnt ? bk[s] : -1;
+            unsigned mk = __ballot_sync(0xffffffffu, my_id >= 0 && bound16(s) >= cut);
+            while (mk) {
+                const int src = __ffs(mk) - 1;
+                mk &= mk - 1;
+                const int32_t id = __shfl_sync(0xffffffffu, my_id, src);
+                if (full32(id) >= lo) add_member(id);
             }
         }
     }
+    if (lane == 0 && cnt > kept_total)
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + CT_SKIPPED), (unsigned long long)(cnt - kept_total));
+    topk_finish(rows, q, j, bk, cnt, kk, lane, spill, nm, m0, m1, out_idx, out_sim, counters);
 }
 
 cudaError_t launch_rescore_topk(const Index &ix, const float *q, int64_t nq, int kk, int64_t *out_idx,
-                                double *out_sim, cudaStream_t st) {
+                                double *out_sim, cudaStream_t st, int mode) {
     const int64_t blocks = (nq * 32 + 255) / 256;
+    if (mode == HN_RESCORE_FILTER16 && ix.rows16) {
+        k_rescore_topk16<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, ix.rows16, q, nq, ix.ws.bucket, ix.ws.count,
+                                                           ix.ws.bucket_cap, ix.ws.qnorm, ix.host_max[4], ix.ws.tlow,
+                                                           kk, out_idx, out_sim, ix.ws.status, ix.ws.counters);
+        return cudaGetLastError();
+    }
     k_rescore_topk<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.ws.bucket, ix.ws.count, ix.ws.bucket_cap,
                                                      ix.ws.qnorm, ix.host_max[4], kk, out_idx, out_sim, ix.ws.status,
                                                      ix.ws.counters);

@@ -317,6 +317,9 @@ __device__ __forceinline__ void tmem_ld64h_issue(uint32_t taddr, uint32_t (&r)[3
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// The reducing loads write every loaded value to a scratch register that is never read:
+// silence the front end's "set but never used" for these two helpers only.
+#pragma nv_diag_suppress 550
 // Maximum of 32 consecutive FP32 columns of this thread's TMEM lane (taddr ..
 // taddr + 31), computed by the load itself (tcgen05.ld.red, sm_103a), waited for.
 __device__ __forceinline__ float tmem_ldmax32(uint32_t taddr) {
@@ -344,6 +347,7 @@ __device__ __forceinline__ void tmem_ldmax2x32(uint32_t taddr, float &m0, float 
         : "memory");
     (void)v;
 }
+#pragma nv_diag_default 550
 
 __device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[32]) {
     asm volatile(""

@@ -310,14 +310,15 @@ class Index:
         return SearchResult(out_idx, out_sim, st.as_dict() if st is not None else None)
 
     def search_topk(self, q: torch.Tensor, k: int, scan: int = SCAN_AUTO, bucket_cap: int = 0,
-                    stats: bool = False, stream=None) -> SearchResult:
+                    stats: bool = False, rescore: int = RESCORE_FILTER16, stream=None) -> SearchResult:
         """Exact top-k of every row of q: idx / sim of shape (nq, k), by similarity
-        descending then index ascending (rank 0 = the 1-NN)."""
+        descending then index ascending (rank 0 = the 1-NN).  `rescore`: RESCORE_FILTER16
+        (FP16-row bound first) or RESCORE_FULL (every survivor in FP32); same result."""
         q = _dev_f32(q, "q")
         nq = q.shape[0]
         out_idx = torch.empty((nq, k), dtype=torch.int64, device=q.device)
         out_sim = torch.empty((nq, k), dtype=torch.float64, device=q.device)
-        opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap))
+        opts = SearchOpts(scan=int(scan), bucket_cap=int(bucket_cap), rescore=int(rescore))
         st = SearchStats() if stats else None
         _check(_lib.hn_search_topk(self._h, q.data_ptr(), nq, int(k), ctypes.byref(opts), out_idx.data_ptr(),
                                    out_sim.data_ptr(), ctypes.byref(st) if st is not None else None,

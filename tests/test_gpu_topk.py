@@ -26,13 +26,14 @@ def _check(res, o_idx, o_sim):
     assert np.array_equal(gs, o_sim), "similarities differ from the oracle's binary64 values"
 
 
+@pytest.mark.parametrize("rescore", [0, 2])   # FP16-row filter (default), every survivor in FP32
 @pytest.mark.parametrize("k", [1, 2, 5, 16, 32])
 @pytest.mark.parametrize("prefix,scan", [(0, STREAM), (1, STREAM), (1, DENSE), (2, DENSE), (1, DENSE2), (2, DENSE2)])
-def test_topk_matches_oracle(hn, k, prefix, scan):
+def test_topk_matches_oracle(hn, k, prefix, scan, rescore):
     w, db, q, _, _ = oracle_case(20011, 700, 4000, 61, 16, 1 / 8)
     o_idx, o_sim = oracle.search_topk(db, q, k)
     with hn.Index(to_dev(db), 16, 1 / 8, prefix=prefix) as ix:
-        r = ix.search_topk(to_dev(q), k, scan=scan, stats=True)
+        r = ix.search_topk(to_dev(q), k, scan=scan, stats=True, rescore=rescore)
         assert r.stats["scan"] == scan
         _check(r, o_idx, o_sim)
         if k == 1:
@@ -90,3 +91,37 @@ def test_topk_rejects_bad_k(hn):
         for k in (0, 33, 101):
             with pytest.raises(hn.HNError):
                 ix.search_topk(to_dev(q), k)
+
+
+@pytest.mark.parametrize("k", [4, 32])
+def test_topk_filter_skips_survivors_on_noisy_data(hn, k):
+    """Many survivors (noisy data, K = 8, alpha = 1/8): the FP16-row bound against the k-th
+    best certified score drops most of them, the answer stays the oracle's, and the
+    survivor count is that of the full rescore."""
+    w, db, q, _, _ = oracle_case(20000, 400, 4000, 63, 8, 1 / 8, 0.3, 0.2)
+    o_idx, o_sim = oracle.search_topk(db, q, k)
+    with hn.Index(to_dev(db), 8, 1 / 8, prefix=1) as ix:
+        qd = to_dev(q)
+        full = ix.search_topk(qd, k, scan=DENSE, stats=True, rescore=2)
+        f16 = ix.search_topk(qd, k, scan=DENSE, stats=True)
+        _check(full, o_idx, o_sim)
+        _check(f16, o_idx, o_sim)
+        assert f16.stats["survivors"] == full.stats["survivors"]
+        assert full.stats["rescore_skipped"] == 0
+        assert f16.stats["rescore_skipped"] >= 0.8 * f16.stats["survivors"]
+
+
+def test_topk_filter_cache_overflow(hn):
+    """A query whose kept survivors pass the per-warp cache (128): every entry is a duplicate of
+    one of 40 rows, so the top-32 band holds far more than 128 kept survivors and pass 2 bounds
+    the survivors again; the answer (ties by index) is the oracle's."""
+    k, alpha = 16, 1 / 8
+    w = hn_synth.make_workload(4000, 8, 400, seed=64)
+    db = oracle.normalize(w.db_raw, k, alpha)
+    db = db[np.arange(4000) % 40]
+    q = oracle.normalize(w.q_raw, k, alpha)
+    q[0] = db[3]
+    o_idx, o_sim = oracle.search_topk(db, q, 32)
+    with hn.Index(to_dev(db), k, alpha, prefix=1) as ix:
+        for scan in (STREAM, DENSE):
+            _check(ix.search_topk(to_dev(q), 32, scan=scan), o_idx, o_sim)

@@ -197,6 +197,12 @@ template <int KP, int PHASE, bool F8, bool MULTI = false, bool REG = false>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_constant__ DenseParams p) {
     static_assert(!REG || PHASE == 4, "the register split serves the one-pass form");
     using C = DenseCfg<KP, PHASE, F8>;
+    // PAIR (one-pass BF16, at least two entry tiles a ring stage): an accumulator buffer holds
+    // one 128-query half of the unit against a pair of 128-entry tiles, written by ONE N = 256
+    // MMA per K step instead of two N = 128 MMAs (one per query half).  Issuer i takes query
+    // half i of every tile pair; TMEM use, the epilogue's loads per warp and the code words are
+    // unchanged.  Measured at c2: 13.10 -> 12.6 ms, the MMA issue sitting on the hand-off chain.
+    constexpr bool PAIR = PHASE == 4 && !F8 && C::kTPS >= 2;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
     uint8_t *sA = smem + C::kStages * C::kStageBytes;
@@ -304,31 +310,49 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                     // wait for every fill of the ring, even one holding none of this issuer's
                     // tiles, so that the parity of the next wait on the slot cannot alias
                     if (!(ok = mbar_wait(smem_u32(&b_full[stage]), sphase, abort_flag, p.wait_ns))) break;
-                    for (int j = 0; j < nt; ++j, ++g) {
-                        if ((uint32_t)(g & 1) != me) continue;
-                        if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, p.wait_ns))) break;
-                        tc_fence_after();
-                        const uint32_t b_addr = smem_u32(sB + stage * C::kStageBytes + j * C::kB);
-#pragma unroll
-                        for (int sub = 0; sub < kDQ / kTileQ; ++sub) {
+                    if (PAIR) {
+                        constexpr uint32_t idesc2 = idesc_bf16_f32(kTileQ, 2 * kDE);
+                        for (int j = 0; j < nt; j += 2) {
+                            if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, p.wait_ns))) break;
+                            tc_fence_after();
+                            const uint32_t b_addr = smem_u32(sB + stage * C::kStageBytes + j * C::kB);
 #pragma unroll
                             for (int kk = 0; kk < KP / 16; ++kk) {
-                                // A: two core matrices along K, 128 B apart (BF16: 16 columns; FP8: the hi
-                                // and lo bytes of 16 columns); 8-row groups KP*16 B apart; A tile `sub` =
-                                // query rows 128*sub .. 128*sub+127
-                                const uint64_t ad = smem_desc(a_addr + sub * kTileQ * KP * 2 + kk * 256, 128, KP * 16);
-                                if (F8) {
-                                    // entry side: the core matrix of columns 16kk.. read twice (K stride 0)
-                                    const uint64_t bd = smem_desc(b_addr + kk * 128, 0, KP * 8);
-                                    umma_f8(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                                } else {
-                                    const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
-                                    umma_bf16(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                const uint64_t ad = smem_desc(a_addr + me * kTileQ * KP * 2 + kk * 256, 128, KP * 16);
+                                const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
+                                umma_bf16(tmem + me * 256, ad, bd, idesc2, kk > 0 ? 1u : 0u);
+                            }
+                            umma_commit(smem_u32(&acc_full[me]));
+                            ++uses;
+                        }
+                        g += nt;
+                    } else {
+                        for (int j = 0; j < nt; ++j, ++g) {
+                            if ((uint32_t)(g & 1) != me) continue;
+                            if (!(ok = mbar_wait(smem_u32(&acc_empty[me]), (uses & 1) ^ 1, abort_flag, p.wait_ns))) break;
+                            tc_fence_after();
+                            const uint32_t b_addr = smem_u32(sB + stage * C::kStageBytes + j * C::kB);
+#pragma unroll
+                            for (int sub = 0; sub < kDQ / kTileQ; ++sub) {
+#pragma unroll
+                                for (int kk = 0; kk < KP / 16; ++kk) {
+                                    // A: two core matrices along K, 128 B apart (BF16: 16 columns; FP8: the hi
+                                    // and lo bytes of 16 columns); 8-row groups KP*16 B apart; A tile `sub` =
+                                    // query rows 128*sub .. 128*sub+127
+                                    const uint64_t ad = smem_desc(a_addr + sub * kTileQ * KP * 2 + kk * 256, 128, KP * 16);
+                                    if (F8) {
+                                        // entry side: the core matrix of columns 16kk.. read twice (K stride 0)
+                                        const uint64_t bd = smem_desc(b_addr + kk * 128, 0, KP * 8);
+                                        umma_f8(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                    } else {
+                                        const uint64_t bd = smem_desc(b_addr + kk * 256, 128, KP * 16);
+                                        umma_bf16(tmem + me * 256 + sub * kDE, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                                    }
                                 }
                             }
+                            umma_commit(smem_u32(&acc_full[me]));
+                            ++uses;
                         }
-                        umma_commit(smem_u32(&acc_full[me]));
-                        ++uses;
                     }
                     if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
                 }
@@ -358,9 +382,13 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
         // range and largest error term (k_f8_group_bounds).
         const int ew = warp - kEpiWarp0;
         const int quarter = warp & 3;             // TMEM lanes this warp may read: 32*quarter ..
-        const int grp = ew >> 3;                  // accumulator buffer (tile parity) this warp serves
-        const int sub = (ew >> 2) & 1;            // query A tile: accumulator columns 128*sub ..
-        const int row = sub * kTileQ + quarter * 32 + lane;
+        const int grp = ew >> 3;                  // accumulator buffer this warp serves
+        const int sub = (ew >> 2) & 1;
+        // PAIR: buffer grp = query half grp, columns 128*sub .. = tile 2p + sub of the pair;
+        // otherwise buffer grp = tile parity grp, columns 128*sub .. = query half sub
+        const int qh = PAIR ? grp : sub;          // query half of this warp's rows
+        const int tp = PAIR ? sub : grp;          // tile parity this warp reads
+        const int row = qh * kTileQ + quarter * 32 + lane;
         const bool releaser = (ew & 7) == 0 && lane == 0;  // hands this group's B stages back
         const uint32_t taddr = tmem + grp * 256 + sub * kDE + ((uint32_t)(quarter * 32) << 16);
         const uint32_t full_bar = smem_u32(&acc_full[grp]), empty_bar = smem_u32(&acc_empty[grp]);
@@ -377,14 +405,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             const int64_t wstride = gr.n_qt * kDQ;  // words between consecutive tiles of a query
             float best = -INFINITY;
             int32_t bgid = -1;  // the 32-entry group of `best`
-            uint32_t *gb = gr.gbits + ch * gr.words * wstride + q + grp * wstride;
+            uint32_t *gb = gr.gbits + ch * gr.words * wstride + q + tp * wstride;
             const int32_t n32 = (int32_t)gr.n;
             const float inv = gr.code_inv, base = p.code_base;
             // tile j sits in slot j % kTPS of stage unit_stage + j / kTPS (mod kStages)
-            int slot = grp % C::kTPS;
-            int stage = unit_stage + grp / C::kTPS;
+            int slot = tp % C::kTPS;
+            int stage = unit_stage + tp / C::kTPS;
             if (stage >= C::kStages) stage -= C::kStages;
-            for (int32_t j = grp; j < nt_u; j += 2, gb += 2 * wstride) {
+            for (int32_t j = tp; j < nt_u; j += 2, gb += 2 * wstride) {
                 // the warp leaves together: its TMEM loads and hand-offs below are warp-wide
                 ok = __all_sync(0xffffffffu, mbar_wait(full_bar, uses & 1u, abort_flag, p.wait_ns));
                 if (!ok) break;
@@ -392,7 +420,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                 tc_fence_after();
                 // this tile's MMAs are done with the stage; the unit's last tile also arrives
                 // for the slots its (short) stage did not fill
-                const uint32_t rel = j == nt_u - 1 ? (uint32_t)(C::kTPS - slot) : 1u;
+                // PAIR: each query half's releaser (tile parity 0) arrives once per pair, and at
+                // the unit's last pair also for the pairs its (short) stage did not hold
+                const uint32_t rel = PAIR ? (j + 2 >= nt_u ? (uint32_t)(1 + (C::kTPS - slot - 2) / 2) : 1u)
+                                          : (j == nt_u - 1 ? (uint32_t)(C::kTPS - slot) : 1u);
                 if (!F8 && releaser) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
                 // group maxima straight from the loads (the values themselves are not needed).
                 // One load per iteration of a loop that is not unrolled: the scratch registers
@@ -466,7 +497,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             if (!ok) break;
             unit_stage = (int)((unit_stage + (nt_u + C::kTPS - 1) / C::kTPS) % C::kStages);
             // one writer per (query, chunk, group): every slot written
-            if (qvalid) gr.cand[q * (2 * gr.chunks) + 2 * ch + grp] = bgid >= 0 ? pack_best(best, (uint32_t)bgid) : 0ull;
+            if (qvalid) gr.cand[q * (2 * gr.chunks) + 2 * ch + tp] = bgid >= 0 ? pack_best(best, (uint32_t)bgid) : 0ull;
         }
     } else {
         // ------------------------------------------------------------ epilogue

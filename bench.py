@@ -200,11 +200,18 @@ def cpu_baseline(wl, c, budget_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.search(db, q)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, a few queries (about a quarter of the budget)
+    m1 = int(max(1, min(m, 0.25 * budget_s / max(per_q * cores, 1e-9))))
+    t1 = time.perf_counter()
+    oracle.search(db, q[:m1], nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": m / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": f"first {m} of {wl.q_raw.shape[0]} queries against all {c['n']} entries "
                       f"(binary64 exhaustive search, OpenMP over {cores} threads); "
                       f"database normalisation {norm_s:.1f}s not included",
-            "seconds": dt}
+            "seconds": dt,
+            "single_core": {"value": m1 / dt1, "unit": "queries/s", "cores": 1,
+                            "sample": f"first {m1} queries, one thread", "seconds": dt1}}
 
 
 def rank_queries(wl, c: dict, rank: int) -> np.ndarray:

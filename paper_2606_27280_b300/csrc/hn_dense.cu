@@ -574,6 +574,20 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                         // itself is recovered by the threshold kernel
                         const float m = max64_f16(r);
                         if (m > best && (t < full_tiles || e0 < n32)) { best = m; bseg = t * 2 + half; }
+                    } else if (PHASE == 2 && !F8) {
+                        // BF16 Phase 2 compares raw group maxima with tau_q: the reducing loads
+                        // return the two 32-entry maxima of this warp's 64 columns directly
+                        float g0, g1;
+                        tmem_ldmax2x32(tmem + buf * 256 + seg * 64 + lane_addr, g0, g1);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+                        const int32_t ti = t - t0;
+                        gword |= ((g0 >= thr ? 1u : 0u) | (g1 >= thr ? 2u : 0u)) << (2 * (ti & 15));
+                        if ((ti & 15) == 15 || t == t1 - 1) {
+                            gb[(int64_t)(ti >> 4) * (gr.n_qt * kDQ)] = gword;
+                            gword = 0;
+                        }
                     } else {
                         float v[64];
                         tmem_ld64(tmem + buf * 256 + seg * 64 + lane_addr, v);

@@ -81,7 +81,6 @@ static void free_index(Index *ix) {
     cudaFree(ix->rows16);
     cudaFree(ix->pre32);
     cudaFree(ix->pre16);
-    cudaFree(ix->pre16h);
     cudaFree(ix->pre8);
     cudaFree(ix->prei8);
     cudaFree(ix->mx);
@@ -231,7 +230,6 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         TRY(dalloc(&ix.prei8, (size_t)n_pad * ix.k_pad16));
     } else {
         TRY(dalloc(&ix.pre16, (size_t)n_pad * ix.k_pad16));
-        TRY(dalloc(&ix.pre16h, (size_t)n_pad * ix.k_pad16));
     }
     TRY(dalloc(&ix.mx, n));
     TRY(dalloc(&ix.dev_max, 8));
@@ -254,7 +252,7 @@ hn_status hn_index_build(const float *x, int64_t n, int32_t d, int32_t k, double
         ix.code_inv = b > 0 ? (float)(127.0 / b) : 1.f;
     }
     ix.bytes = (int64_t)n_pad * kD * (4 + 2) + (ix.pre32 ? n_pad * ix.k_pad4 * 4 : 0) +
-               (ix.pre16 ? 2 * n_pad * ix.k_pad16 * 2 : 0) +
+               (ix.pre16 ? n_pad * ix.k_pad16 * 2 : 0) +
                (ix.pre8 ? (n_pad / kF8Tile) * kF8TileBytes(ix.k_pad16) : 0) +
                (ix.prei8 ? n_pad * ix.k_pad16 : 0) + n * 4;
     if (hs[ST_NOT_NORMALIZED]) {

@@ -1,59 +1,48 @@
 // Dense prefix scan on the 5th-generation tensor cores (tcgen05), Phase 1 and
-// Phase 2 of Algorithm 1 (§3.3) for a BF16 major prefix.
+// Phase 2 of Algorithm 1 (§3.3) for a BF16 (or FP8) major prefix.
 //
-// Two forms.  The two-pass form runs Algorithm 1's phases as two scans (PHASE 1,
-// then PHASE 2 against the threshold).  The one-pass form (PHASE 4) computes the
-// prefix product once: its epilogue keeps, per (query, 32-entry group), an 8-bit
-// code of the group's largest score (hn_internal.cuh) and, per (query, chunk, entry
-// half), the best group as a threshold candidate.  The threshold kernel then scores
-// the candidates in full and k_dense_extract_codes takes the survivors from the
-// groups whose code reaches code(tau_q).  The codes cost one byte per 32 scores of
-// HBM traffic (written once, read once), against a second tensor-core pass over all
-// Q x N scores.  PHASE 3 writes every FP32 score to memory (verification only).
+// The one-pass form (PHASE 4) computes the prefix product once: its epilogue keeps, per
+// (query, 32-entry group), an 8-bit code of the group's largest score (hn_internal.cuh)
+// and, per (query, chunk, tile parity), the best group as a threshold candidate.  The
+// threshold kernel then scores the candidates in full and k_dense_extract_codes takes the
+// survivors from the groups whose code reaches code(tau_q).  The codes cost one byte per 32
+// scores of HBM traffic (written once, read once), against a second tensor-core pass over
+// all Q x N scores.  The two-pass form runs Algorithm 1's phases as two scans: Phase 1 is
+// the PHASE-4 kernel without its code map (threshold candidates only), then PHASE 2 marks,
+// against the threshold, one bit per 32-entry group whose maximum reaches tau_q, and
+// k_dense_extract scores the flagged groups.  PHASE 3 writes every FP32 score to memory
+// (verification only).
 //
-// A work unit pairs 256 queries (two 128-row A tiles, K-major) with a stream
-// of 128-entry B tiles (K-major); per B tile two tcgen05.mma per 16 prefix
-// columns compute the 256 x 128 block of prefix scores s~ = q^ . x^ into tensor
-// memory.  Reusing every B tile for 256 queries halves the L2 -> shared-memory
-// traffic of 128-query tiles, which measured as the limiting stream.
-// Products of two BF16 values are exact in FP32; the sum carries at most the
-// accumulation error bounded in the Phase-2 slack (hn_prep.cu).
+// A work unit pairs 256 queries (two 128-row A tiles, K-major) with a stream of 128-entry
+// B tiles (K-major).  BF16 PHASE 4 with two or more tiles a ring stage: one N = 256 MMA per
+// 16 prefix columns computes a 128-query half against a pair of tiles; otherwise two N = 128
+// MMAs per tile, one per query half.  Reusing every B tile for 256 queries halves the L2 ->
+// shared-memory traffic of 128-query tiles, which measured as the limiting stream.  Products
+// of two BF16 values are exact in FP32; the sum carries at most the accumulation error
+// bounded in the slack of the bound test (hn_prep.cu).
 //
-// Phase 1 only looks for good threshold candidates (their full scores are
-// certified later), so it runs on an FP16 copy of the prefix with FP16
-// accumulation and reduces packed f16 pairs; Phase 2, the certified bound test,
-// runs on the BF16 prefix with FP32 accumulation.
+// FP8 index (F8): kind::f8f6f4 with e4m3 operands.  An entry tile holds kp e4m3 bytes per
+// entry plus its per-entry scales and error terms.  Each MMA takes K = 32 bytes: the query
+// side supplies 16 hi and 16 lo bytes of one 16-column group, the entry side the same 16
+// bytes twice (its K-direction core-matrix stride is 0), so acc = (hi + lo) . x^ costs no
+// extra entry bytes.  The epilogue applies the per-entry scale and error term, u = fma(acc,
+// s_i / 256, b_i) (PHASE 2 and 3), or bounds a group's scores from its largest raw
+// accumulator (PHASE 4); it reads these from the stage, so every epilogue warp releases
+// the stage.
 //
-// FP8 index (F8): kind::f8f6f4 with e4m3 operands.  An entry tile holds kp
-// e4m3 bytes per entry plus its per-entry scales and error terms.  Each MMA
-// takes K = 32 bytes: the query side supplies 16 hi and 16 lo bytes of one
-// 16-column group, the entry side the same 16 bytes twice (its K-direction
-// core-matrix stride is 0), so acc = (hi + lo) . x^ costs no extra entry bytes.
-// The epilogue applies the per-entry scale and error term,
-//   Phase 2: u = fma(acc, s_i / 256, b_i) (packed FP32 pairs), tested against tau_q;
-//   Phase 1: FP16 product with s_i 2^11 (packed), max as for BF16;
-// it reads these from the stage, so every epilogue warp releases the stage.
-//
-// Persistent CTAs (one per SM, 19 warps):
-//   warp 0   producer: 1-D bulk copies of the 256-query unit (once per work unit)
-//            and of 16 KB stages of entry tiles into a ring in shared memory;
-//   warps 1-2 allocate 512 TMEM columns (warp 1); one lane each issues the MMAs of
-//            alternate tiles into its own 256-column accumulator and commits them;
-//   warps 3-18 epilogue (4 per SM sub-partition): TMEM -> registers (thread =
-//            query row, 64 accumulator columns per warp), one max tree, then
-//              Phase 1: running best score and its 64-entry segment per (query, chunk, segment);
-//              Phase 2: one bit per 32-entry group whose maximum reaches tau_q, stored as
-//              a coalesced word per 16 tiles; k_dense_extract then scores the flagged
-//              groups and appends their survivors.  Extracting survivors in the epilogue
-//              itself put a rare but slow path on the accumulator hand-off, which every
-//              tile waits for (c2, BF16: 27.1 ms against 18.5 + 4.9 ms for the two steps).
-// A work unit is (query tile, contiguous chunk of entry tiles); units are
-// numbered chunk-major so that the CTAs running together read the same entry
-// tiles, which then come from L2.
-// Every mbarrier wait gives up after 2 s of global time: the CTA raises a
-// shared abort flag, the others leave their loops, copies and MMAs in flight
-// are drained (again with a limit), TMEM is released and the status word
-// ST_TIMEOUT tells the host.
+// Persistent CTAs (one per SM, 20 warps):
+//   warp 0   producer: 1-D bulk copies of the 256-query unit (once per work unit) and of
+//            16 KB stages of entry tiles into a ring in shared memory;
+//   warps 1-2 allocate 512 TMEM columns (warp 1); one lane each issues the MMAs into its
+//            own 256-column accumulator and commits them;
+//   warp 3   idle (completes the first warp group for the register split);
+//   warps 4-19 epilogue (4 per SM sub-partition), TMEM -> registers with thread = query row.
+// A work unit is (query tile, contiguous chunk of entry tiles); units are numbered
+// chunk-major so that the CTAs running together read the same entry tiles, which then
+// come from L2.
+// Every mbarrier wait gives up after 2 s of global time: the CTA raises a shared abort
+// flag, the others leave their loops, copies and MMAs in flight are drained (again with a
+// limit), TMEM is released and the status word ST_TIMEOUT tells the host.
 #include <algorithm>
 
 #include <cuda_fp8.h>
@@ -83,14 +72,14 @@ constexpr int kMinDenseSmem = 120 * 1024;  // forces one CTA (and one TMEM owner
 // form of batched serving) several that share the tile format, with their work units
 // numbered group by group.
 struct DenseGroup {
-    const void *pre;              // entries, UMMA core-matrix order, n_tiles * 128 rows (FP16 or BF16)
+    const void *pre;              // entries, UMMA core-matrix order, n_tiles * 128 rows (BF16 or FP8 tiles)
     const void *qpre;             // queries, same order, n_qt * 256 rows
     int64_t n, n_tiles, nq;
     int64_t n_qt, tiles_per_chunk, chunks;
     int64_t unit0;                // global number of the group's first work unit
     const float *tau;
-    unsigned long long *cand;     // [nq][2 * chunks] PHASE 1: (best score, 64-entry segment id), PHASE 4:
-                                  //   (best group score, 32-entry group id) per (query, chunk, entry half)
+    unsigned long long *cand;     // [nq][2 * chunks] PHASE 4: (best group score, 32-entry group id)
+                                  //   per (query, chunk, tile parity)
     uint32_t *gbits;              // group map: PHASE 2 [chunk][half][word][n_qt * 256] passing-group bits,
                                   //   16 tiles a word; PHASE 4 [chunk][tile][n_qt * 256] the 4 group codes
                                   //   of a tile in a word
@@ -177,32 +166,24 @@ __device__ __forceinline__ uint32_t code_bits_unclamped(float g, float inv, floa
     return __float_as_uint(__fmaf_ru(g, inv, base));
 }
 
-// Max of 64 f16 scores held as 32 packed pairs (31 packed max + 1), as a float.
-__device__ __forceinline__ float max64_f16(uint32_t (&r)[32]) {
-    __half2 h[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) h[i] = *reinterpret_cast<__half2 *>(&r[i]);
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1)
-#pragma unroll
-        for (int i = 0; i < w; ++i) h[i] = __hmax2(h[2 * i], h[2 * i + 1]);
-    return fmaxf(__low2float(h[0]), __high2float(h[0]));
-}
-
 // MULTI: the launch covers several groups (p.groups); otherwise the one group p.g, read in
 // place from the kernel parameters.
 // REG (one-pass form only, single or multi-group): the setmaxnreg register split, and two
 // reducing TMEM loads in flight per epilogue warp instead of one.
 template <int KP, int PHASE, bool F8, bool MULTI = false, bool REG = false>
 __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_constant__ DenseParams p) {
-    static_assert(!REG || PHASE == 4, "the register split serves the one-pass form");
+    // PHASE 4: the one-pass form; PHASE 1: its epilogue without the code map (the two-pass
+    // form's Phase 1, threshold candidates only)
+    constexpr bool ONEPASS = PHASE == 4 || PHASE == 1;
+    constexpr bool CODES = PHASE == 4;
+    static_assert(!REG || ONEPASS, "the register split serves the one-pass epilogue");
     using C = DenseCfg<KP, PHASE, F8>;
     // PAIR (one-pass BF16, at least two entry tiles a ring stage): an accumulator buffer holds
     // one 128-query half of the unit against a pair of 128-entry tiles, written by ONE N = 256
     // MMA per K step instead of two N = 128 MMAs (one per query half).  Issuer i takes query
     // half i of every tile pair; TMEM use, the epilogue's loads per warp and the code words are
     // unchanged.  Measured at c2: 13.10 -> 12.6 ms, the MMA issue sitting on the hand-off chain.
-    constexpr bool PAIR = PHASE == 4 && !F8 && C::kTPS >= 2;
+    constexpr bool PAIR = ONEPASS && !F8 && C::kTPS >= 2;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
     uint8_t *sA = smem + C::kStages * C::kStageBytes;
@@ -219,14 +200,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             mbar_init(smem_u32(&b_full[i]), 1);
             // one arrival per tile of the stage (FP8: per tile and epilogue warp reading it; the
             // one-pass form's epilogue gives each tile to half the epilogue warps)
-            mbar_init(smem_u32(&b_empty[i]), F8 ? C::kTPS * (PHASE == 4 ? kEpiWarps / 2 : kEpiWarps) : C::kTPS);
+            mbar_init(smem_u32(&b_empty[i]), F8 ? C::kTPS * (ONEPASS ? kEpiWarps / 2 : kEpiWarps) : C::kTPS);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&a_full[i]), 1);
             mbar_init(smem_u32(&a_empty[i]), kIssuers);  // every issuer commits at the end of a unit
             mbar_init(smem_u32(&acc_full[i]), 1);
             // one elected arrive per epilogue warp reading the buffer (one-pass form: half of them)
-            mbar_init(smem_u32(&acc_empty[i]), PHASE == 4 ? kEpiWarps / 2 : kEpiWarps);
+            mbar_init(smem_u32(&acc_empty[i]), ONEPASS ? kEpiWarps / 2 : kEpiWarps);
         }
         for (int i = 0; i < kIssuers; ++i) mbar_init(smem_u32(&drain[i]), 1);
         *abort_flag = 0;
@@ -291,10 +272,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
         // accumulator buffer i (256 columns: A tile `sub` in columns 128*sub ..).
         if (lane == 0) {
             const uint32_t me = (uint32_t)(warp - 1);
-            // Phase 1: FP16 operands, FP16 accumulator; PHASE 2-4: BF16 operands, FP32 accumulator
-            // FP8: e4m3 operands, FP16 (Phase 1) or FP32 (PHASE 2-4) accumulator
-            constexpr uint32_t idesc = F8 ? (PHASE == 1 ? idesc_e4m3_f16(kTileQ, kDE) : idesc_e4m3_f32(kTileQ, kDE))
-                                          : (PHASE == 1 ? idesc_f16_f16(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE));
+            // BF16 operands (FP8: e4m3 operands), FP32 accumulator
+            constexpr uint32_t idesc = F8 ? idesc_e4m3_f32(kTileQ, kDE) : idesc_bf16_f32(kTileQ, kDE);
             uint32_t stage = 0, sphase = 0, abuf = 0, aphase = 0, uses = 0;
             uint64_t g = 0;  // tile counter of this CTA
             bool ok = true;
@@ -366,7 +345,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
         }
     } else if (warp < kEpiWarp0) {
         // idle: completes the first warpgroup
-    } else if (PHASE == 4) {
+    } else if (ONEPASS) {
         // ------------------------------------------------------------ epilogue, one-pass form
         // Two warp groups, one per accumulator buffer: while one group reduces its tile, the
         // other loads the next, so the TMEM loads and the max trees of an SM sub-partition
@@ -479,15 +458,17 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                 // byte of each 2^23 + code float by byte permutes.  The upper clamp only acts
                 // when the tile's largest code would pass 255 (never for scores within the norm
                 // bound); a streaming store, so that the map does not evict the prefix from L2
-                uint32_t c0 = code_bits_unclamped(s0, inv, base), c1 = code_bits_unclamped(s1, inv, base);
-                uint32_t c2 = code_bits_unclamped(s2, inv, base), c3 = code_bits_unclamped(s3, inv, base);
-                if (code_bits_unclamped(m, inv, base) > kCodeBits0 + 255u) {
-                    c0 = min(c0, kCodeBits0 + 255u);
-                    c1 = min(c1, kCodeBits0 + 255u);
-                    c2 = min(c2, kCodeBits0 + 255u);
-                    c3 = min(c3, kCodeBits0 + 255u);
+                if (CODES) {
+                    uint32_t c0 = code_bits_unclamped(s0, inv, base), c1 = code_bits_unclamped(s1, inv, base);
+                    uint32_t c2 = code_bits_unclamped(s2, inv, base), c3 = code_bits_unclamped(s3, inv, base);
+                    if (code_bits_unclamped(m, inv, base) > kCodeBits0 + 255u) {
+                        c0 = min(c0, kCodeBits0 + 255u);
+                        c1 = min(c1, kCodeBits0 + 255u);
+                        c2 = min(c2, kCodeBits0 + 255u);
+                        c3 = min(c3, kCodeBits0 + 255u);
+                    }
+                    __stcs(gb, __byte_perm(__byte_perm(c0, c1, 0x0040), __byte_perm(c2, c3, 0x0040), 0x5410));
                 }
-                __stcs(gb, __byte_perm(__byte_perm(c0, c1, 0x0040), __byte_perm(c2, c3, 0x0040), 0x5410));
                 slot += 2;
                 while (slot >= C::kTPS) {
                     slot -= C::kTPS;
@@ -522,13 +503,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
             const bool qvalid = q < gr.nq;
             const float thr = (PHASE == 2 && qvalid) ? gr.tau[q] : INFINITY;
 
-            float best = -INFINITY;
-            int32_t bseg = -1;   // PHASE 1: the 64-entry segment of `best`
             uint32_t gword = 0;  // PHASE 2: passing-group bits of the current 16 tiles
             uint32_t *gb = PHASE == 2 ? gr.gbits + (ch * 2 + half) * gr.words * (gr.n_qt * kDQ) + q
                                                       : nullptr;
             const int32_t n32 = (int32_t)gr.n;
-            const int32_t full_tiles = n32 / kDE;  // tiles below this index hold no padding rows
             int32_t e0 = t0 * kDE + half * 64;    // first entry of this warp's 64 columns
             for (int32_t tt = t0; ok && tt < t1; tt += C::kTPS) {
                 const int nt = t1 - tt < C::kTPS ? t1 - tt : C::kTPS;
@@ -546,35 +524,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                     const int32_t t = tt + j;
                     // FP8: this warp's 64 per-entry scales / error terms in the stage
                     const uint8_t *esc = smem + stage * C::kStageBytes + j * C::kB + (F8 ? f8_scale_off(KP) : 0);
-                    if (PHASE == 1) {
-                        uint32_t r[32];
-                        tmem_ld64_f16(tmem + buf * 256 + seg * 64 + lane_addr, r);
-                        if (F8) {
-                            // FP16 products acc * (s_i 2^11), packed pairs
-                            const uint4 *h4 = reinterpret_cast<const uint4 *>(esc + 2 * kF8Tile * 4) + half * 8;
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const uint4 hv = h4[i];
-                                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    __half2 a = *reinterpret_cast<__half2 *>(&r[4 * i + u]);
-                                    a = __hmul2(a, *reinterpret_cast<const __half2 *>(&hw[u]));
-                                    r[4 * i + u] = *reinterpret_cast<uint32_t *>(&a);
-                                }
-                            }
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive_cnt(smem_u32(&b_empty[stage]), rel);
-                        }
-                        // the scores are in registers: hand the accumulator back to the MMA warp now
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
-                        // running best score and the 64-entry segment holding it; the entry
-                        // itself is recovered by the threshold kernel
-                        const float m = max64_f16(r);
-                        if (m > best && (t < full_tiles || e0 < n32)) { best = m; bseg = t * 2 + half; }
-                    } else if (PHASE == 2 && !F8) {
+                    if (PHASE == 2 && !F8) {
                         // BF16 Phase 2 compares raw group maxima with tau_q: the reducing loads
                         // return the two 32-entry maxima of this warp's 64 columns directly
                         float g0, g1;
@@ -638,9 +588,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1) k_dense_scan(const __grid_co
                 if (++stage == C::kStages) { stage = 0; sphase ^= 1; }
             }
             if (!ok) break;
-            // one writer per (query, chunk, entry half): no atomics, every slot written
-            if (PHASE == 1 && qvalid)
-                gr.cand[q * (2 * gr.chunks) + 2 * ch + half] = bseg >= 0 ? pack_best(best, (uint32_t)bseg) : 0ull;
         }
     }
 
@@ -916,10 +863,13 @@ static cudaError_t set_attr1() {
 
 template <int KP, bool F8>
 static cudaError_t set_attr2() {
-    cudaError_t e = set_attr1<KP, 1, F8>();
-    if (e == cudaSuccess) e = set_attr1<KP, 2, F8>();
+    cudaError_t e = set_attr1<KP, 2, F8>();
     if (e == cudaSuccess) e = set_attr1<KP, 3, F8>();
     if (e == cudaSuccess) e = set_attr1<KP, 4, F8>();
+    if (e == cudaSuccess) e = set_attr1<KP, 1, F8>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dense_scan<KP, 1, F8, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dense_smem<KP, 1, F8>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dense_scan<KP, 4, F8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  dense_smem<KP, 4, F8>());
@@ -932,17 +882,26 @@ static cudaError_t set_attr2() {
     return e;
 }
 
-// The register-split one-pass form is launched only if its threads are launched with exactly
-// kRegLaunch registers: the split's increases draw on that launch budget.
-template <int KP, bool F8, bool MULTI>
+// The register-split one-pass epilogue (PHASE 4, or PHASE 1 without codes) is launched only
+// if its threads are launched with exactly kRegLaunch registers: the split's increases draw
+// on that launch budget.
+template <int KP, int PHASE, bool F8, bool MULTI>
 static bool reg_split_ok() {
     static int ok = -1;
     if (ok < 0) {
         cudaFuncAttributes a{};
-        ok = cudaFuncGetAttributes(&a, k_dense_scan<KP, 4, F8, MULTI, true>) == cudaSuccess &&
+        ok = cudaFuncGetAttributes(&a, k_dense_scan<KP, PHASE, F8, MULTI, true>) == cudaSuccess &&
              a.numRegs == kRegLaunch && a.maxThreadsPerBlock >= kDenseThreads;
     }
     return ok == 1;
+}
+
+template <int KP, int PHASE, bool F8>
+static void launch_onepass_kernel(const DenseParams &p, int grid, cudaStream_t st) {
+    if (!p.plain && reg_split_ok<KP, PHASE, F8, false>())
+        k_dense_scan<KP, PHASE, F8, false, true><<<grid, kDenseThreads, dense_smem<KP, PHASE, F8>(), st>>>(p);
+    else
+        k_dense_scan<KP, PHASE, F8><<<grid, kDenseThreads, dense_smem<KP, PHASE, F8>(), st>>>(p);
 }
 
 // Kernel attributes for every instantiation; called once before the first launch
@@ -967,15 +926,10 @@ static cudaError_t launch_kp(const DenseParams &p, int phase, int grid, cudaStre
     cudaError_t e = dense_init();
     if (e != cudaSuccess) return e;
     switch (phase) {
-        case 1: k_dense_scan<KP, 1, F8><<<grid, kDenseThreads, dense_smem<KP, 1, F8>(), st>>>(p); break;
+        case 1: launch_onepass_kernel<KP, 1, F8>(p, grid, st); break;
         case 2: k_dense_scan<KP, 2, F8><<<grid, kDenseThreads, dense_smem<KP, 2, F8>(), st>>>(p); break;
         case 3: k_dense_scan<KP, 3, F8><<<grid, kDenseThreads, dense_smem<KP, 3, F8>(), st>>>(p); break;
-        case 4:
-            if (!p.plain && reg_split_ok<KP, F8, false>())
-                k_dense_scan<KP, 4, F8, false, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
-            else
-                k_dense_scan<KP, 4, F8><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
-            break;
+        case 4: launch_onepass_kernel<KP, 4, F8>(p, grid, st); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -1024,6 +978,13 @@ static int64_t onepass_tile_words(const Index &ix, int64_t n_qt_all, int64_t *tp
     *tpc = std::min(n_tiles, (*tpc + 1) & ~(int64_t)1);
     *chunks = (n_tiles + *tpc - 1) / *tpc;
     return *chunks * *tpc * kDQ;
+}
+
+// Candidate slots per query that the two-pass form's Phase 1 (the one-pass chunking) writes.
+int64_t dense_phase1_slots(const Index &ix, int64_t nq) {
+    int64_t tpc = 0, chunks = 0;
+    onepass_tile_words(ix, (nq + kDQ - 1) / kDQ, &tpc, &chunks);
+    return 2 * chunks;
 }
 
 // The one-pass epilogue's tile order needs even unit lengths.
@@ -1114,14 +1075,13 @@ static cudaError_t launch_extract_any(int kp, bool f8, const ExtractParams &x, b
 }
 
 // Fields shared by every dense launch of index ix (PHASE-specific fields left zero).
-static DenseParams dense_base(const Index &ix, int phase) {
+static DenseParams dense_base(const Index &ix) {
     const Workspace &ws = ix.ws;
     const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
     DenseParams p{};
-    // FP8: one tile array for every phase; the query operands differ (qpre16h: Phase-1 e4m3 of
-    // 16 q, qpre16: the hi/lo e4m3 of 256 q of the other phases)
-    p.g.pre = f8 ? (const void *)ix.pre8 : phase == 1 ? (const void *)ix.pre16h : (const void *)ix.pre16;
-    p.g.qpre = phase == 1 ? (const void *)ws.qpre16h : (const void *)ws.qpre16;
+    // the BF16 prefix, or the FP8 tiles; the queries' BF16 A tiles, or their hi/lo e4m3 bytes
+    p.g.pre = f8 ? (const void *)ix.pre8 : (const void *)ix.pre16;
+    p.g.qpre = (const void *)ws.qpre16;
     p.g.n = ix.n;
     p.g.n_tiles = ix.n_tiles * (kTileE / kDE);  // index rows are padded to 256: whole 128-entry tiles
     p.status = ws.status;
@@ -1156,21 +1116,27 @@ static ExtractParams extract_base(const Index &ix, int64_t q0, int64_t nq_pass, 
 cudaError_t launch_dense_scan(const Index &ix, int64_t nq, int phase, cudaStream_t st) {
     if (!dense_scan_supported(ix)) return cudaErrorNotSupported;
     const Workspace &ws = ix.ws;
-    DenseParams p = dense_base(ix, phase);
+    DenseParams p = dense_base(ix);
     const int G = num_sms();
     const int64_t n_qt = (nq + kDQ - 1) / kDQ;
     const int kp = ix.k_pad16;
     const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
     if (phase == 1) {
-        int64_t chunks = 0;
-        p.g.nq = nq;
-        p.g.n_qt = n_qt;
-        dense_chunking(p.g.n_tiles, p.g.n_qt, G, ix.units_per_cta, &p.g.tiles_per_chunk, &chunks);
-        p.g.chunks = chunks;
-        p.n_units = p.g.n_qt * chunks;
-        p.g.tau = ws.tau;
-        p.g.cand = ws.cand;
-        return launch_dense_kernel(kp, f8, p, 1, (int)min64(G, p.n_units), st);
+        // Algorithm 1's Phase 1: the one-pass scan's epilogue without its code map -- the
+        // best 32-entry group per (query, entry chunk, tile parity) from the reducing loads
+        int64_t tpc = 0, chunks = 0;
+        onepass_tile_words(ix, n_qt, &tpc, &chunks);
+        DenseParams p4 = dense_base(ix);
+        p4.g.nq = nq;
+        p4.g.n_qt = n_qt;
+        p4.g.tiles_per_chunk = tpc;
+        p4.g.chunks = chunks;
+        p4.g.words = tpc;
+        p4.g.gbits = ws.gbits;
+        p4.g.cand = ws.cand;
+        p4.n_units = n_qt * chunks;
+        if (!onepass_chunking_ok(p4.g) || 2 * chunks > ws.cand_slots) return cudaErrorInvalidValue;
+        return launch_dense_kernel(kp, f8, p4, 1, (int)min64(G, p4.n_units), st);
     }
     // Phase 2: the tensor-core scan marks the passing 32-entry groups, k_dense_extract turns
     // them into survivors; passes over query tiles keep the bitmap within the workspace
@@ -1220,7 +1186,7 @@ cudaError_t launch_dense_onepass(const Index &ix, const float *q, int64_t nq, in
     if (per < 1) return cudaErrorInvalidValue;      // prepare_search sizes the map for one tile at least
     const int S = (int)(2 * chunks);                // candidate slots per query
     if (S > ws.cand_slots) return cudaErrorInvalidValue;
-    DenseParams p = dense_base(ix, 4);
+    DenseParams p = dense_base(ix);
     p.g.tiles_per_chunk = tpc;
     p.g.chunks = chunks;
     p.g.words = tpc;
@@ -1259,7 +1225,7 @@ cudaError_t launch_prefix_scores(const Index &ix, int64_t nq, int path, float *o
     const int kp = ix.k_pad16;
     const bool f8 = ix.prefix == HN_PREFIX_FP8_E4M3;
     if (path == 0) {
-        DenseParams p = dense_base(ix, 3);
+        DenseParams p = dense_base(ix);
         int64_t chunks = 0;
         p.g.nq = nq;
         p.g.n_qt = (nq + kDQ - 1) / kDQ;
@@ -1362,7 +1328,7 @@ void dense_multi_destroy(DenseMulti *m) {
 
 template <int KP, bool F8>
 static cudaError_t launch_multi_kp(const DenseParams &p, int grid, cudaStream_t st) {
-    if (reg_split_ok<KP, F8, true>())
+    if (reg_split_ok<KP, 4, F8, true>())
         k_dense_scan<KP, 4, F8, true, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);
     else
         k_dense_scan<KP, 4, F8, true><<<grid, kDenseThreads, dense_smem<KP, 4, F8>(), st>>>(p);

@@ -80,9 +80,8 @@ struct Workspace {
     float *qpre32 = nullptr;           // [q_cap][k_pad4] query prefix (FP32, or BF16 values)
     __nv_bfloat16 *qpre16 = nullptr;   // [q_cap rounded to 128][k_pad16] UMMA A tiles (FP8 index:
                                        //   the e4m3 hi/lo pairs of Phase 2, 2 * k_pad16 bytes a query)
-    __half *qpre16h = nullptr;         // same in FP16 (dense Phase 1; FP8 index: e4m3 hi, lo = 0)
-                                       // (int8 index: qpre16 holds k_pad16 int8 codes a query and
-                                       //  qpre16h, read as float[q_cap], 1 / (t_q s), see hn_prep.cu)
+    __half *qpre16h = nullptr;         // int8 index: read as float[q_cap], 1 / (t_q s) (hn_prep.cu);
+                                       // qpre16 then holds k_pad16 int8 codes a query
     float *qeps = nullptr;             // [q_cap] per-query Phase-2 slack E_q (FP32, rounded up)
     float *qeps32 = nullptr;           // [q_cap] slack of the FP32 prefix score over the master rows
                                        //   (best-first rescore): gamma_K |q_maj| max|x_maj| + minor bound
@@ -108,7 +107,6 @@ struct Index {
     __half *rows16 = nullptr;        // [n_pad][128] the rows rounded to FP16 (the rescore's bound)
     float *pre32 = nullptr;          // [n][k_pad4] FP32 prefix (HN_PREFIX_F32)
     __nv_bfloat16 *pre16 = nullptr;  // [n_tiles*256][k_pad16] BF16 prefix, UMMA core-matrix order
-    __half *pre16h = nullptr;        // FP16 copy of the same prefix (dense Phase 1 candidate search)
     uint8_t *pre8 = nullptr;         // HN_PREFIX_FP8_E4M3: [n_tiles * 2] tiles of kF8TileBytes(k_pad16)
     int8_t *prei8 = nullptr;         // HN_PREFIX_I8: [n_tiles * 256][k_pad16] int8 codes, row-major
     float qt = 0.f;                  // FP8: |q~_major| bound the per-entry error terms assume
@@ -148,18 +146,15 @@ __host__ __device__ inline int64_t pre16_offset(int64_t e, int c, int k_pad16) {
 //    matrices of 8 rows x 16 bytes]
 //   [128 x float  s_i / kF8QScale]      (scale of the Phase-2 tensor-core product)
 //   [128 x float  b_i = RU(qt * r_i)]   (r_i = |x_i,major - x~_i|: per-entry error term)
-//   [128 x half   s_i * 2^11]           (scale of the Phase-1 FP16 product)
 //   [4 x float4 (max_i s_i / kF8QScale, min_i s_i / kF8QScale, max_i b_i, 0)] over the
 //    real entries (i < n) of each 32-entry group: the one-pass scan bounds a group's
 //    largest score from its largest raw accumulator with them (zeros for a group
 //    holding padding rows only)
 constexpr int kF8Tile = 128;
-constexpr float kF8QScale = 256.f;   // Phase-2 query prefix scale (hi + lo e4m3 parts)
-constexpr float kF8QScale1 = 16.f;   // Phase-1 query prefix scale (FP16 accumulation stays finite)
-constexpr float kF8HScale = 2048.f;  // Phase-1 entry scale factor
-__host__ __device__ constexpr int64_t kF8TileBytes(int kp) { return (int64_t)kF8Tile * (kp + 10) + 64; }
+constexpr float kF8QScale = 256.f;   // query prefix scale of the tensor-core product (hi + lo e4m3 parts)
+__host__ __device__ constexpr int64_t kF8TileBytes(int kp) { return (int64_t)kF8Tile * (kp + 8) + 64; }
 __host__ __device__ inline int64_t f8_scale_off(int kp) { return (int64_t)kF8Tile * kp; }
-__host__ __device__ inline int64_t f8_group_off(int kp) { return (int64_t)kF8Tile * (kp + 10); }
+__host__ __device__ inline int64_t f8_group_off(int kp) { return (int64_t)kF8Tile * (kp + 8); }
 // byte offset of (row r, byte column c) in a K-major UMMA tile whose rows hold `row_bytes` bytes
 __host__ __device__ inline int64_t umma8_offset(int64_t r, int c, int row_bytes) {
     return (r >> 3) * (int64_t)row_bytes * 8 + (int64_t)(c >> 4) * 128 + (r & 7) * 16 + (c & 15);
@@ -262,6 +257,7 @@ cudaError_t proposal_scratch(hn_proposal *p, int64_t n, int32_t **out);
 int32_t proposal_blocks(const hn_proposal *p);
 int32_t proposal_k(const hn_proposal *p);
 int64_t dense_cand_slots(const Index &ix, int64_t nq);
+int64_t dense_phase1_slots(const Index &ix, int64_t nq);
 // uint32 words of the dense group map the workspace holds for nq queries (onepass: codes, else
 // the two-pass Phase-2 bits), at most limit_bytes when > 0, at least one query tile's
 int64_t dense_gbits_words(const Index &ix, int64_t nq, bool onepass, int64_t limit_bytes);

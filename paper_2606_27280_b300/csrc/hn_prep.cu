@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_prefix_amax(const float *__restrict__ x
 __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64_t n, int k, double alpha,
                                               int prefix, int k_pad4, int k_pad16, int64_t n_pad,
                                               float *__restrict__ rows, float *__restrict__ pre32,
-                                              __nv_bfloat16 *__restrict__ pre16, __half *__restrict__ pre16h,
+                                              __nv_bfloat16 *__restrict__ pre16,
                                               uint8_t *__restrict__ pre8, int8_t *__restrict__ prei8, float qt,
                                               float *__restrict__ mx, float *dev_max, int32_t *status) {
     const int lane = threadIdx.x & 31;
@@ -222,11 +222,6 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             pk.x = *reinterpret_cast<uint32_t *>(&lo);
             pk.y = *reinterpret_cast<uint32_t *>(&hi);
             *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16) + pre16_offset(e, c0, k_pad16)) = pk;
-            __half2 hlo = __floats2half2_rn(pv[0], pv[1]), hhi = __floats2half2_rn(pv[2], pv[3]);
-            uint2 hk;
-            hk.x = *reinterpret_cast<uint32_t *>(&hlo);
-            hk.y = *reinterpret_cast<uint32_t *>(&hhi);
-            *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(pre16h) + pre16_offset(e, c0, k_pad16)) = hk;
         }
         if (prefix == HN_PREFIX_I8 && c0 < k_pad16)
             *reinterpret_cast<uint32_t *>(prei8 + e * k_pad16 + c0) = i8w;
@@ -246,7 +241,6 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ x, int64
             const int r = (int)(e & 127);
             sc2[r] = sc / kF8QScale;
             sc2[kF8Tile + r] = e < n ? __double2float_ru((double)qt * (double)sqrt_up(res2)) : 0.f;
-            reinterpret_cast<__half *>(sc2 + 2 * kF8Tile)[r] = __float2half_rn(sc * kF8HScale);
         }
         if (e < n) {
             const float umin = sqrt_up(min2), umaj = sqrt_up(maj2), ures = sqrt_up(res2);
@@ -327,7 +321,7 @@ cudaError_t launch_pack(Index &ix, const float *x, cudaStream_t st) {
         if (e != cudaSuccess) return e;
     }
     k_pack<<<(unsigned)blocks, 256, 0, st>>>(x, ix.n, ix.k, ix.alpha, ix.prefix, ix.k_pad4, ix.k_pad16, n_pad,
-                                             ix.rows, ix.pre32, ix.pre16, ix.pre16h, ix.pre8, ix.prei8, ix.qt, ix.mx,
+                                             ix.rows, ix.pre32, ix.pre16, ix.pre8, ix.prei8, ix.qt, ix.mx,
                                              ix.dev_max,
                                              ix.ws.status);
     if (ix.prefix == HN_PREFIX_FP8_E4M3) {
@@ -400,7 +394,7 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
     // A row holds 2 * k_pad16 bytes: for every 16 prefix columns, 16 hi bytes then 16 lo bytes.
     float rq2 = 0.f, hi2 = 0.f, lo2 = 0.f, qt2 = 0.f;
     if (prefix == HN_PREFIX_FP8_E4M3) {
-        uint32_t hw = 0, lw = 0, h1 = 0;
+        uint32_t hw = 0, lw = 0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const float a = pv[t] * kF8QScale;                   // exact
@@ -410,7 +404,6 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
             const float lf = f8_decode(lb);
             hw |= (uint32_t)hb << (8 * t);
             lw |= (uint32_t)lb << (8 * t);
-            h1 |= (uint32_t)f8_encode(pv[t] * kF8QScale1) << (8 * t);
             const float qq = (hf + lf) / kF8QScale;  // exact
             const float r = pv[t] - qq;               // exact
             rq2 = __fmaf_ru(r, r, rq2);
@@ -420,11 +413,9 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         }
         if (c0 < k_pad16) {
             const int bc = 32 * (c0 >> 4) + (c0 & 15);
-            uint8_t *a2 = reinterpret_cast<uint8_t *>(qpre16), *a1 = reinterpret_cast<uint8_t *>(qpre16h);
+            uint8_t *a2 = reinterpret_cast<uint8_t *>(qpre16);
             *reinterpret_cast<uint32_t *>(a2 + umma8_offset(j, bc, 2 * k_pad16)) = hw;
             *reinterpret_cast<uint32_t *>(a2 + umma8_offset(j, bc + 16, 2 * k_pad16)) = lw;
-            *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc, 2 * k_pad16)) = h1;
-            *reinterpret_cast<uint32_t *>(a1 + umma8_offset(j, bc + 16, 2 * k_pad16)) = 0u;
         }
         rq2 = warp_sum_up(rq2);
         hi2 = warp_sum_up(hi2);
@@ -457,11 +448,6 @@ __global__ void __launch_bounds__(256) k_query_prep(const float *__restrict__ q,
         pk.x = *reinterpret_cast<uint32_t *>(&lo);
         pk.y = *reinterpret_cast<uint32_t *>(&hi);
         *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(qpre16) + pre16_offset(j, c0, k_pad16)) = pk;
-        __half2 hlo = __floats2half2_rn(pv[0], pv[1]), hhi = __floats2half2_rn(pv[2], pv[3]);
-        uint2 hk;
-        hk.x = *reinterpret_cast<uint32_t *>(&hlo);
-        hk.y = *reinterpret_cast<uint32_t *>(&hhi);
-        *reinterpret_cast<uint2 *>(reinterpret_cast<char *>(qpre16h) + pre16_offset(j, c0, k_pad16)) = hk;
     }
     maj2 = warp_sum(maj2);
     min2 = warp_sum(min2);

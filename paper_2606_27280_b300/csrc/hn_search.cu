@@ -593,10 +593,12 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
                                   cudaStream_t st) {
     const Workspace &ws = ix.ws;
     const int64_t blocks = (nq * 32 + 255) / 256;
-    // candidates: dense segments, or (top-k) the stream scan's per-range entries, or its best entry
+    // candidates: the dense Phase 1's 32-entry groups, or (top-k) the stream scan's per-range
+    // entries, or its best entry
     const bool multi = dense || kk > 1;
+    const int S = dense ? (int)dense_phase1_slots(ix, nq) : multi ? ws.cand_slots : 1;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
-                                                       multi ? ws.cand_slots : 1, dense ? 64 : 1, ix.pre16,
+                                                       S, dense ? 32 : 1, ix.pre16,
                                                        ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
                                                        ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
                                                        keep_best ? 1 : 0);

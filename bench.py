@@ -69,6 +69,8 @@ def parse():
                     help="Phase-2 rescore of the 1-NN search (same result): certified FP16-row bound before the "
                          "FP32 row (default), the FP32 prefix bound (best first), or every survivor in FP32")
     ap.add_argument("--best-first", action="store_true", help="the same as --rescore best_first")
+    ap.add_argument("--train-precision", choices=["bf16", "fp32"], default="bf16",
+                    help="c3: the proposal's training GEMMs on the tensor cores (bf16) or the CUDA cores (fp32)")
     ap.add_argument("--no-autotune", action="store_true", help="c4: keep every index's default scan choices")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bruteforce", action="store_true")
@@ -622,7 +624,7 @@ def run_proposal(args, hn, torch, world, rank, dist, barrier):
     tq = hn.normalize(torch.from_numpy(tq_raw).cuda(), k, alpha)
     del db, tq_raw
     t0 = time.perf_counter()
-    prop = hn.Proposal.train(ix, tq, seed=7)
+    prop = hn.Proposal.train(ix, tq, seed=7, precision=0 if args.train_precision == "bf16" else 1)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del tq
@@ -658,7 +660,8 @@ def run_proposal(args, hn, torch, world, rank, dist, barrier):
                 "config": {"workload": f"c3: N={c['n']}, Q={nq}, K={k}, alpha={alpha}, {c['n_blocks']} blocks, "
                                        f"MLP {k}-256-256-{c['n_blocks']}, {c['n_train']} training pairs, top-4 seed"},
                 "seeded": res["seeded"], "plain": res["plain"], "identical_results": same,
-                "proposal": {"train_s": train_s, "final_loss": info["last_loss"], "steps": info["steps"]},
+                "proposal": {"train_s": train_s, "final_loss": info["last_loss"], "steps": info["steps"],
+                             "train_gemms": args.train_precision},
                 "index_build_s": build_s}
         print(json.dumps(line), flush=True)
     prop.close()

@@ -205,7 +205,11 @@ typedef struct hn_train_opts {
     float lr;                   /* Adam learning rate [1e-3]; beta1 0.9, beta2 0.999, eps 1e-8 */
     uint32_t seed;              /* initial weights and shuffling [0] */
     const hn_proposal *init;    /* non-NULL: continue training this network (weights, Adam state) */
-    int32_t reserved[2];        /* must be zero */
+    int32_t precision;          /* the training GEMMs: 0 = on the tensor cores with BF16 operands and
+                                   FP32 accumulation (default); 1 = FP32 CUDA-core GEMMs (the
+                                   arithmetic hn_mlp_loss_grad checks against binary64).  The master
+                                   weights and the Adam state are FP32 either way */
+    int32_t reserved[1];        /* must be zero */
 } hn_train_opts;
 
 typedef struct hn_proposal_info {
@@ -439,13 +443,33 @@ hn_status hn_proposal_destroy(hn_proposal *proposal);
 /*
  * Verification entry point of the proposal's training kernels: mean softmax
  * cross-entropy of a batch and its gradient w.r.t. all parameters, computed by
- * the same forward and backward kernels hn_proposal_train uses.  params and
- * grads: [W1 (h1 x k), b1, W2 (h2 x h1), b2, W3 (c x h2), b3] float32 (device);
- * x: batch x k, y: batch int32 labels in [0, c).  *loss is written on the host.
- * Synchronises `stream`.
+ * the same forward and backward kernels hn_proposal_train uses with precision 1
+ * (FP32 CUDA-core GEMMs).  params and grads: [W1 (h1 x k), b1, W2 (h2 x h1), b2,
+ * W3 (c x h2), b3] float32 (device); x: batch x k, y: batch int32 labels in
+ * [0, c).  *loss is written on the host.  Synchronises `stream`.
+ * hn_mlp_loss_grad_bf16: the same with the tensor-core GEMMs of precision 0 (every
+ * GEMM operand rounded to BF16, products summed in FP32); HN_ERR_TIMEOUT if a
+ * device-side wait gave up.
  */
 hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
                            const int32_t *y, int32_t batch, float *loss, float *grads, void *stream);
+hn_status hn_mlp_loss_grad_bf16(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
+                                const int32_t *y, int32_t batch, float *loss, float *grads, void *stream);
+
+/*
+ * The tensor-core GEMM of the proposal's training (an extension; the paper has no
+ * network), with strided operands so that every training product -- activations
+ * against weights, error signals against weights, transposed error signals against
+ * activations -- is one call:
+ *   c[i * ldc + j] = sum_{t<k} bf16(a[i * sai + t * sak]) * bf16(b[t * sbk + j * sbj])
+ * for i < m, j < n: operands rounded to BF16 (round to nearest even), products exact
+ * in FP32 and summed in FP32 by tcgen05.mma.  a, b, c: float32 (device,
+ * caller-owned).  Requires m, n >= 0, 1 <= k <= 65536, non-negative strides and
+ * ldc >= n (HN_ERR_INVALID_ARG otherwise).  Synchronises `stream`; HN_ERR_TIMEOUT
+ * if a device-side wait gave up.
+ */
+hn_status hn_gemm_bf16(int32_t m, int32_t n, int32_t k, const float *a, int64_t sai, int64_t sak, const float *b,
+                       int64_t sbk, int64_t sbj, float *c, int64_t ldc, void *stream);
 
 /*
  * One fully connected layer exactly as the proposal's inference runs it (an

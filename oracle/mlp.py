@@ -20,7 +20,8 @@ with the analytic gradients of that loss, and one Adam step
     p <- p - lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
 Parameters are kept as a dict of float64 arrays.  Inference runs each layer on
 BF16-rounded operands (round to nearest even) with the products summed exactly
-here (binary64) and in FP32 on the GPU: `linear_bf16`.
+here (binary64) and in FP32 on the GPU: `linear_bf16`.  Tensor-core training does
+the same to every operand of its contractions: `loss_and_grads_bf16`.
 """
 from __future__ import annotations
 
@@ -103,6 +104,43 @@ def loss_and_grads(p: dict, x: np.ndarray, y: np.ndarray):
     dh1 = da2 @ p["W2"]
     da1 = dh1 * gelu_grad(a1)
     g["W1"] = da1.T @ x
+    g["b1"] = da1.sum(axis=0)
+    return loss, g
+
+
+def loss_and_grads_bf16(p: dict, x: np.ndarray, y: np.ndarray, rnd=bf16_round):
+    """`loss_and_grads` as the tensor-core training computes it: every operand of the six
+    training contractions (the three layer products, the two back-propagated activations and
+    the three weight gradients) rounded to BF16 by `rnd`, the products then summed exactly
+    (binary64) and every other step (bias, GELU, softmax, bias gradients) exact.  With `rnd`
+    the identity this is `loss_and_grads` term for term."""
+    x = np.asarray(x, np.float64)
+    w1, w2, w3 = rnd(p["W1"]), rnd(p["W2"]), rnd(p["W3"])
+    xr = rnd(x)
+    a1 = xr @ w1.T + p["b1"]
+    h1 = gelu(a1)
+    h1r = rnd(h1)
+    a2 = h1r @ w2.T + p["b2"]
+    h2 = gelu(a2)
+    h2r = rnd(h2)
+    z = h2r @ w3.T + p["b3"]
+    b = z.shape[0]
+    zmax = z.max(axis=1, keepdims=True)
+    e = np.exp(z - zmax)
+    s = e.sum(axis=1, keepdims=True)
+    lse = zmax[:, 0] + np.log(s[:, 0])
+    loss = float(np.mean(lse - z[np.arange(b), y]))
+    dz = e / s
+    dz[np.arange(b), y] -= 1.0
+    dz /= b
+    dzr = rnd(dz)
+    g = {"W3": dzr.T @ h2r, "b3": dz.sum(axis=0)}
+    da2 = (dzr @ w3) * gelu_grad(a2)
+    da2r = rnd(da2)
+    g["W2"] = da2r.T @ h1r
+    g["b2"] = da2.sum(axis=0)
+    da1 = (da2r @ w2) * gelu_grad(a1)
+    g["W1"] = rnd(da1).T @ xr
     g["b1"] = da1.sum(axis=0)
     return loss, g
 

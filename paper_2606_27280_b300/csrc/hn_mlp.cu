@@ -123,13 +123,16 @@ __device__ __forceinline__ uint32_t lin_off(int r, int k, int ks) {
     return (uint32_t)((((r >> 3) * (ks >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
-// Stage rows [r0, r0 + rows) x columns [k0, k0 + ks) of a row-major FP32 matrix (R x K, leading
-// dimension ld) as BF16; zeros outside the matrix.  With `vec` (K, ld multiples of 4 and a 16-byte
-// aligned base) each thread moves four consecutive columns at a time -- one 16-byte load, one
-// 8-byte store (four consecutive k are contiguous in a core matrix) -- with four loads in flight
-// before any store, so that the staging is not bound by one load's latency at a time.
-__device__ __forceinline__ void lin_stage(uint8_t *dst, const float *__restrict__ src, int64_t ld, int R, int K,
-                                          int r0, int rows, int k0, int ks, bool vec) {
+// Stage rows [r0, r0 + rows) x columns [k0, k0 + ks) of an FP32 operand (R x K, element (r, k)
+// at src[r * sr + k * sk]) as BF16; zeros outside the matrix.  With `vec` (sk = 1, K and sr
+// multiples of 4, a 16-byte aligned base) each thread moves four consecutive columns at a time --
+// one 16-byte load, one 8-byte store (four consecutive k are contiguous in a core matrix) -- with
+// four loads in flight before any store, so that the staging is not bound by one load's latency
+// at a time.  Otherwise one element a thread, consecutive threads along the operand's contiguous
+// direction (k when sk = 1, else r when sr = 1), so that the loads stay coalesced.
+__device__ __forceinline__ void lin_stage(uint8_t *dst, const float *__restrict__ src, int64_t sr, int64_t sk,
+                                          int R, int K, int r0, int rows, int k0, int ks, bool vec) {
+    const int64_t ld = sr;
     if (vec) {
         const int kq = ks >> 2, total = rows * kq;
         for (int base = threadIdx.x; base < total; base += 4 * kLinThreads) {
@@ -156,11 +159,28 @@ __device__ __forceinline__ void lin_stage(uint8_t *dst, const float *__restrict_
         }
         return;
     }
-    for (int idx = threadIdx.x; idx < rows * ks; idx += kLinThreads) {
-        const int r = idx / ks, k = idx - r * ks;
-        const int gr = r0 + r, gk = k0 + k;
-        const float v = (gr < R && gk < K) ? src[(int64_t)gr * ld + gk] : 0.f;
-        *reinterpret_cast<__nv_bfloat16 *>(dst + lin_off(r, k, ks)) = __float2bfloat16_rn(v);
+    // strided operand (a transposed activation or weight): consecutive threads take consecutive
+    // rows when rows are adjacent in memory; eight loads in flight per thread before any store
+    const bool rows_fast = sk != 1 && sr == 1;
+    const int total = rows * ks;
+    for (int base = threadIdx.x; base < total; base += 8 * kLinThreads) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kLinThreads;
+            int r, k;
+            if (rows_fast) { k = idx / rows; r = idx - k * rows; } else { r = idx / ks; k = idx - r * ks; }
+            const int gr = r0 + r, gk = k0 + k;
+            v[u] = (idx < total && gr < R && gk < K) ? src[(int64_t)gr * sr + (int64_t)gk * sk] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * kLinThreads;
+            if (idx >= total) break;
+            int r, k;
+            if (rows_fast) { k = idx / rows; r = idx - k * rows; } else { r = idx / ks; k = idx - r * ks; }
+            *reinterpret_cast<__nv_bfloat16 *>(dst + lin_off(r, k, ks)) = __float2bfloat16_rn(v[u]);
+        }
     }
 }
 
@@ -186,13 +206,18 @@ __device__ __forceinline__ void topk_insert(float (&ts)[TK], int (&ti)[TK], floa
 // TK = 0: store out.  TK = 4 or 8 (the proposal's last layer): no output matrix; each row's
 // TK best columns of this CTA's 256 (score desc, column asc) go to cand[row][blockIdx.x][TK] as
 // pack_best keys, 0 for none, and k_topk_keys picks the row's best among its tiles.
+// in: element (r, k) at in[r * sai + k * sak]; w: element (j, k) at w[j * swj + k * swk].
+// pre (TK = 0, act 1, may be NULL): the pre-activation values, stored like out.
 template <int TK>
 __global__ void __launch_bounds__(kLinThreads) k_linear_bf16(int M, int N, int K, const float *__restrict__ in,
-                                                             int64_t ldi, const float *__restrict__ w, int64_t ldw,
+                                                             int64_t sai, int64_t sak, const float *__restrict__ w,
+                                                             int64_t swj, int64_t swk,
                                                              const float *__restrict__ bias, int act,
                                                              float *__restrict__ out, int64_t ldo,
+                                                             float *__restrict__ pre,
                                                              unsigned long long *__restrict__ cand,
-                                                             int32_t *__restrict__ status) {
+                                                             int32_t *__restrict__ status, int kper,
+                                                             float *__restrict__ part) {
     extern __shared__ __align__(1024) uint8_t lsm[];
     uint8_t *sa = lsm, *sb = lsm + 2 * kLinA;
     uint64_t *done = reinterpret_cast<uint64_t *>(lsm + 2 * (kLinA + kLinB));  // [2] MMA completion per slice buffer
@@ -215,22 +240,24 @@ __global__ void __launch_bounds__(kLinThreads) k_linear_bf16(int M, int N, int K
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     constexpr uint32_t idesc = idesc_bf16_f32(kLinM, kLinN);
+    // this CTA's share of K: [kbeg, kend), a multiple of 16 wide (kper is a multiple of kLinKs)
     const int kp = (K + 15) & ~15;
-    const bool vec_in = (K & 3) == 0 && (ldi & 3) == 0 && ((uintptr_t)in & 15u) == 0;
-    const bool vec_w = (K & 3) == 0 && (ldw & 3) == 0 && ((uintptr_t)w & 15u) == 0;
-    const int slices = (kp + kLinKs - 1) / kLinKs;
+    const int kbeg = (int)min((int64_t)blockIdx.z * kper, (int64_t)kp), kend = (int)min((int64_t)kbeg + kper, (int64_t)kp);
+    const bool vec_in = sak == 1 && (K & 3) == 0 && (sai & 3) == 0 && ((uintptr_t)in & 15u) == 0;
+    const bool vec_w = swk == 1 && (K & 3) == 0 && (swj & 3) == 0 && ((uintptr_t)w & 15u) == 0;
+    const int slices = (kend - kbeg + kLinKs - 1) / kLinKs;
     constexpr uint64_t kLimit = 2000000000ull;
     bool ok = true;
     int issued = 0;  // slices whose MMAs were issued (and committed)
     for (int s = 0; s < slices; ++s) {
-        const int buf = s & 1, k0 = s * kLinKs, ks = min(kLinKs, kp - k0);
+        const int buf = s & 1, k0 = kbeg + s * kLinKs, ks = min(kLinKs, kend - k0);
         // the MMAs of slice s - 2 read this buffer: wait for their commit
         if (s >= 2) {
             ok = mbar_wait(smem_u32(&done[buf]), (uint32_t)(((s - 2) >> 1) & 1), abort_flag, kLimit);
             if (!__syncthreads_and(ok)) break;
         }
-        lin_stage(sa + buf * kLinA, in, ldi, M, K, r0, kLinM, k0, ks, vec_in);
-        lin_stage(sb + buf * kLinB, w, ldw, N, K, c0, kLinN, k0, ks, vec_w);
+        lin_stage(sa + buf * kLinA, in, sai, sak, M, K, r0, kLinM, k0, ks, vec_in);
+        lin_stage(sb + buf * kLinB, w, swj, swk, N, K, c0, kLinN, k0, ks, vec_w);
         // generic-proxy stores must be visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -259,16 +286,28 @@ __global__ void __launch_bounds__(kLinThreads) k_linear_bf16(int M, int N, int K
         const int rl = quarter * 32 + lane, r = r0 + rl;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         if constexpr (TK == 0) {
+            // a K split writes its plain partial sums to its own (M x N) slab of `part`
+            float *o = part ? part + (int64_t)blockIdx.z * M * N : out;
+            const int64_t ldd = part ? N : ldo;
             for (int cb = colhalf * (kLinN / 2); cb < (colhalf + 1) * (kLinN / 2); cb += 32) {
                 float v[32];
                 tmem_ld32(tmem + cb + lane_addr, v);
-                if (r < M) {
+                if (r < M && part) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int j = c0 + cb + i;
+                        if (j < N) o[(int64_t)r * ldd + j] = v[i];
+                    }
+                } else if (r < M) {
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
                         const int j = c0 + cb + i;
                         if (j < N) {
                             float x = v[i] + (bias ? bias[j] : 0.f);
-                            if (act == 1) x = gelu_f(x);
+                            if (act == 1) {
+                                if (pre) pre[(int64_t)r * ldo + j] = x;
+                                x = gelu_f(x);
+                            }
                             out[(int64_t)r * ldo + j] = x;
                         }
                     }
@@ -343,17 +382,19 @@ __global__ void k_topk_keys(const unsigned long long *__restrict__ cand, int64_t
 }
 
 template <int TK>
-static cudaError_t launch_linear(int M, int N, int K, const float *in, int64_t ldi, const float *w, int64_t ldw,
-                                 const float *bias, int act, float *out, int64_t ldo, unsigned long long *cand,
-                                 int32_t *status, cudaStream_t st) {
+static cudaError_t launch_linear(int M, int N, int K, const float *in, int64_t sai, int64_t sak, const float *w,
+                                 int64_t swj, int64_t swk, const float *bias, int act, float *out, int64_t ldo,
+                                 float *pre, unsigned long long *cand, int32_t *status, cudaStream_t st,
+                                 int splits = 1, int kper = 1 << 30, float *part = nullptr) {
     static bool ready = false;
     if (!ready) {
         cudaError_t e = cudaFuncSetAttribute(k_linear_bf16<TK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLinSmem);
         if (e != cudaSuccess) return e;
         ready = true;
     }
-    dim3 grid((unsigned)((N + kLinN - 1) / kLinN), (unsigned)((M + kLinM - 1) / kLinM));
-    k_linear_bf16<TK><<<grid, kLinThreads, kLinSmem, st>>>(M, N, K, in, ldi, w, ldw, bias, act, out, ldo, cand, status);
+    dim3 grid((unsigned)((N + kLinN - 1) / kLinN), (unsigned)((M + kLinM - 1) / kLinM), (unsigned)splits);
+    k_linear_bf16<TK><<<grid, kLinThreads, kLinSmem, st>>>(M, N, K, in, sai, sak, w, swj, swk, bias, act, out, ldo, pre,
+                                                           cand, status, kper, part);
     return cudaGetLastError();
 }
 
@@ -361,7 +402,72 @@ cudaError_t linear_bf16(int M, int N, int K, const float *in, int64_t ldi, const
                         const float *bias, int act, float *out, int64_t ldo, int32_t *status, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
     if (M < 0 || N < 0 || K < 1) return cudaErrorInvalidValue;
-    return launch_linear<0>(M, N, K, in, ldi, w, ldw, bias, act, out, ldo, nullptr, status, st);
+    return launch_linear<0>(M, N, K, in, ldi, 1, w, ldw, 1, bias, act, out, ldo, nullptr, nullptr, status, st);
+}
+
+static int g_lin_sms = 0;
+static int lin_sms() {
+    if (g_lin_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_lin_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_lin_sms <= 0) g_lin_sms = 148;
+    }
+    return g_lin_sms;
+}
+
+// K split of a tensor-core GEMM whose output tiles alone would leave SMs idle (a weight
+// gradient: K is the batch, M x N the weight): enough splits for about two CTAs per SM, each
+// at least four K slices.  Returns the split count; *kper = K elements per split, a multiple of
+// kLinKs, every split non-empty.
+static int lin_splits(int M, int N, int K, int *kper) {
+    const int64_t tiles = (int64_t)((M + kLinM - 1) / kLinM) * ((N + kLinN - 1) / kLinN);
+    const int kp = (K + 15) & ~15;
+    const int64_t want = std::min<int64_t>((kp + 4 * kLinKs - 1) / (4 * kLinKs), std::max<int64_t>(1, 2 * lin_sms() / tiles));
+    if (want <= 1) {
+        *kper = 1 << 30;
+        return 1;
+    }
+    int per = (int)((kp + want - 1) / want);
+    per = (per + kLinKs - 1) / kLinKs * kLinKs;
+    *kper = per;
+    return (kp + per - 1) / per;
+}
+
+// Partial-sum floats any split GEMM needs at most: splits x M x N <= 2 SMs x tiles x tile area.
+static int64_t lin_split_cap() { return (int64_t)2 * lin_sms() * kLinM * kLinN; }
+
+// C = the partial slabs summed in split order (deterministic).
+__global__ void k_splitk_sum(const float *__restrict__ part, int splits, int M, int N, float *__restrict__ C,
+                             int64_t ldc) {
+    const int64_t mn = (int64_t)M * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+        float v = part[e];
+        for (int z = 1; z < splits; ++z) v += part[z * mn + e];
+        const int64_t i = e / N;
+        C[i * ldc + (e - i * N)] = v;
+    }
+}
+
+// The training GEMMs on the tensor cores, with the FP32 gemm()'s operand convention:
+// C(i,j) = sum_k bf16(A(i,k)) bf16(B(k,j)) [+ bias[j], act, pre], A(i,k) = A[i*sai + k*sak],
+// B(k,j) = B[k*sbk + j*sbj]; products exact, summed in FP32.  Without bias or activation and
+// given a partial-sum buffer of lin_split_cap() floats, K is split across CTAs.
+static cudaError_t gemm_bf16(int M, int N, int K, const float *A, int64_t sai, int64_t sak, const float *B, int64_t sbk,
+                             int64_t sbj, float *C, int64_t ldc, int32_t *status, cudaStream_t st,
+                             const float *bias = nullptr, int act = 0, float *pre = nullptr, float *part = nullptr) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    if (M < 0 || N < 0 || K < 1) return cudaErrorInvalidValue;
+    int kper = 1 << 30, splits = 1;
+    if (part && !bias && act == 0 && !pre) splits = lin_splits(M, N, K, &kper);
+    if (splits == 1)
+        return launch_linear<0>(M, N, K, A, sai, sak, B, sbj, sbk, bias, act, C, ldc, pre, nullptr, status, st);
+    cudaError_t e = launch_linear<0>(M, N, K, A, sai, sak, B, sbj, sbk, nullptr, 0, C, ldc, nullptr, nullptr, status, st,
+                                     splits, kper, part);
+    if (e != cudaSuccess) return e;
+    const int64_t mn = (int64_t)M * N;
+    k_splitk_sum<<<(unsigned)std::min<int64_t>((mn + 255) / 256, 8 * lin_sms()), 256, 0, st>>>(part, splits, M, N, C, ldc);
+    return cudaGetLastError();
 }
 
 // Last layer with its top-k fused (topk <= 8): per row the topk best columns of
@@ -373,8 +479,8 @@ static cudaError_t linear_bf16_topk(int M, int N, int K, const float *in, int64_
     if (M == 0) return cudaSuccess;
     const int tiles = (N + kLinN - 1) / kLinN;
     const int tk = topk <= 4 ? 4 : 8;
-    cudaError_t e = tk == 4 ? launch_linear<4>(M, N, K, in, ldi, w, ldw, bias, 0, nullptr, 0, cand, status, st)
-                            : launch_linear<8>(M, N, K, in, ldi, w, ldw, bias, 0, nullptr, 0, cand, status, st);
+    cudaError_t e = tk == 4 ? launch_linear<4>(M, N, K, in, ldi, 1, w, ldw, 1, bias, 0, nullptr, 0, nullptr, cand, status, st)
+                            : launch_linear<8>(M, N, K, in, ldi, 1, w, ldw, 1, bias, 0, nullptr, 0, nullptr, cand, status, st);
     if (e != cudaSuccess) return e;
     k_topk_keys<<<(unsigned)(((int64_t)M * 32 + 255) / 256), 256, 0, st>>>(cand, M, tiles * tk, topk, out);
     return cudaGetLastError();
@@ -586,42 +692,56 @@ static cudaError_t forward_infer(const Net &n, const float *w, Acts &a, int rows
     return e;
 }
 
-// Training forward pass (FP32 CUDA-core GEMMs, so that the gradients stay comparable with the
-// binary64 oracle); with `train`, pre-activations are kept.
-static cudaError_t forward(const Net &n, const float *w, Acts &a, int rows, bool train, cudaStream_t st) {
-    cudaError_t e = gemm(rows, n.h1, n.k, a.x, n.k, 1, w + n.o_w1, 1, n.k, a.h1, n.h1, st, 0.f, w + n.o_b1, 1,
-                         train ? a.a1 : nullptr);
+// The training GEMMs: with `bf16` on the tensor cores (BF16 operands, FP32 accumulation, the
+// precision the proposal is specified in), otherwise FP32 CUDA-core tiles (the gradient check
+// against the binary64 oracle).  status: device word set to 1 if a tensor-core wait gave up.
+struct TrainGemm {
+    bool bf16;
+    int32_t *status;
+    cudaStream_t st;
+    float *part = nullptr;  // lin_split_cap() floats: K-split partial sums (weight gradients)
+    cudaError_t operator()(int M, int N, int K, const float *A, int64_t sai, int64_t sak, const float *B, int64_t sbk,
+                           int64_t sbj, float *C, int64_t ldc, const float *bias = nullptr, int act = 0,
+                           float *pre = nullptr) const {
+        return bf16 ? gemm_bf16(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, status, st, bias, act, pre, part)
+                    : gemm(M, N, K, A, sai, sak, B, sbk, sbj, C, ldc, st, 0.f, bias, act, pre);
+    }
+};
+
+// Training forward pass; with `train`, pre-activations are kept.
+static cudaError_t forward(const Net &n, const float *w, Acts &a, int rows, bool train, const TrainGemm &G) {
+    cudaError_t e = G(rows, n.h1, n.k, a.x, n.k, 1, w + n.o_w1, 1, n.k, a.h1, n.h1, w + n.o_b1, 1, train ? a.a1 : nullptr);
     if (e == cudaSuccess)
-        e = gemm(rows, n.h2, n.h1, a.h1, n.h1, 1, w + n.o_w2, 1, n.h1, a.h2, n.h2, st, 0.f, w + n.o_b2, 1,
-                 train ? a.a2 : nullptr);
-    if (e == cudaSuccess) e = gemm(rows, n.c, n.h2, a.h2, n.h2, 1, w + n.o_w3, 1, n.h2, a.z, n.c, st, 0.f, w + n.o_b3, 0);
+        e = G(rows, n.h2, n.h1, a.h1, n.h1, 1, w + n.o_w2, 1, n.h1, a.h2, n.h2, w + n.o_b2, 1, train ? a.a2 : nullptr);
+    if (e == cudaSuccess) e = G(rows, n.c, n.h2, a.h2, n.h2, 1, w + n.o_w3, 1, n.h2, a.z, n.c, w + n.o_b3, 0);
     return e;
 }
 
 // Loss (row losses in a.row_loss) and parameter gradients g for labels a.y; a.z is overwritten by dz.
-static cudaError_t backward(const Net &n, const float *w, Acts &a, int rows, float *g, cudaStream_t st) {
+static cudaError_t backward(const Net &n, const float *w, Acts &a, int rows, float *g, const TrainGemm &G) {
+    cudaStream_t st = G.st;
     const unsigned wb = (unsigned)((rows * 32 + 255) / 256);
     k_softmax_xent<<<wb, 256, 0, st>>>(a.z, a.y, rows, n.c, 1.f / rows, a.z, a.row_loss);
     float *dz = a.z;
     cudaError_t e = cudaGetLastError();
     // layer 3
-    if (e == cudaSuccess) e = gemm(n.c, n.h2, rows, dz, 1, n.c, a.h2, n.h2, 1, g + n.o_w3, n.h2, st);
+    if (e == cudaSuccess) e = G(n.c, n.h2, rows, dz, 1, n.c, a.h2, n.h2, 1, g + n.o_w3, n.h2);
     if (e == cudaSuccess) { k_colsum<<<(n.c + 255) / 256, 256, 0, st>>>(dz, rows, n.c, g + n.o_b3); e = cudaGetLastError(); }
-    if (e == cudaSuccess) e = gemm(rows, n.h2, n.c, dz, n.c, 1, w + n.o_w3, n.h2, 1, a.dh2, n.h2, st);
+    if (e == cudaSuccess) e = G(rows, n.h2, n.c, dz, n.c, 1, w + n.o_w3, n.h2, 1, a.dh2, n.h2);
     if (e == cudaSuccess) {
         k_gelu_back<<<(unsigned)(((int64_t)rows * n.h2 + 255) / 256), 256, 0, st>>>(a.dh2, a.a2, (int64_t)rows * n.h2, a.dh2);
         e = cudaGetLastError();
     }
     // layer 2
-    if (e == cudaSuccess) e = gemm(n.h2, n.h1, rows, a.dh2, 1, n.h2, a.h1, n.h1, 1, g + n.o_w2, n.h1, st);
+    if (e == cudaSuccess) e = G(n.h2, n.h1, rows, a.dh2, 1, n.h2, a.h1, n.h1, 1, g + n.o_w2, n.h1);
     if (e == cudaSuccess) { k_colsum<<<(n.h2 + 255) / 256, 256, 0, st>>>(a.dh2, rows, n.h2, g + n.o_b2); e = cudaGetLastError(); }
-    if (e == cudaSuccess) e = gemm(rows, n.h1, n.h2, a.dh2, n.h2, 1, w + n.o_w2, n.h1, 1, a.dh1, n.h1, st);
+    if (e == cudaSuccess) e = G(rows, n.h1, n.h2, a.dh2, n.h2, 1, w + n.o_w2, n.h1, 1, a.dh1, n.h1);
     if (e == cudaSuccess) {
         k_gelu_back<<<(unsigned)(((int64_t)rows * n.h1 + 255) / 256), 256, 0, st>>>(a.dh1, a.a1, (int64_t)rows * n.h1, a.dh1);
         e = cudaGetLastError();
     }
     // layer 1
-    if (e == cudaSuccess) e = gemm(n.h1, n.k, rows, a.dh1, 1, n.h1, a.x, n.k, 1, g + n.o_w1, n.k, st);
+    if (e == cudaSuccess) e = G(n.h1, n.k, rows, a.dh1, 1, n.h1, a.x, n.k, 1, g + n.o_w1, n.k);
     if (e == cudaSuccess) { k_colsum<<<(n.h1 + 255) / 256, 256, 0, st>>>(a.dh1, rows, n.h1, g + n.o_b1); e = cudaGetLastError(); }
     return e;
 }
@@ -763,6 +883,8 @@ hn_status hn_proposal_train(const hn_index *index, const float *train_q, const i
     const float lr = o.lr > 0 ? o.lr : 1e-3f;
     if (h1 < 1 || h2 < 1 || h1 > 4096 || h2 > 4096 || epochs < 0 || batch < 1 || batch > (1 << 20))
         return fail(HN_ERR_INVALID_ARG, "bad training options");
+    if (o.precision != 0 && o.precision != 1) return fail(HN_ERR_INVALID_ARG, "precision must be 0 or 1");
+    if (o.reserved[0]) return fail(HN_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (o.init && (o.init->net.k != ix.k || o.init->n_blocks != ix.n_blocks))
         return fail(HN_ERR_INVALID_ARG, "init proposal does not match the index");
     cudaStream_t st = (cudaStream_t)stream;
@@ -821,6 +943,12 @@ hn_status hn_proposal_train(const hn_index *index, const float *train_q, const i
     }
     // training
     if (e == cudaSuccess && hs == HN_OK) e = p->acts.ensure(n, std::min<int64_t>(batch, npairs), true);
+    int32_t *gstatus = nullptr;  // set by a tensor-core GEMM whose bounded wait gave up
+    if (e == cudaSuccess && hs == HN_OK) e = cudaMalloc(&gstatus, sizeof(int32_t));
+    if (e == cudaSuccess && hs == HN_OK) e = cudaMemsetAsync(gstatus, 0, sizeof(int32_t), st);
+    float *gpart = nullptr;  // K-split partial sums of the tensor-core weight gradients
+    if (e == cudaSuccess && hs == HN_OK && o.precision == 0) e = cudaMalloc(&gpart, sizeof(float) * lin_split_cap());
+    const TrainGemm G{o.precision == 0, gstatus, st, gpart};
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (int ep = 0; e == cudaSuccess && hs == HN_OK && ep < epochs; ++ep) {
         const uint64_t salt = ((uint64_t)o.seed << 32) ^ (uint64_t)(p->epochs_done + 1) * 0xD1B54A32D192ED03ull;
@@ -834,8 +962,8 @@ hn_status hn_proposal_train(const hn_index *index, const float *train_q, const i
             const int rows = (int)std::min<int64_t>(batch, npairs - r0);
             k_gather_prefix<<<(unsigned)(((int64_t)rows * n.k + 255) / 256), 256, 0, st>>>(
                 train_q, perm + r0, rows, n.k, p->acts.x, y_all, p->acts.y);
-            TRYE(forward(n, p->w, p->acts, rows, true, st));
-            TRYE(backward(n, p->w, p->acts, rows, g, st));
+            TRYE(forward(n, p->w, p->acts, rows, true, G));
+            TRYE(backward(n, p->w, p->acts, rows, g, G));
             ++p->step;
             const float c1 = 1.f - powf(b1, (float)p->step), c2 = 1.f - powf(b2, (float)p->step);
             k_adam<<<(unsigned)((n.np + 255) / 256), 256, 0, st>>>(p->w, g, p->m, p->v, n.np, lr, b1, b2, eps, c1, c2);
@@ -853,9 +981,14 @@ hn_status hn_proposal_train(const hn_index *index, const float *train_q, const i
     if (e == cudaSuccess && hs == HN_OK) {
         k_round_bf16<<<(unsigned)((n.np + 255) / 256), 256, 0, st>>>(p->w, n.np, p->w_inf);
         TRYE(cudaGetLastError());
+        int32_t hstat = 0;
+        TRYE(cudaMemcpyAsync(&hstat, gstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         TRYE(cudaStreamSynchronize(st));
+        if (e == cudaSuccess && hstat) hs = fail(HN_ERR_TIMEOUT, "a tensor-core training GEMM's device-side wait timed out");
     }
 #undef TRYE
+    cudaFree(gstatus);
+    cudaFree(gpart);
     cudaFree(y_all); cudaFree(perm); cudaFree(keys); cudaFree(g); cudaFree(loss_dev); cudaFree(nn); cudaFree(nn_sim);
     if (hs != HN_OK) { destroy_proposal(p); return hs; }
     if (e != cudaSuccess) { destroy_proposal(p); return cuda_fail(e, "hn_proposal_train"); }
@@ -953,8 +1086,8 @@ hn_status hn_proposal_load(const char *path, hn_proposal **out) {
     return HN_OK;
 }
 
-hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
-                           const int32_t *y, int32_t batch, float *loss, float *grads, void *stream) {
+static hn_status mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
+                               const int32_t *y, int32_t batch, float *loss, float *grads, bool bf16, void *stream) {
     if (!params || !x || !y || !loss || !grads) return fail(HN_ERR_INVALID_ARG, "NULL argument");
     if (k < 1 || h1 < 1 || h2 < 1 || c < 1 || batch < 1 || k > 4096 || h1 > 4096 || h2 > 4096 || c > (1 << 20))
         return fail(HN_ERR_INVALID_ARG, "bad sizes");
@@ -963,22 +1096,66 @@ hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h
     n.set(k, h1, h2, c);
     Acts a;
     float *loss_dev = nullptr;
+    int32_t *status = nullptr;
     cudaError_t e = a.ensure(n, batch, true);
     if (e == cudaSuccess) e = cudaMalloc(&loss_dev, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.x, x, sizeof(float) * batch * k, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(a.y, y, sizeof(int32_t) * batch, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = forward(n, params, a, batch, true, st);
-    if (e == cudaSuccess) e = backward(n, params, a, batch, grads, st);
+    float *part = nullptr;
+    if (e == cudaSuccess && bf16) e = cudaMalloc(&part, sizeof(float) * lin_split_cap());
+    const TrainGemm G{bf16, status, st, part};
+    if (e == cudaSuccess) e = forward(n, params, a, batch, true, G);
+    if (e == cudaSuccess) e = backward(n, params, a, batch, grads, G);
+    int32_t hstat = 0;
     if (e == cudaSuccess) {
         k_sum<<<1, 256, 0, st>>>(a.row_loss, batch, loss_dev);
         float h = 0;
         e = cudaMemcpyAsync(&h, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         *loss = h / batch;
     }
     cudaFree(loss_dev);
+    cudaFree(status);
+    cudaFree(part);
     a.release();
     if (e != cudaSuccess) return cuda_fail(e, "hn_mlp_loss_grad");
+    if (hstat) return fail(HN_ERR_TIMEOUT, "a tensor-core GEMM's device-side wait timed out");
+    return HN_OK;
+}
+
+hn_status hn_mlp_loss_grad(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
+                           const int32_t *y, int32_t batch, float *loss, float *grads, void *stream) {
+    return mlp_loss_grad(params, k, h1, h2, c, x, y, batch, loss, grads, false, stream);
+}
+
+hn_status hn_mlp_loss_grad_bf16(const float *params, int32_t k, int32_t h1, int32_t h2, int32_t c, const float *x,
+                                const int32_t *y, int32_t batch, float *loss, float *grads, void *stream) {
+    return mlp_loss_grad(params, k, h1, h2, c, x, y, batch, loss, grads, true, stream);
+}
+
+hn_status hn_gemm_bf16(int32_t m, int32_t n, int32_t k, const float *a, int64_t sai, int64_t sak, const float *b,
+                       int64_t sbk, int64_t sbj, float *c, int64_t ldc, void *stream) {
+    if (m < 0 || n < 0 || k < 1 || k > 65536) return fail(HN_ERR_INVALID_ARG, "need m, n >= 0 and 1 <= k <= 65536");
+    if (m == 0 || n == 0) return HN_OK;
+    if (!a || !b || !c) return fail(HN_ERR_INVALID_ARG, "NULL argument");
+    if (sai < 0 || sak < 0 || sbk < 0 || sbj < 0 || ldc < n) return fail(HN_ERR_INVALID_ARG, "bad strides");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *status = nullptr;
+    int32_t hstat = 0;
+    float *part = nullptr;
+    cudaError_t e = cudaMalloc(&status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&part, sizeof(float) * lin_split_cap());
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = gemm_bf16(m, n, k, a, sai, sak, b, sbk, sbj, c, ldc, status, st, nullptr, 0, nullptr, part);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hstat, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(status);
+    cudaFree(part);
+    if (e != cudaSuccess) return cuda_fail(e, "hn_gemm_bf16");
+    if (hstat) return fail(HN_ERR_TIMEOUT, "a device-side wait timed out");
     return HN_OK;
 }
 

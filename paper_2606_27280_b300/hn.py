@@ -43,7 +43,7 @@ class SearchOpts(ctypes.Structure):
 class TrainOpts(ctypes.Structure):
     _fields_ = [("hidden1", ctypes.c_int32), ("hidden2", ctypes.c_int32), ("epochs", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("seed", ctypes.c_uint32),
-                ("init", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 2)]
+                ("init", ctypes.c_void_p), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class ProposalInfo(ctypes.Structure):
@@ -124,6 +124,8 @@ SIGNATURES = {
     "hn_proposal_load": ([ctypes.c_char_p, _vp], _i32),
     "hn_proposal_destroy": ([_vp], _i32),
     "hn_mlp_loss_grad": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
+    "hn_mlp_loss_grad_bf16": ([_vp, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp], _i32),
+    "hn_gemm_bf16": ([_i32, _i32, _i32, _vp, _i64, _i64, _vp, _i64, _i64, _vp, _i64, _vp], _i32),
     "hn_linear_bf16": ([_vp, _i32, _i32, _vp, _i32, _vp, _i32, _vp, _vp], _i32),
     "hn_proposal_logits": ([_vp, _vp, _i64, _vp, _vp], _i32),
     "hn_bruteforce_static": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
@@ -356,14 +358,16 @@ class Proposal:
     @classmethod
     def train(cls, index: Index, train_q: torch.Tensor, labels: torch.Tensor | None = None, hidden1: int = 0,
               hidden2: int = 0, epochs: int = 0, batch: int = 0, lr: float = 0.0, seed: int = 0,
-              init: "Proposal | None" = None, stream=None) -> "Proposal":
+              init: "Proposal | None" = None, precision: int = 0, stream=None) -> "Proposal":
+        """precision 0: the training GEMMs on the tensor cores (BF16 operands, FP32 sums); 1: FP32
+        CUDA-core GEMMs.  The master weights and Adam state are FP32 either way."""
         train_q = _dev_f32(train_q, "train_q")
         if labels is not None:
             if labels.dtype != torch.int32 or not labels.is_cuda or labels.numel() != train_q.shape[0]:
                 raise ValueError("labels must be a CUDA int32 tensor with one entry per query")
             labels = labels.contiguous()
         opts = TrainOpts(hidden1=hidden1, hidden2=hidden2, epochs=epochs, batch=batch, lr=lr, seed=seed,
-                         init=init._h.value if init is not None else None)
+                         init=init._h.value if init is not None else None, precision=int(precision))
         h = ctypes.c_void_p()
         _check(_lib.hn_proposal_train(index._h, train_q.data_ptr(), labels.data_ptr() if labels is not None else None,
                                       train_q.shape[0], ctypes.byref(opts), ctypes.byref(h), _stream(stream)),
@@ -417,8 +421,9 @@ class Proposal:
         self.close()
 
 
-def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, stream=None):
-    """(mean cross-entropy, gradient) of the proposal MLP, from the library's training kernels."""
+def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, bf16: bool = False, stream=None):
+    """(mean cross-entropy, gradient) of the proposal MLP, from the library's training kernels:
+    FP32 CUDA-core GEMMs, or with `bf16` the tensor-core GEMMs (BF16 operands, FP32 sums)."""
     k, h1, h2, c = (int(v) for v in dims)
     params = params.contiguous()
     x = x.contiguous()
@@ -427,9 +432,30 @@ def mlp_loss_grad(params: torch.Tensor, dims, x: torch.Tensor, y: torch.Tensor, 
         raise TypeError("params/x float32, y int32")
     grads = torch.empty_like(params)
     loss = ctypes.c_float()
-    _check(_lib.hn_mlp_loss_grad(params.data_ptr(), k, h1, h2, c, x.data_ptr(), y.data_ptr(), x.shape[0],
-                                 ctypes.byref(loss), grads.data_ptr(), _stream(stream)), "hn_mlp_loss_grad")
+    fn = _lib.hn_mlp_loss_grad_bf16 if bf16 else _lib.hn_mlp_loss_grad
+    _check(fn(params.data_ptr(), k, h1, h2, c, x.data_ptr(), y.data_ptr(), x.shape[0],
+              ctypes.byref(loss), grads.data_ptr(), _stream(stream)), "hn_mlp_loss_grad")
     return loss.value, grads
+
+
+def gemm_bf16(a: torch.Tensor, b: torch.Tensor, m: int, n: int, k: int, sai: int, sak: int, sbk: int, sbj: int,
+              stream=None) -> torch.Tensor:
+    """out[i, j] = sum_t bf16(a_flat[i*sai + t*sak]) * bf16(b_flat[t*sbk + j*sbj]) on the tensor cores
+    (FP32 sums); a, b float32 CUDA tensors addressed through their flat storage; out (m, n)."""
+    if a.dtype != torch.float32 or b.dtype != torch.float32 or not a.is_cuda or not b.is_cuda:
+        raise TypeError("a and b: float32 CUDA tensors")
+    a = a.contiguous()
+    b = b.contiguous()
+    if min(m, n, k) < 0 or min(sai, sak, sbk, sbj) < 0:
+        raise ValueError("sizes and strides must be non-negative")
+    if m and n and k:
+        # the library reads a and b through these strides: keep every read inside the tensors
+        if (m - 1) * sai + (k - 1) * sak >= a.numel() or (k - 1) * sbk + (n - 1) * sbj >= b.numel():
+            raise ValueError("strides address elements outside a or b")
+    out = torch.empty((m, n), dtype=torch.float32, device=a.device)
+    _check(_lib.hn_gemm_bf16(int(m), int(n), int(k), a.data_ptr(), int(sai), int(sak), b.data_ptr(), int(sbk),
+                             int(sbj), out.data_ptr(), int(n), _stream(stream)), "hn_gemm_bf16")
+    return out
 
 
 def linear_bf16(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None, act: int = 0,

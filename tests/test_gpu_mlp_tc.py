@@ -12,7 +12,7 @@ import torch
 import hn_synth
 import oracle
 from oracle import mlp
-from tests._gpu_util import to_dev
+from tests._gpu_util import assert_parity, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -129,3 +129,119 @@ def test_proposal_logits_and_topk(hn, tmp_path):
     # the ranking is that of the scores: score descending, block ascending
     order = np.lexsort((np.arange(z.shape[1])[None, :].repeat(z.shape[0], 0), -z), axis=1)[:, :4]
     assert np.array_equal(top, order)
+
+
+def _strided(rng, rows, cols, row_major):
+    """A (rows, cols) matrix held row-major or column-major: (flat storage, row stride, col stride)."""
+    a = rng.standard_normal((rows, cols)).astype(np.float32)
+    if row_major:
+        return a, a.ravel(), cols, 1
+    return a, np.ascontiguousarray(a.T).ravel(), 1, rows
+
+
+@pytest.mark.parametrize("a_rows,b_rows", [(True, False), (False, True), (True, True), (False, False)])
+@pytest.mark.parametrize("m,n,k", [(300, 256, 16), (17, 40, 8), (256, 256, 1000), (129, 300, 200), (5, 3, 1),
+                                   (512, 16, 4096), (130, 70, 3001)])
+def test_gemm_bf16_strides_match_definition(hn, a_rows, b_rows, m, n, k):
+    """The training GEMM C = bf16(A) bf16(B) for every operand layout training uses (an
+    activation read by rows or, for a weight gradient, by columns; a weight read by rows or
+    transposed), at ragged sizes and K up to 1000 (a batch-sized weight-gradient contraction),
+    element by element against the binary64 definition with the FP32 sum's bound.  The long
+    contractions (K of 1000 and more on few output tiles) run split across CTAs, the last split
+    ragged at K = 3001."""
+    rng = np.random.default_rng(m * 7 + n * 3 + k)
+    a, af, sai, sak = _strided(rng, m, k, a_rows)
+    b, bf, sbk, sbj = _strided(rng, k, n, b_rows)
+    got = hn.gemm_bf16(to_dev(af), to_dev(bf), m, n, k, sai, sak, sbk, sbj).cpu().numpy().astype(np.float64)
+    ab, bb = mlp.bf16_round(a), mlp.bf16_round(b)
+    want = ab @ bb
+    gamma = k * U / (1 - k * U)
+    bound = gamma * (np.abs(ab) @ np.abs(bb)) + U * np.abs(want) + 1e-30
+    err = np.abs(got - want)
+    assert np.all(err <= bound), (float(np.max(err / bound)), float(np.max(err)))
+
+
+def test_gemm_bf16_edges(hn):
+    from paper_2606_27280_b300 import hn as binding
+    a = to_dev(np.ones(64, np.float32))
+    assert hn.gemm_bf16(a, a, 0, 4, 4, 4, 1, 4, 1).shape == (0, 4)
+    # the last elements read: a 3*16 + 15 = 63, b 15*4 + 3 = 63; both fit
+    assert torch.all(hn.gemm_bf16(a, a, 4, 4, 16, 16, 1, 4, 1) == 16.0)
+    # a split contraction sums its partials in a fixed order: repeated calls agree bit for bit
+    rng = np.random.default_rng(5)
+    x = to_dev(rng.standard_normal(4096 * 300).astype(np.float32))
+    y = to_dev(rng.standard_normal(4096 * 200).astype(np.float32))
+    r1 = hn.gemm_bf16(x, y, 300, 200, 4096, 1, 300, 200, 1)
+    r2 = hn.gemm_bf16(x, y, 300, 200, 4096, 1, 300, 200, 1)
+    assert torch.equal(r1, r2)
+    with pytest.raises(ValueError):          # one more row of a would read element 79
+        hn.gemm_bf16(a, a, 5, 4, 16, 16, 1, 4, 1)
+    with pytest.raises(hn.HNError) as e:     # K = 0 is not a contraction
+        hn.gemm_bf16(a, a, 4, 4, 0, 4, 1, 4, 1)
+    assert e.value.status == binding.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dims,batch,seed", [((16, 32, 24, 50), 64, 0), ((8, 20, 12, 7), 5, 1),
+                                             ((16, 256, 256, 300), 130, 2), ((16, 256, 256, 4096), 1024, 3)])
+def test_mlp_gradients_bf16_match_oracle(hn, dims, batch, seed):
+    """Tensor-core training gradients against the binary64 oracle that rounds every contraction
+    operand to BF16.  Where they differ: the FP32 sums (gamma_K relative) and the GPU's own FP32
+    hidden values and back-propagated signals, which may round to the neighbouring BF16 value
+    (probability about |FP32 error| / BF16 step per element, each such step 2^-8 relative); a
+    CPU simulation of that arithmetic stays below 2e-4 normwise per tensor.  The bound, 1e-3,
+    is under half of what leaving the operands unrounded moves the weight gradients (2e-3 to
+    5e-3), which the test checks on the oracle side."""
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(dims, seed)
+    for key in ("b1", "b2", "b3"):
+        p[key] = rng.standard_normal(p[key].shape) * 0.2
+    flat32 = mlp.flatten(p).astype(np.float32)
+    x = rng.standard_normal((batch, dims[0])).astype(np.float32)
+    y = rng.integers(0, dims[3], batch).astype(np.int32)
+    p64 = mlp.unflatten(flat32.astype(np.float64), dims)
+    loss_ref, g_ref = mlp.loss_and_grads_bf16(p64, x.astype(np.float64), y)
+    _, g_exact = mlp.loss_and_grads(p64, x.astype(np.float64), y)
+    loss, g = hn.mlp_loss_grad(to_dev(flat32), dims, to_dev(x), to_dev(y), bf16=True)
+    g = mlp.unflatten(g.cpu().numpy().astype(np.float64), dims)
+    assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref)), (loss, loss_ref)
+    tol = 1e-3
+    for name in mlp.PARAM_ORDER:
+        ref = np.linalg.norm(g_ref[name])
+        rel = np.linalg.norm(g[name] - g_ref[name]) / max(ref, 1e-30)
+        assert rel <= tol, (name, rel)
+        if name.startswith("W"):   # the bound tells rounded from unrounded operands apart
+            assert np.linalg.norm(g_exact[name] - g_ref[name]) / ref > 2 * tol, name
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_training_precisions_train_and_seed_exactly(hn, precision):
+    """Both training precisions bring the loss below that of a uniform guess over the blocks
+    and seed an exact search, as does the untrained network."""
+    k, alpha = 16, 1 / 8
+    w = hn_synth.make_workload(30000, 300, 6000, seed=71)
+    db = oracle.normalize(w.db_raw, k, alpha)
+    q = oracle.normalize(w.q_raw, k, alpha)
+    tq_raw, _ = hn_synth.queries_from(w.db_raw, 16000, seed=72)
+    tq = to_dev(oracle.normalize(tq_raw, k, alpha))
+    o_idx, o_sim = oracle.search(db, q)
+    with hn.Index(to_dev(db), k, alpha, prefix=1, n_blocks=128) as ix:
+        with hn.Proposal.train(ix, tq, hidden1=64, hidden2=64, epochs=0, seed=9, precision=precision) as p0, \
+             hn.Proposal.train(ix, tq, hidden1=64, hidden2=64, epochs=4, batch=1024, lr=2e-3, seed=9,
+                               precision=precision) as p4:
+            assert p4.info()["steps"] == 4 * 16
+            assert np.isfinite(p4.info()["last_loss"]) and p4.info()["last_loss"] < np.log(128)
+            r = ix.search(to_dev(q), proposal=p4, seed_topk=4)
+            assert_parity(r.idx, r.sim, o_idx, o_sim)
+            r0 = ix.search(to_dev(q), proposal=p0, seed_topk=4)
+            assert_parity(r0.idx, r0.sim, o_idx, o_sim)
+
+
+def test_training_rejects_bad_precision(hn):
+    from paper_2606_27280_b300 import hn as binding
+    k, alpha = 16, 1 / 8
+    w = hn_synth.make_workload(3000, 0, 500, seed=73)
+    db = to_dev(oracle.normalize(w.db_raw, k, alpha))
+    with hn.Index(db, k, alpha, prefix=1, n_blocks=16) as ix:
+        with pytest.raises(hn.HNError) as e:
+            hn.Proposal.train(ix, db[:256], epochs=1, precision=2)
+        assert e.value.status == binding.ERR_INVALID_ARG

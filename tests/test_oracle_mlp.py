@@ -126,3 +126,54 @@ def test_linear_bf16_is_the_plain_layer_on_rounded_operands():
     xr, wr = rng.standard_normal((5, 33)), rng.standard_normal((4, 33))
     assert np.array_equal(mlp.linear_bf16(xr, wr), mlp.bf16_round(xr) @ mlp.bf16_round(wr).T)
     assert not np.array_equal(mlp.linear_bf16(xr, wr), xr @ wr.T)
+
+
+def _case(dims, batch, seed):
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(dims, seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.3
+    return p, rng.standard_normal((batch, dims[0])), rng.integers(0, dims[3], batch)
+
+
+def test_bf16_gradient_without_rounding_is_the_exact_gradient():
+    """With the rounding taken out, the BF16-operand loss and gradients are the exact ones
+    (which the finite differences above pin), for every parameter."""
+    p, x, y = _case((5, 7, 6, 9), 11, 7)
+    l0, g0 = mlp.loss_and_grads(p, x, y)
+    l1, g1 = mlp.loss_and_grads_bf16(p, x, y, rnd=lambda a: a)
+    assert abs(l0 - l1) <= 1e-15 * abs(l0)
+    for k in mlp.PARAM_ORDER:
+        assert np.allclose(g1[k], g0[k], rtol=1e-14, atol=1e-17), k
+
+
+def test_bf16_gradient_rounds_every_contraction_operand():
+    """The rounding reaches each operand of the training contractions once: the three weight
+    matrices, the input, both hidden activations and the three back-propagated signals (dz
+    and the two GELU-scaled hidden gradients), identified by shape and, for the forward
+    activations, by value against the exact forward pass."""
+    dims, batch = (5, 7, 6, 9), 11
+    p, x, y = _case(dims, batch, 8)
+    seen = []
+    mlp.loss_and_grads_bf16(p, x, y, rnd=lambda a: (seen.append(np.array(a, np.float64)), a)[1])
+    k, h1, h2, c = dims
+    shapes = sorted(a.shape for a in seen)
+    assert shapes == sorted([(h1, k), (h2, h1), (c, h2), (batch, k), (batch, h1), (batch, h2), (batch, c),
+                             (batch, h2), (batch, h1)])
+    _, (x64, a1, h1v, a2, h2v) = mlp.forward(p, x)
+    assert any(a.shape == h1v.shape and np.array_equal(a, h1v) for a in seen)
+    assert any(a.shape == h2v.shape and np.array_equal(a, h2v) for a in seen)
+    assert any(a.shape == x64.shape and np.array_equal(a, x64) for a in seen)
+    for name in ("W1", "W2", "W3"):
+        assert any(a.shape == p[name].shape and np.array_equal(a, p[name]) for a in seen)
+
+
+def test_bf16_gradient_is_within_the_operand_rounding_of_the_exact_one():
+    """Rounding the operands moves the weight gradients by about the BF16 unit (2^-8 relative,
+    2^-9 on average per operand): normwise between 1e-4 and 2e-2 of the exact gradient."""
+    p, x, y = _case((16, 64, 48, 40), 96, 9)
+    _, g0 = mlp.loss_and_grads(p, x, y)
+    _, g1 = mlp.loss_and_grads_bf16(p, x, y)
+    for k in ("W1", "W2", "W3"):
+        rel = np.linalg.norm(g1[k] - g0[k]) / np.linalg.norm(g0[k])
+        assert 1e-4 < rel < 2e-2, (k, rel)

@@ -350,21 +350,25 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // Algorithm 1, step 2, with more than one Phase-1 candidate.  Phase 1 leaves S
 // candidate keys (prefix score, id) per query: for the stream scan S = 1 (top-1)
 // or one per entry range (top-k), the id being an entry; for the dense scan
-// S = 2 x chunks and the id names a 64-entry segment (128-entry tile * 2 + half)
-// whose maximum (FP16) prefix score is the key.  One warp per query takes the
-// R = max(4, kk) best keys; for a segment it recomputes the 64 prefix scores from
-// the stored prefixes (FP32 FMA) and keeps the best valid entry, so the R entries
-// are distinct.  Each chosen entry is scored in full in FP32 (lane l owns dims
-// 4l..4l+3), giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j>
-// (binary64, the oracle's value; eps_r bounds the FP32 error of a 128-term sum in
-// any order).  T_q is the kk-th largest of these bounds (the largest for the
-// 1-NN): at least kk entries score >= T_q, so the kk-th best similarity is >= T_q
-// (-inf when fewer than kk entries were found).  Any entry is a valid candidate:
-// the choice only decides how tight T_q is.  The Phase-2 prefix threshold is
+// S = 2 x chunks (one per entry chunk and tile parity) and the id names a 32-entry
+// group whose largest prefix score is the key.  One warp per query takes up to
+// kSeedR = 32 keys (all of them when S <= 32; the 32 largest otherwise); for a group it
+// recomputes the group's prefix scores from the stored prefixes (FP32 FMA) and keeps the
+// best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
+// FP32, giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j> (binary64, the
+// oracle's value; eps_r bounds the FP32 error of a 128-term sum in any order).  T_q is
+// the kk-th largest of these bounds (the largest for the 1-NN): at least kk entries
+// score >= T_q, so the kk-th best similarity is >= T_q (-inf when fewer than kk entries
+// were found).  Any entry is a valid candidate and the order they are scored in does not
+// matter: the choice only decides how tight T_q is.  The Phase-2 prefix threshold is
 //   tau_q = RD(T_q - E_q),
 // so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  the entry cannot
 // be among the kk best.
-constexpr int kSeedR = 4;
+// Scoring: lane r holds candidate r; eight lanes score one candidate (the group's entries
+// split eight ways, then 16 of the 128 dimensions each), four candidates at a time, so
+// the gathers of four candidates are in flight together.
+constexpr int kSeedR = 32;
+constexpr int kCandLanes = 8;
 
 __device__ inline float warp_sum_f(float v) {
 #pragma unroll
@@ -416,67 +420,125 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                                                         float *__restrict__ tau, float *__restrict__ tlow,
                                                         int32_t *__restrict__ count,
                                                         int32_t *__restrict__ bucket, int cap, int keep_best) {
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned long long s_keys[8][kSeedR];  // 256 threads: eight warps
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (j >= nq) return;
     if (lane == 0) count[j] = 0;
     const unsigned long long *cj = cand + j * (int64_t)S;
-    const int R = kk > kSeedR ? kk : kSeedR;
-    float lb = -INFINITY;  // lane r: the bound of the entry found in round r
-    int64_t lb_e = -1;     // and that entry
-    int found = 0;
-    const float4 qv = reinterpret_cast<const float4 *>(q + j * kD)[lane];
-    const float *qp = qpre32 + j * kp;
-    const float eps_r = rescore_eps(qnorm[j], xnorm_max);
-    unsigned long long taken = ~0ull;
-    for (int r = 0; r < R; ++r) {
-        unsigned long long km = 0;
-        for (int s = lane; s < S; s += 32) {
-            const unsigned long long k = cj[s];
-            if (k < taken && k > km) km = k;
+    // 1. the candidate keys, lane r holding the r-th (0: none); nc = how many lanes hold one
+    unsigned long long mine = 0ull;
+    int nc = 0;
+    if (S <= 2 * kSeedR) {
+        // the non-empty keys of rank < kSeedR (rank = larger keys, equal keys by slot),
+        // compacted in slot order
+        const unsigned long long k0 = lane < S ? cj[lane] : 0ull;
+        const unsigned long long k1 = lane + 32 < S ? cj[lane + 32] : 0ull;
+        int r0 = 0, r1 = 0;
+        for (int o = 0; o < 32; ++o) {
+            const unsigned long long a0 = __shfl_sync(0xffffffffu, k0, o), a1 = __shfl_sync(0xffffffffu, k1, o);
+            r0 += (a0 > k0 || (a0 == k0 && o < lane)) + (a1 > k0);
+            r1 += (a0 >= k1) + (a1 > k1 || (a1 == k1 && o < lane));
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(0xffffffffu, km, o);
-            km = other > km ? other : km;
-        }
-        if (km == 0ull) break;
-        taken = km;
-        int64_t e = best_idx(km);
-        if (seg_entries > 1) {
-            // best valid entry of the segment by recomputed prefix score (lowest index on ties)
-            const int64_t e0 = e * seg_entries;
-            unsigned long long kb = 0;
-            for (int i = lane; i < seg_entries; i += 32) {
-                const int64_t ei = e0 + i;
-                if (ei < n) {
-                    const float sc = pre16 ? prefix_score16(pre16, ei, qp, kp) : prefix_score_rows(rows, ei, qp, kp);
-                    const unsigned long long key = pack_best(sc, (uint32_t)ei);
-                    kb = key > kb ? key : kb;
-                }
+        const bool keep0 = k0 != 0ull && r0 < kSeedR, keep1 = k1 != 0ull && r1 < kSeedR;
+        const unsigned m0 = __ballot_sync(0xffffffffu, keep0), m1 = __ballot_sync(0xffffffffu, keep1);
+        const unsigned below = (1u << lane) - 1u;
+        if (keep0) s_keys[wib][__popc(m0 & below)] = k0;
+        if (keep1) s_keys[wib][__popc(m0) + __popc(m1 & below)] = k1;
+        __syncwarp();
+        nc = __popc(m0) + __popc(m1);
+        mine = lane < nc ? s_keys[wib][lane] : 0ull;
+        __syncwarp();
+    } else {
+        // many slots (a small batch over many chunks): the kSeedR largest, one per round
+        unsigned long long taken = ~0ull;
+        for (int r = 0; r < kSeedR; ++r) {
+            unsigned long long km = 0;
+            for (int s = lane; s < S; s += 32) {
+                const unsigned long long k = cj[s];
+                if (k < taken && k > km) km = k;
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, km, o);
+                km = other > km ? other : km;
+            }
+            if (km == 0ull) break;
+            taken = km;
+            if (lane == r) mine = km;
+            nc = r + 1;
+        }
+    }
+    // 2. score them, four at a time; lane c ends with candidate c's bound and entry
+    float lb = -INFINITY;  // lane c: the certified bound of candidate c's entry
+    int64_t lb_e = -1;     // and that entry (-1: none)
+    const float *qp = qpre32 + j * kp;
+    const float eps_r = rescore_eps(qnorm[j], xnorm_max);
+    const int g = lane / kCandLanes, t = lane % kCandLanes;
+    constexpr int kPerBatch = 32 / kCandLanes;
+    for (int c0 = 0; c0 < nc; c0 += kPerBatch) {
+        const int c = c0 + g;
+        const unsigned long long key = __shfl_sync(0xffffffffu, mine, c & 31);
+        int64_t e = (c < nc && key != 0ull) ? (int64_t)best_idx(key) : -1;
+        if (seg_entries > 1) {
+            // best valid entry of the group by recomputed prefix score (lowest index on ties)
+            unsigned long long kb = 0;
+            if (e >= 0) {
+                const int64_t e0 = e * seg_entries;
+                for (int i = t; i < seg_entries; i += kCandLanes) {
+                    const int64_t ei = e0 + i;
+                    if (ei < n) {
+                        const float sc = pre16 ? prefix_score16(pre16, ei, qp, kp) : prefix_score_rows(rows, ei, qp, kp);
+                        const unsigned long long k2 = pack_best(sc, (uint32_t)ei);
+                        kb = k2 > kb ? k2 : kb;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = kCandLanes / 2; o; o >>= 1) {
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, kb, o);
                 kb = other > kb ? other : kb;
             }
-            if (kb == 0ull) continue;
-            e = best_idx(kb);
+            e = kb ? (int64_t)best_idx(kb) : -1;
         }
-        const float4 xv = reinterpret_cast<const float4 *>(rows + e * kD)[lane];
-        const float sim = warp_sum_f(fmaf(qv.x, xv.x, fmaf(qv.y, xv.y, fmaf(qv.z, xv.z, qv.w * xv.w))));
-        if (lane == found) { lb = __fsub_rd(sim, eps_r); lb_e = e; }
-        ++found;
+        // full FP32 score: 16 dimensions a lane, then a sum over the candidate's eight lanes
+        float sim = 0.f;
+        if (e >= 0) {
+            const float4 *qr = reinterpret_cast<const float4 *>(q + j * kD) + 4 * t;
+            const float4 *xr = reinterpret_cast<const float4 *>(rows + e * kD) + 4 * t;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 a = qr[u], x = xr[u];
+                sim = fmaf(a.x, x.x, sim);
+                sim = fmaf(a.y, x.y, sim);
+                sim = fmaf(a.z, x.z, sim);
+                sim = fmaf(a.w, x.w, sim);
+            }
+        }
+#pragma unroll
+        for (int o = kCandLanes / 2; o; o >>= 1) sim += __shfl_xor_sync(0xffffffffu, sim, o);
+        const float bound = __fsub_rd(sim, eps_r);
+#pragma unroll
+        for (int gi = 0; gi < kPerBatch; ++gi) {
+            const float v = __shfl_sync(0xffffffffu, bound, gi * kCandLanes);
+            const int64_t ve = __shfl_sync(0xffffffffu, e, gi * kCandLanes);
+            if (lane == c0 + gi && ve >= 0) {
+                lb = v;
+                lb_e = ve;
+            }
+        }
     }
+    const unsigned vmask = __ballot_sync(0xffffffffu, lb_e >= 0);
+    const int found = __popc(vmask);
     // the kk-th largest bound: the lane whose value has exactly kk-1 larger ones (ties by lane)
     float t_low = -INFINITY;
     if (found >= kk) {
         int rank = 0;
-        for (int o = 0; o < found; ++o) {
+        for (int o = 0; o < 32; ++o) {
             const float v = __shfl_sync(0xffffffffu, lb, o);
-            rank += (v > lb || (v == lb && o < lane)) ? 1 : 0;
+            rank += (((vmask >> o) & 1u) && (v > lb || (v == lb && o < lane))) ? 1 : 0;
         }
-        const unsigned hit = __ballot_sync(0xffffffffu, lane < found && rank == kk - 1);
+        const unsigned hit = __ballot_sync(0xffffffffu, lb_e >= 0 && rank == kk - 1);
         t_low = __shfl_sync(0xffffffffu, lb, __ffs(hit) - 1);
     }
     if (lane == 0) {

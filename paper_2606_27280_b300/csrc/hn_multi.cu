@@ -424,7 +424,7 @@ hn_status hn_autotune(hn_index *index, const int64_t *sizes, int32_t n_sizes, hn
         if (dense_min != 0x7FFFFFFF) {
             float bt = 1e30f;
             int32_t bu = ix.units_per_cta;
-            const int32_t cand[4] = {8, 16, 32, 64};
+            const int32_t cand[4] = {32, 64, 128, 256};
             for (int c = 0; st == HN_OK && c < 4; ++c) {
                 ix.units_per_cta = cand[c];
                 float t = 0;

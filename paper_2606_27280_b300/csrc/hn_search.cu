@@ -354,8 +354,8 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // or one per entry range (top-k), the id being an entry; for the dense scan
 // S = 2 x chunks (one per entry chunk and tile parity) and the id names a 32-entry
 // group whose largest prefix score is the key.  One warp per query takes up to
-// R keys, R from 4 to kSeedR = 32 growing with N (see seed_candidates): the R largest when
-// S <= 64, beyond that each of R lanes takes the largest of every R-th slot; for a group it recomputes the group's prefix
+// R keys, R from 4 to kSeedR = 32 growing with N (see seed_candidates): the R largest
+// among each lane's two largest of every 32nd slot (the R largest of all when S <= 64); for a group it recomputes the group's prefix
 // scores (FP32 FMA over the BF16 prefix, the FP8 prefix times its scale, or the FP16 rows)
 // and keeps the best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
 // FP32, giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j> (binary64, the
@@ -469,11 +469,20 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
     // 1. the candidate keys, lane r holding the r-th (0: none); nc = how many lanes hold one
     unsigned long long mine = 0ull;
     int nc = 0;
-    if (S <= 2 * kSeedR) {
-        // the non-empty keys of rank < R (rank = larger keys, equal keys by slot),
-        // compacted in slot order
-        const unsigned long long k0 = lane < S ? cj[lane] : 0ull;
-        const unsigned long long k1 = lane + 32 < S ? cj[lane + 32] : 0ull;
+    {
+        // each lane's two largest keys among slots lane, lane + 32, ... (all of them when
+        // S <= 64); of these, the non-empty keys of rank < R (rank = larger keys, equal keys
+        // by slot), compacted in slot order
+        unsigned long long k0 = 0ull, k1 = 0ull;
+        for (int s = lane; s < S; s += 32) {
+            const unsigned long long k = cj[s];
+            if (k > k0) {
+                k1 = k0;
+                k0 = k;
+            } else if (k > k1) {
+                k1 = k;
+            }
+        }
         int r0 = 0, r1 = 0;
         for (int o = 0; o < 32; ++o) {
             const unsigned long long a0 = __shfl_sync(0xffffffffu, k0, o), a1 = __shfl_sync(0xffffffffu, k1, o);
@@ -489,16 +498,6 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
         nc = __popc(m0) + __popc(m1);
         mine = lane < nc ? s_keys[wib][lane] : 0ull;
         __syncwarp();
-    } else {
-        // many slots (a small batch over many chunks): lane r < R takes the largest key among
-        // slots r, r + R, ... -- R distinct candidates, the overall best among them, without
-        // a full selection
-        if (lane < R)
-            for (int s = lane; s < S; s += R) {
-                const unsigned long long k = cj[s];
-                mine = k > mine ? k : mine;
-            }
-        nc = R;
     }
     // 2. score them, four at a time; lane c ends with candidate c's bound and entry
     float lb = -INFINITY;  // lane c: the certified bound of candidate c's entry

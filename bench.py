@@ -82,18 +82,23 @@ def parse():
 
 
 DRAM_PROFILE = os.path.join(ROOT, "profiles", "k_dense_scan_c2_dram.md")
-DENSE_SOURCE = os.path.join(ROOT, "paper_2606_27280_b300", "csrc", "hn_dense.cu")
+# the scan kernel and the header that fixes its launch configuration (work-unit granularity)
+DENSE_SOURCES = [os.path.join(ROOT, "paper_2606_27280_b300", "csrc", f) for f in ("hn_dense.cu", "hn_internal.cuh")]
 
 
 def measured_traffic(workload: str, prefix: str, scan: int):
     """DRAM bytes (read + write) per launch of the reported dense-scan kernel from the committed
     ncu capture; None unless the capture covers this workload, prefix and scan form and the
-    kernel source is unchanged since (its sha256 is recorded beside the figures)."""
+    kernel's sources are unchanged since (the sha256 of hn_dense.cu followed by hn_internal.cuh
+    is recorded beside the figures)."""
     try:
         with open(DRAM_PROFILE) as f:
             text = f.read()
-        with open(DENSE_SOURCE, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for path in DENSE_SOURCES:
+            with open(path, "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
     except OSError:
         return None
     vals = {}

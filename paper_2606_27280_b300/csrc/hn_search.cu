@@ -356,8 +356,8 @@ cudaError_t launch_stream_scan(const Index &ix, int64_t nq, int phase, cudaStrea
 // group whose largest prefix score is the key.  One warp per query takes up to
 // R keys, R from 4 to kSeedR = 32 growing with N (see seed_candidates): the R largest
 // among each lane's two largest of every 32nd slot (the R largest of all when S <= 64); for a group it recomputes the group's prefix
-// scores (FP32 FMA over the BF16 prefix, the FP8 prefix times its scale, or the FP16 rows)
-// and keeps the best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
+// scores (FP32 FMA over the BF16 prefix, or the FP8 prefix times its scale) and keeps the
+// best valid entry, so the entries are distinct.  Each chosen entry is scored in full in
 // FP32, giving the certified lower bound RD(fp32_j - eps_r) <= <q, x_j> (binary64, the
 // oracle's value; eps_r bounds the FP32 error of a 128-term sum in any order).  T_q is
 // the kk-th largest of these bounds (the largest for the 1-NN): at least kk entries
@@ -433,26 +433,9 @@ __device__ inline float prefix_score8(const uint8_t *__restrict__ pre8, int64_t 
     return s * *reinterpret_cast<const float *>(tile + f8_scale_off(kp16) + 4 * r);
 }
 
-// The same FP32 FMA chain over an entry's FP16 row (the first kp values; kp a multiple of 4).
-__device__ inline float prefix_score_h(const __half *__restrict__ rows16, int64_t e, const float *qp, int kp) {
-    const __half *x = rows16 + e * kD;
-    float s = 0.f;
-    for (int c = 0; c < kp; c += 4) {
-        const uint2 raw = *reinterpret_cast<const uint2 *>(x + c);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&raw.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&raw.y));
-        s = fmaf(qp[c], a.x, s);
-        s = fmaf(qp[c + 1], a.y, s);
-        s = fmaf(qp[c + 2], b.x, s);
-        s = fmaf(qp[c + 3], b.y, s);
-    }
-    return s;
-}
-
 __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict__ rows, const float *__restrict__ q,
                                                         int64_t nq, int64_t n, const unsigned long long *__restrict__ cand,
                                                         int S, int seg_entries, const __nv_bfloat16 *__restrict__ pre16,
-                                                        const __half *__restrict__ rows16,
                                                         const uint8_t *__restrict__ pre8, int kp16,
                                                         int kp, const float *__restrict__ qpre32,
                                                         const float *__restrict__ qeps,
@@ -519,10 +502,9 @@ __global__ void __launch_bounds__(256) k_seed_threshold(const float *__restrict_
                 for (int i = t; i < seg_entries; i += kCandLanes) {
                     const int64_t ei = e0 + i;
                     if (ei < n) {
-                        const float sc = pre16    ? prefix_score16(pre16, ei, qp, kp)
-                                         : pre8   ? prefix_score8(pre8, ei, qp, kp, kp16)
-                                         : rows16 ? prefix_score_h(rows16, ei, qp, kp)
-                                                  : prefix_score_rows(rows, ei, qp, kp);
+                        const float sc = pre16  ? prefix_score16(pre16, ei, qp, kp)
+                                         : pre8 ? prefix_score8(pre8, ei, qp, kp, kp16)
+                                                : prefix_score_rows(rows, ei, qp, kp);
                         const unsigned long long k2 = pack_best(sc, (uint32_t)ei);
                         kb = k2 > kb ? k2 : kb;
                     }
@@ -703,7 +685,7 @@ cudaError_t launch_seed_threshold(const Index &ix, const float *q, int64_t nq, b
     const bool multi = dense || kk > 1;
     const int S = dense ? (int)dense_phase1_slots(ix, nq) : multi ? ws.cand_slots : 1;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q, nq, ix.n, multi ? ws.cand : ws.key1,
-                                                       S, dense ? 32 : 1, ix.pre16, ix.rows16, ix.pre8, ix.k_pad16,
+                                                       S, dense ? 32 : 1, ix.pre16, ix.pre8, ix.k_pad16,
                                                        ix.k_pad4, ws.qpre32, ws.qeps, ws.qnorm, ix.host_max[4], kk,
                                                        ws.tau, ws.tlow, ws.count, ws.bucket, ws.bucket_cap,
                                                        keep_best ? 1 : 0, seed_candidates(ix.n, kk));
@@ -716,7 +698,7 @@ cudaError_t launch_seed_threshold_at(const Index &ix, const float *q, int64_t q0
     const int64_t blocks = (nq * 32 + 255) / 256;
     const int cap = ws.bucket_cap;
     k_seed_threshold<<<(unsigned)blocks, 256, 0, st>>>(ix.rows, q + q0 * kD, nq, ix.n, ws.cand + q0 * S, S, seg_entries,
-                                                       ix.pre16, ix.rows16, ix.pre8, ix.k_pad16, ix.k_pad4,
+                                                       ix.pre16, ix.pre8, ix.k_pad16, ix.k_pad4,
                                                        ws.qpre32 + q0 * ix.k_pad4, ws.qeps + q0,
                                                        ws.qnorm + q0, ix.host_max[4], kk, ws.tau + q0, ws.tlow + q0,
                                                        ws.count + q0, ws.bucket + q0 * cap, cap, keep_best ? 1 : 0,

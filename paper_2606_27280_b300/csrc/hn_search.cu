@@ -670,8 +670,8 @@ cudaError_t stream_argmax_f32(const float *db_pre, int64_t n_db, int64_t n_db_ti
 }
 
 // Candidates scored per query: each costs the same at any N, while the survivors a tighter
-// threshold removes grow with N -- about one per 128k entries, 4 to 32, and at least kk.
-int seed_candidates(int64_t n, int kk) {
+// threshold removes grow with N -- one per 2^17 entries, 4 to 32, and at least kk.
+static int seed_candidates(int64_t n, int kk) {
     const int64_t r = std::min<int64_t>(kSeedR, std::max<int64_t>(4, n >> 17));
     return (int)std::max<int64_t>(r, std::min(kk, kSeedR));
 }
